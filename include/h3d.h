@@ -1,0 +1,167 @@
+/*
+ * h3d.h -- C ABI of the GB300 HODLR3D library (libh3d.so).
+ *
+ * HODLR3D (Kandappan, Gujjula & Ambikasaran, arXiv 2307.16303) represents the
+ * kernel matrix A_ij = f(|r_i - r_j|), A_ii = 0 (Sec. 3.1, Eq. Laplace3D), of N
+ * points in a cube on a uniform octree (Sec. 2.1).  Pairs of same-level boxes
+ * that share no boundary or only a vertex are admissible (Definition admh3d) and
+ * are stored as low-rank factors found by partially pivoted ACA (Sec. 4.1,
+ * Eq. prank); self, edge and face neighbours at the leaf level stay dense and
+ * are recomputed on the fly in every product (Alg. 2).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named "device" must be CUDA device (or managed) memory on the
+ *     current device; the caller owns them.  Host pointers are plain memory;
+ *     page-locked memory makes the copies of h3d_matvec_host asynchronous.
+ *   - Point order: x and y are always in the caller's original point order;
+ *     the library permutes internally.
+ *   - Multi-column vectors are N x nrhs, column-major (column c starts at c*N).
+ *   - Element type of x and y is double for H3D_FP64 handles and float for
+ *     H3D_FP32 handles.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Products
+ *     are stream-ordered and asynchronous; the build synchronises the stream.
+ *   - Errors are returned as h3d_status, never by abort.  A device-side error
+ *     (for example a point outside the domain) is reported by the call that
+ *     detects it.
+ *   - A handle may be used by one stream at a time; concurrent calls on one
+ *     handle race on its internal scratch buffers.
+ */
+#ifndef H3D_H
+#define H3D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct h3d_handle_s *h3d_handle;
+
+typedef enum {
+    H3D_OK = 0,
+    H3D_ERR_ARG = 1,       /* invalid argument (null pointer, bad size, unsupported option) */
+    H3D_ERR_DOMAIN = 2,    /* a point lies outside the domain cube, or is NaN/Inf          */
+    H3D_ERR_OOM = 3,       /* a device allocation failed                                   */
+    H3D_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed                  */
+    H3D_ERR_ACA_RANK = 5,  /* an admissible block did not reach the tolerance by rank_cap  */
+    H3D_ERR_TIMEOUT = 6,   /* a bounded device wait gave up (reserved)                     */
+    H3D_ERR_STATE = 7,     /* handle in an unusable state (an earlier call failed)         */
+    H3D_ERR_DEPTH = 8      /* more than leaf_size coincident points: depth would exceed 21 */
+} h3d_status;
+
+/* Kernel functions f(r) of Sec. 3.1 / Sec. 5.1.  Laplace and Yukawa carry the
+ * 1/(4 pi) normalisation; the paper's own 1/r^4 and cos(r)/r are unnormalised. */
+typedef enum {
+    H3D_LAPLACE = 0,   /* 1 / (4 pi r)                 */
+    H3D_YUKAWA = 1,    /* exp(-kappa r) / (4 pi r)     */
+    H3D_INV_R4 = 2,    /* 1 / r^4                      */
+    H3D_COS_R = 3      /* cos(r) / r                   */
+} h3d_kernel;
+
+/* Storage and arithmetic type of the factors, the near field and x / y.
+ * ACA pivots, residuals and stopping tests are always FP64.                  */
+typedef enum {
+    H3D_FP64 = 0,
+    H3D_FP32 = 1
+} h3d_precision;
+
+typedef struct {
+    int precision;          /* h3d_precision, default H3D_FP32                          */
+    double kappa;           /* Yukawa decay, default 1.0                                 */
+    int rank_cap;           /* largest ACA rank per block, 1..512, default 512           */
+    double lo[3];           /* lower corner of the domain cube, default (-1,-1,-1)       */
+    double side;            /* edge length of the domain cube, default 2.0               */
+    int64_t workspace_bytes;/* device scratch budget for the build; 0 = automatic        */
+} h3d_options;
+
+/* Fill *opt with the defaults listed above. */
+void h3d_default_options(h3d_options *opt);
+
+/* Alg. 1 (InitializeHODLR3D): build the octree, the interaction and near lists
+ * and the ACA factors of every admissible block.
+ *   points    device, N x 3 row-major FP64 coordinates (x0,y0,z0,x1,...).  Not
+ *             retained: the handle keeps its own sorted copy.
+ *   N         number of points, 1 <= N < 2^31.
+ *   kernel    h3d_kernel.
+ *   leaf_size N_max of Sec. 2.1: the depth L is the smallest level at which no
+ *             box holds more than leaf_size points; 1..512.
+ *   tol       ACA tolerance epsilon of Alg. 1 (>= 0; 0 asks for full rank).
+ *   opt       NULL for defaults.
+ *   stream    stream for all device work; synchronised before return.
+ *   out       receives the handle; untouched on error.
+ * Errors: H3D_ERR_ARG, H3D_ERR_DOMAIN, H3D_ERR_DEPTH, H3D_ERR_ACA_RANK,
+ *         H3D_ERR_OOM, H3D_ERR_CUDA.  On error every allocation is released.  */
+h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int leaf_size,
+                     double tol, const h3d_options *opt, void *stream, h3d_handle *out);
+
+/* Alg. 2 (MatVec): y = A~ x, the dense near field recomputed on the fly plus the
+ * low-rank blocks of every level.
+ *   x  device, N x nrhs in the caller's order (read only).
+ *   y  device, N x nrhs, overwritten (not accumulated).  Must not alias x.
+ *   nrhs >= 1.
+ * Allocates nothing; enqueues kernels on `stream` and returns.               */
+h3d_status h3d_matvec(h3d_handle h, const void *x, void *y, int nrhs, void *stream);
+
+/* y = A~^T x: the same blocks with the roles of the two factors exchanged (the
+ * compressed operator is not exactly symmetric because every ordered pair is
+ * compressed on its own, as Alg. 1 does).  Arguments as h3d_matvec.          */
+h3d_status h3d_matvec_T(h3d_handle h, const void *x, void *y, int nrhs, void *stream);
+
+/* h3d_matvec with HOST x and y: copies x to the device, runs the product and
+ * copies y back, all on `stream`, then synchronises the stream.  Device staging
+ * buffers are allocated on the first call (and grown if nrhs grows) and kept by
+ * the handle.                                                                 */
+h3d_status h3d_matvec_host(h3d_handle h, const void *x_host, void *y_host, int nrhs, void *stream);
+
+/* Release every device allocation of the handle.  h3d_free(NULL) is H3D_OK.
+ * Synchronises the device before freeing.                                    */
+h3d_status h3d_free(h3d_handle h);
+
+/* Static English text for a status code. */
+const char *h3d_status_string(h3d_status s);
+
+/* Sizes and counts of a built handle (Table "ResultsNotations" quantities). */
+typedef struct {
+    int64_t N;
+    int depth;                 /* L                                                 */
+    int precision, kernel, leaf_size;
+    double tol;
+    int64_t n_boxes;           /* non-empty boxes, all levels                       */
+    int64_t n_leaves;
+    int64_t n_blocks;          /* admissible (low-rank) blocks, all levels          */
+    int64_t n_vertex_blocks;   /* of which vertex-sharing                           */
+    int64_t n_near;            /* dense self/edge/face leaf pairs                   */
+    int max_rank;
+    int64_t sum_rank;
+    int64_t factor_entries;    /* sum over blocks of r (m + n)                      */
+    int64_t factor_bytes;      /* stored factor bytes including padding             */
+    int64_t near_interactions; /* sum over near pairs of m * n                      */
+    int64_t device_bytes;      /* all device memory held by the handle              */
+    double build_ms;
+} h3d_stats;
+
+h3d_status h3d_get_stats(h3d_handle h, h3d_stats *s);
+
+/* Diagnostics (host outputs; sizes from h3d_get_stats; used by the tests).
+ * Tree: perm[s] = original index of the s-th point in Morton order; keys[s] its
+ * 63-bit Morton key; nbox[l] (l = 0..L) non-empty boxes per level; box_key /
+ * box_start / box_end per box, levels concatenated in order, boxes in Morton
+ * order within a level (box_key is the 3l-bit Morton prefix).                */
+h3d_status h3d_export_tree(h3d_handle h, int64_t *perm, uint64_t *keys, int *nbox,
+                           uint64_t *box_key, int64_t *box_start, int64_t *box_end);
+
+/* Lists: admissible blocks in (level, target, source) order with level-local
+ * box indices and class 3 = vertex, 4 = well separated; near pairs (leaf
+ * level) in (target, source) order with class 0 = self, 1 = face, 2 = edge.  */
+h3d_status h3d_export_lists(h3d_handle h, int *blk_level, int *blk_tgt, int *blk_src, int *blk_cls,
+                            int *near_tgt, int *near_src, int *near_cls);
+
+/* ACA ranks (per block) and pivots (concatenated in block order): sigma are
+ * row indices local to the target box, tau column indices local to the source. */
+h3d_status h3d_export_pivots(h3d_handle h, int *rank, int *sigma, int *tau);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* H3D_H */

@@ -1,0 +1,230 @@
+"""Thin ctypes binding over libh3d.so (C ABI in include/h3d.h).
+
+Argument marshalling only: every step of the build and of the product runs in
+the library's CUDA kernels.  PyTorch provides device memory and streams.  If
+the library has not been built, loading raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libh3d.so")
+
+KERNELS = {"laplace": 0, "yukawa": 1, "inv_r4": 2, "cos_r": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1}
+STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_OOM", 4: "H3D_ERR_CUDA",
+                5: "H3D_ERR_ACA_RANK", 6: "H3D_ERR_TIMEOUT", 7: "H3D_ERR_STATE", 8: "H3D_ERR_DEPTH"}
+
+# every entry point declared in include/h3d.h
+EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3d_matvec_host", "h3d_free",
+           "h3d_status_string", "h3d_get_stats", "h3d_export_tree", "h3d_export_lists", "h3d_export_pivots")
+
+
+class H3DError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        msg = lib().h3d_status_string(status).decode()
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)} ({msg})")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("kappa", C.c_double), ("rank_cap", C.c_int),
+                ("lo", C.c_double * 3), ("side", C.c_double), ("workspace_bytes", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("N", C.c_int64), ("depth", C.c_int), ("precision", C.c_int), ("kernel", C.c_int),
+                ("leaf_size", C.c_int), ("tol", C.c_double), ("n_boxes", C.c_int64), ("n_leaves", C.c_int64),
+                ("n_blocks", C.c_int64), ("n_vertex_blocks", C.c_int64), ("n_near", C.c_int64),
+                ("max_rank", C.c_int), ("sum_rank", C.c_int64), ("factor_entries", C.c_int64),
+                ("factor_bytes", C.c_int64), ("near_interactions", C.c_int64), ("device_bytes", C.c_int64),
+                ("build_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libh3d.so; raise if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libh3d.so not built ({LIB_PATH}); run paper_2307_16303_gb300.build_ext.build()")
+        L = C.CDLL(LIB_PATH)
+        P, i64, i32, f64 = C.c_void_p, C.c_int64, C.c_int, C.c_double
+        sig = {
+            "h3d_default_options": (None, [C.POINTER(Options)]),
+            "h3d_build": (i32, [P, i64, i32, i32, f64, C.POINTER(Options), P, C.POINTER(P)]),
+            "h3d_matvec": (i32, [P, P, P, i32, P]),
+            "h3d_matvec_T": (i32, [P, P, P, i32, P]),
+            "h3d_matvec_host": (i32, [P, P, P, i32, P]),
+            "h3d_free": (i32, [P]),
+            "h3d_status_string": (C.c_char_p, [i32]),
+            "h3d_get_stats": (i32, [P, C.POINTER(Stats)]),
+            "h3d_export_tree": (i32, [P, P, P, P, P, P, P]),
+            "h3d_export_lists": (i32, [P, P, P, P, P, P, P, P]),
+            "h3d_export_pivots": (i32, [P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _np(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+class H3DMatrix:
+    """A built HODLR3D operator.  ``points``: (N, 3) float64 CUDA tensor."""
+
+    def __init__(self, points, kernel: str = "laplace", leaf_size: int = 128, tol: float = 1e-7,
+                 precision: str = "fp32", rank_cap: int = 512, kappa: float = 1.0, lo=(-1.0, -1.0, -1.0),
+                 side: float = 2.0, workspace_bytes: int = 0, stream=None):
+        import torch
+        if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float64
+                and points.dim() == 2 and points.shape[1] == 3):
+            raise ValueError("points must be an (N, 3) float64 CUDA tensor")
+        pts = points.contiguous()
+        opt = Options()
+        lib().h3d_default_options(C.byref(opt))
+        opt.precision = PRECISIONS[precision]
+        opt.kappa = kappa
+        opt.rank_cap = rank_cap
+        for d in range(3):
+            opt.lo[d] = lo[d]
+        opt.side = side
+        opt.workspace_bytes = workspace_bytes
+        h = C.c_void_p()
+        st = lib().h3d_build(pts.data_ptr(), pts.shape[0], KERNELS[kernel], leaf_size, tol, C.byref(opt),
+                             _stream_ptr(stream), C.byref(h))
+        if st != 0:
+            raise H3DError(st, "h3d_build")
+        self._h = h
+        self.N = pts.shape[0]
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.kernel, self.leaf_size, self.tol = kernel, leaf_size, tol
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.h3d_free(self._h)
+            self._h = None
+
+    def _check_x(self, x):
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == self.dtype):
+            raise ValueError(f"x must be a CUDA {self.dtype} tensor")
+        if x.shape[0] != self.N or x.dim() not in (1, 2):
+            raise ValueError("x must have N rows")
+
+    def _apply(self, fn, x, out, stream):
+        import torch
+        self._check_x(x)
+        nrhs = 1 if x.dim() == 1 else x.shape[1]
+        # column-major N x nrhs == row-major nrhs x N
+        xc = x.contiguous() if x.dim() == 1 else x.t().contiguous()
+        if out is None:
+            out = torch.empty_like(xc)
+        st = fn(self._h, xc.data_ptr(), out.data_ptr(), nrhs, _stream_ptr(stream))
+        if st != 0:
+            raise H3DError(st, fn.__name__)
+        return out if x.dim() == 1 else out.t()
+
+    def matvec(self, x, out=None, stream=None):
+        """y = A~ x (Alg. 2).  x: (N,) or (N, nrhs) CUDA tensor of the handle's dtype."""
+        return self._apply(lib().h3d_matvec, x, out, stream)
+
+    def matvec_T(self, x, out=None, stream=None):
+        """y = A~^T x."""
+        return self._apply(lib().h3d_matvec_T, x, out, stream)
+
+    def matvec_raw(self, x_ptr: int, y_ptr: int, nrhs: int, stream=None, transpose: bool = False):
+        """Call the C ABI directly on device pointers (column-major N x nrhs)."""
+        fn = lib().h3d_matvec_T if transpose else lib().h3d_matvec
+        st = fn(self._h, x_ptr, y_ptr, nrhs, _stream_ptr(stream))
+        if st != 0:
+            raise H3DError(st, "h3d_matvec")
+
+    def matvec_host(self, x: np.ndarray, y: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """y = A~ x with host arrays (x: (N,) or column-major (N, nrhs))."""
+        dt = np.float64 if self.precision == "fp64" else np.float32
+        if x.dtype != dt or x.shape[0] != self.N:
+            raise ValueError(f"x must be a host {dt.__name__} array with N rows")
+        nrhs = 1 if x.ndim == 1 else x.shape[1]
+        if not (x.flags.f_contiguous or x.ndim == 1):
+            raise ValueError("x must be column-major")
+        if y is None:
+            y = np.empty_like(x, order="F")
+        st = lib().h3d_matvec_host(self._h, _np(x), _np(y), nrhs, _stream_ptr(stream))
+        if st != 0:
+            raise H3DError(st, "h3d_matvec_host")
+        return y
+
+    def matvec_host_ptr(self, x_ptr: int, y_ptr: int, nrhs: int, stream=None):
+        st = lib().h3d_matvec_host(self._h, x_ptr, y_ptr, nrhs, _stream_ptr(stream))
+        if st != 0:
+            raise H3DError(st, "h3d_matvec_host")
+
+    def stats(self) -> dict:
+        s = Stats()
+        st = lib().h3d_get_stats(self._h, C.byref(s))
+        if st != 0:
+            raise H3DError(st, "h3d_get_stats")
+        return s.as_dict()
+
+    def export_tree(self) -> dict:
+        s = self.stats()
+        N, nb, L = s["N"], s["n_boxes"], s["depth"]
+        perm = np.zeros(N, np.int64)
+        keys = np.zeros(N, np.uint64)
+        nbox = np.zeros(L + 1, np.int32)
+        bkey = np.zeros(nb, np.uint64)
+        bs = np.zeros(nb, np.int64)
+        be = np.zeros(nb, np.int64)
+        st = lib().h3d_export_tree(self._h, _np(perm), _np(keys), _np(nbox), _np(bkey), _np(bs), _np(be))
+        if st != 0:
+            raise H3DError(st, "h3d_export_tree")
+        return {"L": L, "perm": perm, "keys": keys, "nbox": nbox, "box_key": bkey, "box_start": bs, "box_end": be}
+
+    def export_lists(self) -> dict:
+        s = self.stats()
+        nb, nn = s["n_blocks"], s["n_near"]
+        a = {k: np.zeros(max(nb, 1), np.int32) for k in ("level", "tgt", "src", "cls")}
+        b = {k: np.zeros(max(nn, 1), np.int32) for k in ("near_tgt", "near_src", "near_cls")}
+        st = lib().h3d_export_lists(self._h, _np(a["level"]), _np(a["tgt"]), _np(a["src"]), _np(a["cls"]),
+                                    _np(b["near_tgt"]), _np(b["near_src"]), _np(b["near_cls"]))
+        if st != 0:
+            raise H3DError(st, "h3d_export_lists")
+        out = {k: v[:nb] for k, v in a.items()}
+        out.update({k: v[:nn] for k, v in b.items()})
+        return out
+
+    def export_pivots(self) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+        s = self.stats()
+        rank = np.zeros(max(s["n_blocks"], 1), np.int32)
+        sig = np.zeros(max(s["sum_rank"], 1), np.int32)
+        tau = np.zeros(max(s["sum_rank"], 1), np.int32)
+        st = lib().h3d_export_pivots(self._h, _np(rank), _np(sig), _np(tau))
+        if st != 0:
+            raise H3DError(st, "h3d_export_pivots")
+        return rank[:s["n_blocks"]], sig[:s["sum_rank"]], tau[:s["sum_rank"]]

@@ -1,0 +1,264 @@
+// h3d_api.cu -- the extern "C" entry points declared in include/h3d.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "h3d_internal.cuh"
+
+using h3d::Handle;
+
+struct h3d_handle_s {
+    Handle h;
+};
+
+namespace {
+
+template <class F>
+h3d_status guard(F &&f) {
+    try {
+        f();
+        return H3D_OK;
+    } catch (const h3d::Error &e) {
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        return H3D_ERR_OOM;
+    }
+}
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+void h3d_default_options(h3d_options *opt) {
+    if (!opt) return;
+    opt->precision = H3D_FP32;
+    opt->kappa = 1.0;
+    opt->rank_cap = h3d::kMaxRank;
+    opt->lo[0] = opt->lo[1] = opt->lo[2] = -1.0;
+    opt->side = 2.0;
+    opt->workspace_bytes = 0;
+}
+
+const char *h3d_status_string(h3d_status s) {
+    switch (s) {
+    case H3D_OK: return "ok";
+    case H3D_ERR_ARG: return "invalid argument";
+    case H3D_ERR_DOMAIN: return "point outside the domain cube (or not finite)";
+    case H3D_ERR_OOM: return "device allocation failed";
+    case H3D_ERR_CUDA: return "CUDA error";
+    case H3D_ERR_ACA_RANK: return "ACA did not reach the tolerance within rank_cap";
+    case H3D_ERR_TIMEOUT: return "bounded device wait timed out";
+    case H3D_ERR_STATE: return "handle unusable";
+    case H3D_ERR_DEPTH: return "tree depth would exceed 21 (too many coincident points)";
+    }
+    return "unknown status";
+}
+
+h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int leaf_size, double tol,
+                     const h3d_options *opt, void *stream, h3d_handle *out) {
+    if (!out || !points || N < 1 || N >= (int64_t)1 << 31) return H3D_ERR_ARG;
+    if (leaf_size < 1 || leaf_size > h3d::kMaxLeaf || !(tol >= 0.0) || !std::isfinite(tol)) return H3D_ERR_ARG;
+    if ((int)kernel < 0 || (int)kernel > 3) return H3D_ERR_ARG;
+    h3d_options o;
+    h3d_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != H3D_FP32 && o.precision != H3D_FP64) return H3D_ERR_ARG;
+    if (o.rank_cap < 1 || o.rank_cap > h3d::kMaxRank) return H3D_ERR_ARG;
+    if (!(o.side > 0.0) || !std::isfinite(o.side)) return H3D_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(o.lo[d])) return H3D_ERR_ARG;
+    if (!(o.kappa >= 0.0) || !std::isfinite(o.kappa)) return H3D_ERR_ARG;
+    if (!is_device_ptr(points)) return H3D_ERR_ARG;
+
+    h3d_handle_s *hs = new (std::nothrow) h3d_handle_s;
+    if (!hs) return H3D_ERR_OOM;
+    Handle &h = hs->h;
+    h.N = N;
+    h.kernel = kernel;
+    h.prec = o.precision;
+    h.leaf_size = leaf_size;
+    h.rank_cap = o.rank_cap;
+    h.tol = tol;
+    h.kappa = o.kappa;
+    h.side = o.side;
+    for (int d = 0; d < 3; ++d) h.lo[d] = o.lo[d];
+    cudaStream_t s = as_stream(stream);
+    const auto t0 = std::chrono::steady_clock::now();
+    h3d_status st = guard([&] {
+        h3d::Arena tmp;
+        h.d_err = h.mem.get<int>(1);
+        h3d::build_tree(h, points, s, tmp);
+        h3d::build_lists(h, s, tmp);
+        h3d::build_factors(h, s, tmp, o.workspace_bytes);
+        h3d::build_matvec_plan(h, s, tmp);
+        H3D_CUDA(cudaStreamSynchronize(s));
+    });
+    if (st != H3D_OK) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        delete hs;
+        return st;
+    }
+    h.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    h.ok = true;
+    *out = hs;
+    return H3D_OK;
+}
+
+static h3d_status matvec_common(h3d_handle hh, const void *x, void *y, int nrhs, void *stream, bool transpose) {
+    if (!hh) return H3D_ERR_ARG;
+    Handle &h = hh->h;
+    if (!h.ok) return H3D_ERR_STATE;
+    if (!x || !y || nrhs < 1 || x == y) return H3D_ERR_ARG;
+    return guard([&] { h3d::run_matvec(h, x, y, nrhs, transpose, as_stream(stream)); });
+}
+
+h3d_status h3d_matvec(h3d_handle h, const void *x, void *y, int nrhs, void *stream) {
+    return matvec_common(h, x, y, nrhs, stream, false);
+}
+
+h3d_status h3d_matvec_T(h3d_handle h, const void *x, void *y, int nrhs, void *stream) {
+    return matvec_common(h, x, y, nrhs, stream, true);
+}
+
+h3d_status h3d_matvec_host(h3d_handle hh, const void *x_host, void *y_host, int nrhs, void *stream) {
+    if (!hh) return H3D_ERR_ARG;
+    Handle &h = hh->h;
+    if (!h.ok) return H3D_ERR_STATE;
+    if (!x_host || !y_host || nrhs < 1) return H3D_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    return guard([&] {
+        const size_t bytes = (size_t)h.N * (size_t)nrhs * h.elem();
+        if (h.host_cols < nrhs) {
+            H3D_CUDA(cudaStreamSynchronize(s));
+            if (h.hx) h.mem.free_one(h.hx);
+            if (h.hy) h.mem.free_one(h.hy);
+            h.hx = h.hy = nullptr;
+            h.host_cols = 0;
+            h.hx = h.mem.alloc(bytes);
+            h.hy = h.mem.alloc(bytes);
+            h.host_cols = nrhs;
+        }
+        H3D_CUDA(cudaMemcpyAsync(h.hx, x_host, bytes, cudaMemcpyHostToDevice, s));
+        h3d::run_matvec(h, h.hx, h.hy, nrhs, false, s);
+        H3D_CUDA(cudaMemcpyAsync(y_host, h.hy, bytes, cudaMemcpyDeviceToHost, s));
+        H3D_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+h3d_status h3d_free(h3d_handle hh) {
+    if (!hh) return H3D_OK;
+    cudaDeviceSynchronize();
+    delete hh;
+    return H3D_OK;
+}
+
+h3d_status h3d_get_stats(h3d_handle hh, h3d_stats *st) {
+    if (!hh || !st) return H3D_ERR_ARG;
+    const Handle &h = hh->h;
+    if (!h.ok) return H3D_ERR_STATE;
+    std::memset(st, 0, sizeof(*st));
+    st->N = h.N;
+    st->depth = h.L;
+    st->precision = h.prec;
+    st->kernel = h.kernel;
+    st->leaf_size = h.leaf_size;
+    st->tol = h.tol;
+    st->n_boxes = h.n_boxes;
+    st->n_leaves = h.nleaf;
+    st->n_blocks = h.nblk;
+    st->n_near = h.nnear;
+    st->max_rank = h.max_rank;
+    st->sum_rank = h.sum_rank;
+    st->factor_entries = h.factor_entries;
+    st->factor_bytes = (h.u_elems + h.v_elems) * (int64_t)h.elem();
+    st->near_interactions = h.near_interactions;
+    st->device_bytes = (int64_t)h.mem.total();
+    st->build_ms = h.build_ms;
+    // vertex blocks: count on demand
+    std::vector<unsigned char> cls((size_t)h.nblk);
+    if (h.nblk > 0 && cudaMemcpy(cls.data(), h.blk_cls, (size_t)h.nblk, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return H3D_ERR_CUDA;
+    st->n_vertex_blocks = std::count(cls.begin(), cls.end(), (unsigned char)3);
+    return H3D_OK;
+}
+
+h3d_status h3d_export_tree(h3d_handle hh, int64_t *perm, uint64_t *keys, int *nbox, uint64_t *box_key,
+                           int64_t *box_start, int64_t *box_end) {
+    if (!hh || !perm || !keys || !nbox || !box_key || !box_start || !box_end) return H3D_ERR_ARG;
+    const Handle &h = hh->h;
+    if (!h.ok) return H3D_ERR_STATE;
+    return guard([&] {
+        const size_t n = (size_t)h.N, nb = (size_t)h.n_boxes;
+        std::vector<int> p(n), bs(nb), be(nb);
+        H3D_CUDA(cudaMemcpy(p.data(), h.perm, n * sizeof(int), cudaMemcpyDeviceToHost));
+        H3D_CUDA(cudaMemcpy(keys, h.keys, n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        H3D_CUDA(cudaMemcpy(box_key, h.box_key, nb * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        H3D_CUDA(cudaMemcpy(bs.data(), h.box_start, nb * sizeof(int), cudaMemcpyDeviceToHost));
+        H3D_CUDA(cudaMemcpy(be.data(), h.box_end, nb * sizeof(int), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) perm[i] = p[i];
+        for (size_t i = 0; i < nb; ++i) { box_start[i] = bs[i]; box_end[i] = be[i]; }
+        for (int l = 0; l <= h.L; ++l) nbox[l] = h.nbox[l];
+    });
+}
+
+h3d_status h3d_export_lists(h3d_handle hh, int *blk_level, int *blk_tgt, int *blk_src, int *blk_cls, int *near_tgt,
+                            int *near_src, int *near_cls) {
+    if (!hh) return H3D_ERR_ARG;
+    const Handle &h = hh->h;
+    if (!h.ok) return H3D_ERR_STATE;
+    if (h.nblk > 0 && (!blk_level || !blk_tgt || !blk_src || !blk_cls)) return H3D_ERR_ARG;
+    if (!near_tgt || !near_src || !near_cls) return H3D_ERR_ARG;
+    return guard([&] {
+        const size_t nb = (size_t)h.nblk, nn = (size_t)h.nnear;
+        std::vector<unsigned char> lev(nb), cls(nb), ncl(nn);
+        std::vector<int> nptr((size_t)h.nleaf + 1);
+        if (nb > 0) {
+            H3D_CUDA(cudaMemcpy(lev.data(), h.blk_lev, nb, cudaMemcpyDeviceToHost));
+            H3D_CUDA(cudaMemcpy(cls.data(), h.blk_cls, nb, cudaMemcpyDeviceToHost));
+            H3D_CUDA(cudaMemcpy(blk_tgt, h.blk_tgt, nb * sizeof(int), cudaMemcpyDeviceToHost));
+            H3D_CUDA(cudaMemcpy(blk_src, h.blk_src, nb * sizeof(int), cudaMemcpyDeviceToHost));
+        }
+        for (size_t b = 0; b < nb; ++b) {
+            blk_level[b] = lev[b];
+            blk_cls[b] = cls[b];
+            blk_tgt[b] -= (int)h.box_off[lev[b]];
+            blk_src[b] -= (int)h.box_off[lev[b]];
+        }
+        H3D_CUDA(cudaMemcpy(nptr.data(), h.near_ptr, nptr.size() * sizeof(int), cudaMemcpyDeviceToHost));
+        H3D_CUDA(cudaMemcpy(near_src, h.near_src, nn * sizeof(int), cudaMemcpyDeviceToHost));
+        H3D_CUDA(cudaMemcpy(ncl.data(), h.near_cls, nn, cudaMemcpyDeviceToHost));
+        for (int z = 0; z < h.nleaf; ++z)
+            for (int p = nptr[z]; p < nptr[z + 1]; ++p) near_tgt[p] = z;
+        for (size_t p = 0; p < nn; ++p) near_cls[p] = ncl[p];
+    });
+}
+
+h3d_status h3d_export_pivots(h3d_handle hh, int *rank, int *sigma, int *tau) {
+    if (!hh) return H3D_ERR_ARG;
+    const Handle &h = hh->h;
+    if (!h.ok) return H3D_ERR_STATE;
+    if ((h.nblk > 0 && !rank) || (h.sum_rank > 0 && (!sigma || !tau))) return H3D_ERR_ARG;
+    return guard([&] {
+        if (h.nblk > 0) H3D_CUDA(cudaMemcpy(rank, h.rank, (size_t)h.nblk * sizeof(int), cudaMemcpyDeviceToHost));
+        if (h.sum_rank > 0) {
+            H3D_CUDA(cudaMemcpy(sigma, h.sigma, (size_t)h.sum_rank * sizeof(int), cudaMemcpyDeviceToHost));
+            H3D_CUDA(cudaMemcpy(tau, h.tau, (size_t)h.sum_rank * sizeof(int), cudaMemcpyDeviceToHost));
+        }
+    });
+}
+
+}  // extern "C"

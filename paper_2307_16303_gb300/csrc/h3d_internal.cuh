@@ -1,0 +1,285 @@
+// h3d_internal.cuh -- shared declarations of the CUDA HODLR3D library.
+//
+// Data layout in HBM (all indices refer to points in Morton order):
+//   points     px/py/pz: FP64 SoA, sorted; ploc: float4 per point, FP32 offset
+//              from the centre of its leaf box (near field in FP32).
+//   boxes      all non-empty boxes of all levels, level-major, Morton order
+//              inside a level; index g is "global", g - box_off[l] "level-local".
+//   blocks     admissible pairs (target X, source Y) of every level in
+//              (level, target, source) order.
+//   U factors  target side, per box A at level l: one panel per leaf Z under A,
+//              panel = ld_Z x R_A column-major (ld_Z = m_Z rounded up to the
+//              vector width), R_A = sum of the ranks of A's blocks.  A leaf
+//              task reads one contiguous panel per level.
+//   V factors  source side, per box Y: n_Y x ldv_Y row-major, ldv_Y = R'_Y
+//              rounded up, R'_Y = sum of ranks of the blocks whose source is Y.
+//   t          per block b, r_b entries at tofs_b (target-major order), so the
+//              coefficients of all blocks of a target box are contiguous.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "../../include/h3d.h"
+
+namespace h3d {
+
+constexpr int kMaxDepth = 21;
+constexpr int kMaxLeaf = 512;
+constexpr int kMaxRank = 512;
+
+// 1 / (4 pi) to more digits than a double holds.
+#define H3D_INV4PI 0.0795774715459476678844418816863
+
+// ----------------------------------------------------------------------------
+// error handling
+struct Error {
+    h3d_status st;
+};
+
+#define H3D_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e__ = (call);                                                        \
+        if (e__ != cudaSuccess) {                                                        \
+            if (getenv("H3D_DEBUG"))                                                     \
+                fprintf(stderr, "h3d: %s failed at %s:%d: %s\n", #call, __FILE__, __LINE__, \
+                        cudaGetErrorString(e__));                                        \
+            throw ::h3d::Error{e__ == cudaErrorMemoryAllocation ? H3D_ERR_OOM : H3D_ERR_CUDA}; \
+        }                                                                                \
+    } while (0)
+
+#define H3D_LAUNCH_CHECK() H3D_CUDA(cudaGetLastError())
+
+inline void fail(h3d_status st) { throw Error{st}; }
+
+// Device allocation owned by the handle.
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+class Arena {
+  public:
+    ~Arena() { release(); }
+    void *alloc(size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(H3D_ERR_OOM);
+        }
+        blocks_.push_back({p, bytes});
+        total_ += bytes;
+        return p;
+    }
+    template <class T>
+    T *get(size_t n) { return static_cast<T *>(alloc(n * sizeof(T))); }
+    void free_one(void *p) {
+        for (size_t i = 0; i < blocks_.size(); ++i)
+            if (blocks_[i].p == p) {
+                cudaFree(p);
+                total_ -= blocks_[i].bytes;
+                blocks_.erase(blocks_.begin() + (long)i);
+                return;
+            }
+    }
+    void release() {
+        for (auto &b : blocks_) cudaFree(b.p);
+        blocks_.clear();
+        total_ = 0;
+    }
+    size_t total() const { return total_; }
+
+  private:
+    std::vector<DevMem> blocks_;
+    size_t total_ = 0;
+};
+
+// ----------------------------------------------------------------------------
+// the handle
+struct Handle {
+    // parameters
+    int64_t N = 0;
+    int kernel = H3D_LAPLACE, prec = H3D_FP32, leaf_size = 0, rank_cap = kMaxRank;
+    double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
+    int L = 0;
+
+    Arena mem;          // everything the handle keeps
+    int *d_err = nullptr;
+
+    // points
+    double *px = nullptr, *py = nullptr, *pz = nullptr;
+    float4 *ploc = nullptr;
+    int *perm = nullptr;         // sorted position -> original index
+    uint64_t *keys = nullptr;    // sorted keys
+
+    // boxes
+    int nbox[kMaxDepth + 1] = {0};
+    int64_t box_off[kMaxDepth + 2] = {0};
+    int64_t n_boxes = 0;
+    uint64_t *box_key = nullptr;
+    int *box_start = nullptr, *box_end = nullptr, *box_parent = nullptr;
+    int *box_leaf_lo = nullptr, *box_leaf_hi = nullptr;   // leaf (level-local) range under a box
+    int nleaf = 0;
+    int *leaf_anc = nullptr;     // [(l-1) * nleaf + z] global ancestor at level l (l = 1..L)
+    int *point_leaf = nullptr;   // sorted point -> level-local leaf index
+
+    // blocks (admissible, all levels)
+    int64_t nblk = 0;
+    int64_t blk_off[kMaxDepth + 2] = {0};
+    int *blk_tgt = nullptr, *blk_src = nullptr;  // global box indices
+    unsigned char *blk_cls = nullptr, *blk_lev = nullptr;
+    int *blk_partner = nullptr;                   // index of the transposed block
+    int64_t *tgt_ptr = nullptr;                   // per global box: first block with this target (n_boxes + 1)
+
+    // near lists (leaf level)
+    int64_t nnear = 0;
+    int *near_ptr = nullptr;                      // per leaf, nleaf + 1
+    int *near_src = nullptr;                      // level-local leaf index
+    unsigned char *near_cls = nullptr;
+    unsigned char *near_dir = nullptr;            // packed offset (dx+1)*9+(dy+1)*3+(dz+1)
+
+    // ranks and pivots
+    int *rank = nullptr;
+    int64_t *piv_off = nullptr;                   // nblk + 1
+    int *sigma = nullptr, *tau = nullptr;
+    int64_t sum_rank = 0;
+    int max_rank = 0;
+
+    // factor layout
+    int *R = nullptr;                             // per box: target-side columns
+    int64_t *tbase = nullptr;                     // per box: first t entry of its blocks
+    int64_t *ubase = nullptr;                     // per box: U element offset
+    int *Rv = nullptr, *ldv = nullptr;            // per box: source-side columns and row stride
+    int64_t *vbase = nullptr;                     // per box: V element offset
+    int64_t *vcol0 = nullptr;                     // per box: first global V column
+    int *cu = nullptr, *cv = nullptr;             // per block: column offset in target / source box
+    int64_t *tofs = nullptr;                      // per block: t offset (target-major)
+    int64_t *map_v = nullptr;                     // per global V column: t index
+    int *leaf_ld = nullptr;                       // per leaf: padded rows
+    int64_t *leaf_lp = nullptr;                   // per leaf: prefix of padded rows (nleaf + 1)
+    void *U = nullptr, *V = nullptr;
+    int64_t u_elems = 0, v_elems = 0, factor_entries = 0;
+
+    // matvec work lists and scratch
+    int ngtask = 0;                               // gather tasks
+    int4 *gtask = nullptr;                        // (box, row0, row1, out slot or -1)
+    int64_t *gtask_pbase = nullptr;               // per task: partial base (or -1 = direct)
+    int nsplit = 0;                               // boxes whose gather is split
+    int *split_box = nullptr;                     // global box index
+    int *split_task0 = nullptr, *split_ntask = nullptr;
+    int64_t *split_pbase = nullptr;
+    int64_t partial_elems = 0;
+    void *t = nullptr;                            // sum_rank entries
+    void *partial = nullptr;
+    void *xs = nullptr;                           // N (sorted x of one column)
+    // transpose product
+    int64_t *tp_base = nullptr;                   // per (leaf, level<L): partial base, [(l-1)*nleaf+z]
+    int64_t tpartial_elems = 0;
+    void *tpartial = nullptr;
+    int nsplit_T = 0;                             // boxes above the leaf level with R > 0
+    int *tsplit_box = nullptr, *tsplit_level = nullptr;
+
+    // host staging for h3d_matvec_host
+    void *hx = nullptr, *hy = nullptr;
+    int64_t host_cols = 0;
+
+    int64_t near_interactions = 0;
+    int64_t n_vertex = 0;
+    double build_ms = 0;
+    bool ok = false;
+
+    size_t elem() const { return prec == H3D_FP64 ? 8 : 4; }
+};
+
+// ----------------------------------------------------------------------------
+// device helpers
+
+// FP64 kernel entry with explicitly rounded operations, used by ACA: the same
+// sequence of IEEE operations as a plain C evaluation without contraction
+// (d2 = fma(dz,dz,fma(dy,dy,dx*dx)), correctly rounded sqrt and division).
+__device__ __forceinline__ double kernel_exact(int kind, double kappa, double ax, double ay, double az,
+                                               double bx, double by, double bz) {
+    double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by), dz = __dsub_rn(az, bz);
+    double d2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+    if (d2 == 0.0) return 0.0;
+    double r = __dsqrt_rn(d2);
+    switch (kind) {
+    case H3D_LAPLACE: return __ddiv_rn(H3D_INV4PI, r);
+    case H3D_YUKAWA: return __ddiv_rn(__dmul_rn(H3D_INV4PI, exp(__dmul_rn(-kappa, r))), r);
+    case H3D_INV_R4: return __ddiv_rn(1.0, __dmul_rn(d2, d2));
+    default: return __ddiv_rn(cos(r), r);
+    }
+}
+
+// Fast FP64 kernel from a squared distance (near field of FP64 products).
+__device__ __forceinline__ double kernel_fast(int kind, double kappa, double d2) {
+    if (d2 == 0.0) return 0.0;
+    double ir = rsqrt(d2);
+    switch (kind) {
+    case H3D_LAPLACE: return H3D_INV4PI * ir;
+    case H3D_YUKAWA: return H3D_INV4PI * exp(-kappa * d2 * ir) * ir;
+    case H3D_INV_R4: return (ir * ir) * (ir * ir);
+    default: return cos(d2 * ir) * ir;
+    }
+}
+
+// Fast FP32 kernel from a squared distance (near field of FP32 products).
+__device__ __forceinline__ float kernel_fast(int kind, float kappa, float d2) {
+    if (d2 == 0.0f) return 0.0f;
+    float ir = rsqrtf(d2);
+    switch (kind) {
+    case H3D_LAPLACE: return (float)H3D_INV4PI * ir;
+    case H3D_YUKAWA: return (float)H3D_INV4PI * __expf(-kappa * d2 * ir) * ir;
+    case H3D_INV_R4: return (ir * ir) * (ir * ir);
+    default: return __cosf(d2 * ir) * ir;
+    }
+}
+
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Coordinates of a box from its Morton prefix at `level` (x bit most significant).
+__host__ __device__ inline void box_coords(uint64_t key, int level, int &x, int &y, int &z) {
+    x = y = z = 0;
+    for (int b = 0; b < level; ++b) {
+        unsigned t = (unsigned)((key >> (3 * b)) & 7ull);
+        x |= ((t >> 2) & 1u) << b;
+        y |= ((t >> 1) & 1u) << b;
+        z |= (t & 1u) << b;
+    }
+}
+
+__host__ __device__ inline uint64_t box_key_of(int x, int y, int z, int level) {
+    uint64_t k = 0;
+    for (int b = 0; b < level; ++b)
+        k |= ((uint64_t)(((x >> b) & 1) << 2 | ((y >> b) & 1) << 1 | ((z >> b) & 1))) << (3 * b);
+    return k;
+}
+
+// ----------------------------------------------------------------------------
+// host-side building blocks (h3d_util.cu)
+int64_t scan_exclusive(const int *in, int64_t *out, int64_t n, cudaStream_t s, Arena &tmp);
+int64_t scan_exclusive(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s, Arena &tmp);
+void radix_sort_pairs(uint64_t *keys, int *vals, int64_t n, int key_bits, cudaStream_t s, Arena &tmp);
+template <class T>
+T read_scalar(const T *d, cudaStream_t s) {
+    T v;
+    H3D_CUDA(cudaMemcpyAsync(&v, d, sizeof(T), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaStreamSynchronize(s));
+    return v;
+}
+int num_sms();
+
+// build stages
+void build_tree(Handle &h, const double *points, cudaStream_t s, Arena &tmp);   // h3d_tree.cu
+void build_lists(Handle &h, cudaStream_t s, Arena &tmp);                         // h3d_tree.cu
+void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget);      // h3d_aca.cu
+void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp);                   // h3d_matvec.cu
+void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s);  // h3d_matvec.cu
+
+}  // namespace h3d

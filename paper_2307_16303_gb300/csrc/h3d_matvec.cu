@@ -1,0 +1,661 @@
+// h3d_matvec.cu -- the HODLR3D matrix-vector product (Alg. 2) and its
+// transpose on the GPU.
+//
+// Forward product y = A~ x, per right-hand side:
+//   A5  xs = x[perm]                                  (k_permute_in)
+//   A7  t_b = V_b^T xs(Y_b) for every block, grouped by source box Y: the
+//       source box's V (n_Y x ldv_Y row-major) is streamed once with 128-bit
+//       loads, threads over columns, rows split across tasks when Y is large
+//       (partials reduced by k_reduce_partials)      (k_gather)
+//   A6+A8+A9 one CTA per leaf Z: the dense self/face/edge near field with
+//       kernel entries recomputed from staged source points, plus, for every
+//       level, the panel of the ancestor's U restricted to Z's rows times the
+//       ancestor's t; the sum is written straight to y in the caller's order
+//                                                     (k_leaf)
+// Transposed product y = A~^T x (the factor roles exchanged):
+//   t'_b = U_b^T xs(X_b) per leaf panel, partials reduced per box
+//                                                     (k_leafT_gather, k_reduceT)
+//   per leaf: near field (K is symmetric, the near lists are symmetric) plus
+//   V rows of every ancestor source box times t'       (k_leafT)
+#include <algorithm>
+
+#include "h3d_internal.cuh"
+
+namespace h3d {
+
+namespace {
+
+constexpr int kGatherThreads = 256;
+constexpr int kLeafThreads = 128;
+constexpr int64_t kTaskElems = 1 << 18;   // factor entries streamed by one gather task
+constexpr int kTaskMaxRows = 2048;
+
+struct __align__(16) Pt4d {
+    double x, y, z, w;
+};
+__device__ __forceinline__ Pt4d make_pt4d(double x, double y, double z, double w) { return Pt4d{x, y, z, w}; }
+
+template <class T> struct Vec;
+template <> struct Vec<float> {
+    using type = float4;
+    static constexpr int W = 4;
+    __device__ static __forceinline__ void get(const float4 &v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+};
+template <> struct Vec<double> {
+    using type = double2;
+    static constexpr int W = 2;
+    __device__ static __forceinline__ void get(const double2 &v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
+};
+
+template <class T>
+__device__ __forceinline__ typename Vec<T>::type ld_stream(const T *p) {
+    return __ldcs(reinterpret_cast<const typename Vec<T>::type *>(p));
+}
+
+template <class T>
+__global__ void k_permute_in(const T *__restrict__ x, const int *__restrict__ perm, int64_t n, T *__restrict__ xs) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) xs[i] = x[perm[i]];
+}
+
+// ---------------------------------------------------------------------------
+// A7: T_Y = V_Y^T xs(Y) over rows [r0, r1) of Y
+struct GatherArgs {
+    const int4 *task;            // (box, row0, row1, direct?1:0)
+    const int64_t *pbase;        // partial base per task
+    const int *box_start, *Rv, *ldv;
+    const int64_t *vbase, *vcol0, *map_v;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs G, const T *__restrict__ V,
+                                                           const T *__restrict__ xs, T *__restrict__ t,
+                                                           T *__restrict__ partial) {
+    constexpr int W = Vec<T>::W;
+    __shared__ T xsm[kTaskMaxRows];
+    __shared__ T red[kGatherThreads * W];
+    const int4 task = G.task[blockIdx.x];
+    const int Y = task.x, r0 = task.y, r1 = task.z;
+    const int nrows = r1 - r0;
+    const int ld = G.ldv[Y], RvY = G.Rv[Y];
+    const int ncv = ld / W;
+    const T *Vb = V + G.vbase[Y] + (int64_t)r0 * ld;
+    const int ys = G.box_start[Y] + r0;
+    for (int r = threadIdx.x; r < nrows; r += kGatherThreads) xsm[r] = xs[ys + r];
+    __syncthreads();
+    const bool direct = task.w != 0;
+    const int64_t pb = G.pbase[blockIdx.x];
+    const int64_t vc0 = G.vcol0[Y];
+    if (ncv >= kGatherThreads) {
+        for (int cv = threadIdx.x; cv < ncv; cv += kGatherThreads) {
+            T acc[W];
+#pragma unroll
+            for (int e = 0; e < W; ++e) acc[e] = 0;
+            const T *p = Vb + cv * W;
+            int r = 0;
+            for (; r + 4 <= nrows; r += 4) {
+                typename Vec<T>::type v0 = ld_stream(p + (int64_t)r * ld), v1 = ld_stream(p + (int64_t)(r + 1) * ld),
+                                      v2 = ld_stream(p + (int64_t)(r + 2) * ld), v3 = ld_stream(p + (int64_t)(r + 3) * ld);
+                T a0[W], a1[W], a2[W], a3[W];
+                Vec<T>::get(v0, a0); Vec<T>::get(v1, a1); Vec<T>::get(v2, a2); Vec<T>::get(v3, a3);
+#pragma unroll
+                for (int e = 0; e < W; ++e)
+                    acc[e] += a0[e] * xsm[r] + a1[e] * xsm[r + 1] + a2[e] * xsm[r + 2] + a3[e] * xsm[r + 3];
+            }
+            for (; r < nrows; ++r) {
+                T a[W];
+                Vec<T>::get(ld_stream(p + (int64_t)r * ld), a);
+#pragma unroll
+                for (int e = 0; e < W; ++e) acc[e] += a[e] * xsm[r];
+            }
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                const int c = cv * W + e;
+                if (c < RvY) {
+                    if (direct) t[G.map_v[vc0 + c]] = acc[e];
+                    else partial[pb + c] = acc[e];
+                }
+            }
+        }
+        return;
+    }
+    // few columns: split the rows over G groups, reduce in shared memory
+    const int Gn = kGatherThreads / ncv;
+    const int g = threadIdx.x / ncv, cv = threadIdx.x - g * ncv;
+    T acc[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) acc[e] = 0;
+    if (g < Gn) {
+        const T *p = Vb + cv * W;
+        int r = g;
+        for (; r + 3 * Gn < nrows; r += 4 * Gn) {
+            typename Vec<T>::type v0 = ld_stream(p + (int64_t)r * ld), v1 = ld_stream(p + (int64_t)(r + Gn) * ld),
+                                  v2 = ld_stream(p + (int64_t)(r + 2 * Gn) * ld),
+                                  v3 = ld_stream(p + (int64_t)(r + 3 * Gn) * ld);
+            T a0[W], a1[W], a2[W], a3[W];
+            Vec<T>::get(v0, a0); Vec<T>::get(v1, a1); Vec<T>::get(v2, a2); Vec<T>::get(v3, a3);
+#pragma unroll
+            for (int e = 0; e < W; ++e)
+                acc[e] += a0[e] * xsm[r] + a1[e] * xsm[r + Gn] + a2[e] * xsm[r + 2 * Gn] + a3[e] * xsm[r + 3 * Gn];
+        }
+        for (; r < nrows; r += Gn) {
+            T a[W];
+            Vec<T>::get(ld_stream(p + (int64_t)r * ld), a);
+#pragma unroll
+            for (int e = 0; e < W; ++e) acc[e] += a[e] * xsm[r];
+        }
+#pragma unroll
+        for (int e = 0; e < W; ++e) red[g * ld + cv * W + e] = acc[e];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < RvY; c += kGatherThreads) {
+        T s = 0;
+        for (int q = 0; q < Gn; ++q) s += red[q * ld + c];
+        if (direct) t[G.map_v[vc0 + c]] = s;
+        else partial[pb + c] = s;
+    }
+}
+
+struct SplitArgs {
+    const int *box, *ntask;
+    const int64_t *pbase;
+    const int *Rv, *ldv;
+    const int64_t *vcol0, *map_v;
+};
+
+template <class T>
+__global__ void k_reduce_partials(SplitArgs S, const T *__restrict__ partial, T *__restrict__ t) {
+    const int q = blockIdx.x;
+    const int Y = S.box[q], nt = S.ntask[q], ld = S.ldv[Y], R = S.Rv[Y];
+    const int64_t pb = S.pbase[q], vc0 = S.vcol0[Y];
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        T s = 0;
+        for (int k = 0; k < nt; ++k) s += partial[pb + (int64_t)k * ld + c];
+        t[S.map_v[vc0 + c]] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// near field helpers: stage one source leaf, accumulate over it.
+struct LeafArgs {
+    int L, nleaf, kind;
+    double kappa, hL;
+    int64_t offL;
+    const int *box_start, *box_end, *perm, *leaf_ld, *leaf_anc, *R, *leaf_lo;
+    const int64_t *leaf_lp, *ubase, *tbase;
+    const int *near_ptr, *near_src;
+    const unsigned char *near_dir;
+    const float4 *ploc;
+    const double *px, *py, *pz;
+    // transpose
+    const int *Rv, *ldv;
+    const int64_t *vbase, *vcol0, *map_v, *tp_base;
+};
+
+// Near-field sum for targets of leaf z: out[i] = sum over near leaves of
+// K(i,j) xs_j (i in [0, m)).  Thread layout: S source groups x m targets.
+template <class T>
+__device__ void near_field(const LeafArgs &A, int z, int zs, int m, const T *__restrict__ xs, T *outsm,
+                           float4 *srcf, Pt4d *srcd, T *partsm);
+
+template <>
+__device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const float *__restrict__ xs, float *outsm,
+                                  float4 *srcf, Pt4d *, float *partsm) {
+    const int T_ = kLeafThreads;
+    const int S = m <= T_ ? max(1, T_ / m) : 1;
+    const int ntg = m <= T_ ? 1 : (m + T_ - 1) / T_;   // targets per thread when m > T
+    const int s = m <= T_ ? threadIdx.x / m : 0;
+    const int i0 = m <= T_ ? threadIdx.x - s * m : threadIdx.x;
+    const bool active = m <= T_ ? (s < S) : true;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float4 tl[4];
+    for (int q = 0; q < ntg && q < 4; ++q) {
+        const int i = i0 + q * T_;
+        tl[q] = (active && i < m) ? A.ploc[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float kap = (float)A.kappa;
+    for (int p = A.near_ptr[z]; p < A.near_ptr[z + 1]; ++p) {
+        const int y = A.near_src[p];
+        const int ys = A.box_start[A.offL + y], n = A.box_end[A.offL + y] - ys;
+        const int d = A.near_dir[p];
+        const float sx = (float)((d / 9 - 1) * A.hL), sy = (float)(((d / 3) % 3 - 1) * A.hL),
+                    sz = (float)((d % 3 - 1) * A.hL);
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += T_) {
+            const float4 q = A.ploc[ys + j];
+            srcf[j] = make_float4(q.x + sx, q.y + sy, q.z + sz, xs[ys + j]);
+        }
+        __syncthreads();
+        if (active) {
+            for (int q = 0; q < ntg && q < 4; ++q) {
+                const int i = i0 + q * T_;
+                if (i >= m) break;
+                float a = 0.f;
+                for (int j = s; j < n; j += S) {
+                    const float4 sp = srcf[j];
+                    const float dx = tl[q].x - sp.x, dy = tl[q].y - sp.y, dz = tl[q].z - sp.z;
+                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    a = fmaf(kernel_fast(A.kind, kap, d2), sp.w, a);
+                }
+                acc[q] += a;
+            }
+        }
+    }
+    // reduce over source groups
+    if (m <= T_) {
+        if (active) partsm[threadIdx.x] = acc[0];
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += T_) {
+            float v = 0.f;
+            for (int g = 0; g < S; ++g) v += partsm[g * m + i];
+            outsm[i] = v;
+        }
+    } else {
+        for (int q = 0; q < ntg && q < 4; ++q) {
+            const int i = i0 + q * T_;
+            if (i < m) outsm[i] = acc[q];
+        }
+    }
+    __syncthreads();
+}
+
+template <>
+__device__ void near_field<double>(const LeafArgs &A, int z, int zs, int m, const double *__restrict__ xs,
+                                   double *outsm, float4 *, Pt4d *srcd, double *partsm) {
+    const int T_ = kLeafThreads;
+    const int S = m <= T_ ? max(1, T_ / m) : 1;
+    const int ntg = m <= T_ ? 1 : (m + T_ - 1) / T_;
+    const int s = m <= T_ ? threadIdx.x / m : 0;
+    const int i0 = m <= T_ ? threadIdx.x - s * m : threadIdx.x;
+    const bool active = m <= T_ ? (s < S) : true;
+    double acc[4] = {0, 0, 0, 0};
+    double tx[4], ty[4], tz[4];
+    for (int q = 0; q < ntg && q < 4; ++q) {
+        const int i = i0 + q * T_;
+        const bool ok = active && i < m;
+        tx[q] = ok ? A.px[zs + i] : 0.0;
+        ty[q] = ok ? A.py[zs + i] : 0.0;
+        tz[q] = ok ? A.pz[zs + i] : 0.0;
+    }
+    for (int p = A.near_ptr[z]; p < A.near_ptr[z + 1]; ++p) {
+        const int y = A.near_src[p];
+        const int ys = A.box_start[A.offL + y], n = A.box_end[A.offL + y] - ys;
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += T_)
+            srcd[j] = make_pt4d(A.px[ys + j], A.py[ys + j], A.pz[ys + j], xs[ys + j]);
+        __syncthreads();
+        if (active) {
+            for (int q = 0; q < ntg && q < 4; ++q) {
+                const int i = i0 + q * T_;
+                if (i >= m) break;
+                double a = 0.0;
+                for (int j = s; j < n; j += S) {
+                    const Pt4d sp = srcd[j];
+                    const double dx = tx[q] - sp.x, dy = ty[q] - sp.y, dz = tz[q] - sp.z;
+                    const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                    a = fma(kernel_fast(A.kind, A.kappa, d2), sp.w, a);
+                }
+                acc[q] += a;
+            }
+        }
+    }
+    if (m <= T_) {
+        if (active) partsm[threadIdx.x] = acc[0];
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += T_) {
+            double v = 0.0;
+            for (int g = 0; g < S; ++g) v += partsm[g * m + i];
+            outsm[i] = v;
+        }
+    } else {
+        for (int q = 0; q < ntg && q < 4; ++q) {
+            const int i = i0 + q * T_;
+            if (i < m) outsm[i] = acc[q];
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// A6 + A8 + A9: one CTA per leaf
+template <class T>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__restrict__ U, const T *__restrict__ t,
+                                                       const T *__restrict__ xs, T *__restrict__ y) {
+    constexpr int W = Vec<T>::W;
+    __shared__ T outsm[kMaxLeaf];
+    __shared__ T nearsm[kMaxLeaf];
+    __shared__ T red[kLeafThreads * W];
+    __shared__ __align__(16) unsigned char srcbuf[kMaxLeaf * 32];
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+    const int ld = A.leaf_ld[z];
+    const int nr = ld / W;
+
+    // far field: rows in vectors of W, columns split over Gc groups
+    const int Gc = nr <= kLeafThreads ? kLeafThreads / nr : 1;
+    T acc[2][W];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < W; ++e) acc[h][e] = 0;
+    const int g = nr <= kLeafThreads ? threadIdx.x / nr : 0;
+    const int rv0 = nr <= kLeafThreads ? threadIdx.x - g * nr : threadIdx.x;
+    if (g < Gc) {
+        for (int l = 1; l <= A.L; ++l) {
+            const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
+            const int RA = A.R[Ag];
+            if (RA == 0) continue;
+            const T *panel = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
+            const T *tA = t + A.tbase[Ag];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int rv = rv0 + h * kLeafThreads;
+                if (rv >= nr) break;
+                const T *p = panel + rv * W;
+                int c = g;
+                for (; c + 3 * Gc < RA; c += 4 * Gc) {
+                    typename Vec<T>::type v0 = ld_stream(p + (int64_t)c * ld), v1 = ld_stream(p + (int64_t)(c + Gc) * ld),
+                                          v2 = ld_stream(p + (int64_t)(c + 2 * Gc) * ld),
+                                          v3 = ld_stream(p + (int64_t)(c + 3 * Gc) * ld);
+                    const T t0 = __ldg(tA + c), t1 = __ldg(tA + c + Gc), t2 = __ldg(tA + c + 2 * Gc),
+                            t3 = __ldg(tA + c + 3 * Gc);
+                    T a0[W], a1[W], a2[W], a3[W];
+                    Vec<T>::get(v0, a0); Vec<T>::get(v1, a1); Vec<T>::get(v2, a2); Vec<T>::get(v3, a3);
+#pragma unroll
+                    for (int e = 0; e < W; ++e) acc[h][e] += a0[e] * t0 + a1[e] * t1 + a2[e] * t2 + a3[e] * t3;
+                }
+                for (; c < RA; c += Gc) {
+                    T a[W];
+                    Vec<T>::get(ld_stream(p + (int64_t)c * ld), a);
+                    const T tc = __ldg(tA + c);
+#pragma unroll
+                    for (int e = 0; e < W; ++e) acc[h][e] += a[e] * tc;
+                }
+            }
+        }
+    }
+    // reduce over column groups into outsm (far part)
+    if (Gc > 1) {
+        if (g < Gc)
+#pragma unroll
+            for (int e = 0; e < W; ++e) red[g * ld + rv0 * W + e] = acc[0][e];
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += kLeafThreads) {
+            T v = 0;
+            for (int q = 0; q < Gc; ++q) v += red[q * ld + i];
+            outsm[i] = v;
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int rv = rv0 + h * kLeafThreads;
+            if (rv < nr)
+#pragma unroll
+                for (int e = 0; e < W; ++e)
+                    if (rv * W + e < m) outsm[rv * W + e] = acc[h][e];
+        }
+    }
+    __syncthreads();
+    // near field (red reused for the source-group partials), then y[perm] = near + far
+    near_field<T>(A, z, zs, m, xs, nearsm, reinterpret_cast<float4 *>(srcbuf), reinterpret_cast<Pt4d *>(srcbuf),
+                  red);
+    for (int i = threadIdx.x; i < m; i += kLeafThreads) y[A.perm[zs + i]] = outsm[i] + nearsm[i];
+}
+
+// ---------------------------------------------------------------------------
+// transpose: t'_A = U_A^T xs(A), per leaf panel
+template <class T>
+__global__ void __launch_bounds__(kLeafThreads) k_leafT_gather(LeafArgs A, const T *__restrict__ U,
+                                                               const T *__restrict__ xs, T *__restrict__ t,
+                                                               T *__restrict__ tpart) {
+    __shared__ T xsm[kMaxLeaf];
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+    const int ld = A.leaf_ld[z];
+    for (int i = threadIdx.x; i < m; i += kLeafThreads) xsm[i] = xs[zs + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kLeafThreads / 32;
+    for (int l = 1; l <= A.L; ++l) {
+        const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
+        const int RA = A.R[Ag];
+        if (RA == 0) continue;
+        const T *panel = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
+        T *out = (l == A.L) ? t + A.tbase[Ag] : tpart + A.tp_base[(int64_t)(l - 1) * A.nleaf + z];
+        for (int c = warp; c < RA; c += nw) {
+            const T *col = panel + (int64_t)c * ld;
+            T s = 0;
+            for (int i = lane; i < m; i += 32) s += __ldcs(col + i) * xsm[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) out[c] = s;
+        }
+    }
+}
+
+// sum the per-leaf partials of every box A above the leaf level
+struct ReduceTArgs {
+    const int *box;       // global box indices of levels 1..L-1 with R > 0
+    const int *level;
+    const int *R, *leaf_lo, *leaf_hi;
+    const int64_t *tbase, *tp_base;
+    int nleaf;
+};
+
+template <class T>
+__global__ void k_reduceT(ReduceTArgs S, const T *__restrict__ tpart, T *__restrict__ t) {
+    const int Ag = S.box[blockIdx.x];
+    const int l = S.level[blockIdx.x];
+    const int RA = S.R[Ag], z0 = S.leaf_lo[Ag], z1 = S.leaf_hi[Ag];
+    const int64_t base = S.tp_base[(int64_t)(l - 1) * S.nleaf + z0];
+    for (int c = threadIdx.x; c < RA; c += blockDim.x) {
+        T s = 0;
+        for (int z = z0; z < z1; ++z) s += tpart[base + (int64_t)(z - z0) * RA + c];
+        t[S.tbase[Ag] + c] = s;
+    }
+}
+
+// per leaf: near field + rows of every ancestor source box's V times t'
+template <class T>
+__global__ void __launch_bounds__(kLeafThreads) k_leafT(LeafArgs A, const T *__restrict__ V, const T *__restrict__ t,
+                                                        const T *__restrict__ xs, T *__restrict__ y) {
+    __shared__ T outsm[kMaxLeaf];
+    __shared__ T nearsm[kMaxLeaf];
+    __shared__ T tsm[2048];
+    __shared__ __align__(16) unsigned char srcbuf[kMaxLeaf * 32];
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+    for (int i = threadIdx.x; i < m; i += kLeafThreads) outsm[i] = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kLeafThreads / 32;
+    for (int l = 1; l <= A.L; ++l) {
+        const int Yg = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
+        const int RvY = A.Rv[Yg];
+        if (RvY == 0) continue;
+        const int ld = A.ldv[Yg];
+        const int64_t vc0 = A.vcol0[Yg];
+        const T *rows = V + A.vbase[Yg] + (int64_t)(zs - A.box_start[Yg]) * ld;
+        for (int c0 = 0; c0 < RvY; c0 += 2048) {
+            const int nc = min(2048, RvY - c0);
+            __syncthreads();
+            for (int c = threadIdx.x; c < nc; c += kLeafThreads) tsm[c] = t[A.map_v[vc0 + c0 + c]];
+            __syncthreads();
+            for (int i = warp; i < m; i += nw) {
+                const T *row = rows + (int64_t)i * ld + c0;
+                T s = 0;
+                for (int c = lane; c < nc; c += 32) s += __ldcs(row + c) * tsm[c];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) outsm[i] += s;
+            }
+        }
+    }
+    __syncthreads();
+    near_field<T>(A, z, zs, m, xs, nearsm, reinterpret_cast<float4 *>(srcbuf), reinterpret_cast<Pt4d *>(srcbuf),
+                  tsm);
+    for (int i = threadIdx.x; i < m; i += kLeafThreads) y[A.perm[zs + i]] = outsm[i] + nearsm[i];
+}
+
+unsigned gridn(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+LeafArgs leaf_args(const Handle &h) {
+    LeafArgs A{};
+    A.L = h.L; A.nleaf = h.nleaf; A.kind = h.kernel; A.kappa = h.kappa;
+    A.hL = h.side / (double)(1 << h.L);
+    A.offL = h.box_off[h.L];
+    A.box_start = h.box_start; A.box_end = h.box_end; A.perm = h.perm; A.leaf_ld = h.leaf_ld;
+    A.leaf_anc = h.leaf_anc; A.R = h.R; A.leaf_lo = h.box_leaf_lo;
+    A.leaf_lp = h.leaf_lp; A.ubase = h.ubase; A.tbase = h.tbase;
+    A.near_ptr = h.near_ptr; A.near_src = h.near_src; A.near_dir = h.near_dir;
+    A.ploc = h.ploc; A.px = h.px; A.py = h.py; A.pz = h.pz;
+    A.Rv = h.Rv; A.ldv = h.ldv; A.vbase = h.vbase; A.vcol0 = h.vcol0; A.map_v = h.map_v; A.tp_base = h.tp_base;
+    return A;
+}
+
+// transpose reduce work list (host-built)
+struct TPlan {
+    int n = 0;
+    int *box = nullptr, *level = nullptr;
+};
+
+template <class T>
+void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s) {
+    const int64_t n = h.N;
+    T *xs = (T *)h.xs, *t = (T *)h.t;
+    k_permute_in<T><<<gridn(n, 256), 256, 0, s>>>(x, h.perm, n, xs);
+    LeafArgs A = leaf_args(h);
+    if (!transpose) {
+        if (h.ngtask > 0) {
+            GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
+            k_gather<T><<<h.ngtask, kGatherThreads, 0, s>>>(G, (const T *)h.V, xs, t, (T *)h.partial);
+        }
+        if (h.nsplit > 0) {
+            SplitArgs S{h.split_box, h.split_ntask, h.split_pbase, h.Rv, h.ldv, h.vcol0, h.map_v};
+            k_reduce_partials<T><<<h.nsplit, 256, 0, s>>>(S, (const T *)h.partial, t);
+        }
+        k_leaf<T><<<h.nleaf, kLeafThreads, 0, s>>>(A, (const T *)h.U, t, xs, y);
+    } else {
+        if (h.nblk > 0) {
+            k_leafT_gather<T><<<h.nleaf, kLeafThreads, 0, s>>>(A, (const T *)h.U, xs, t, (T *)h.tpartial);
+            if (h.nsplit_T > 0) {
+                ReduceTArgs R{h.tsplit_box, h.tsplit_level, h.R, h.box_leaf_lo, h.box_leaf_hi, h.tbase, h.tp_base,
+                              h.nleaf};
+                k_reduceT<T><<<h.nsplit_T, 256, 0, s>>>(R, (const T *)h.tpartial, t);
+            }
+        }
+        k_leafT<T><<<h.nleaf, kLeafThreads, 0, s>>>(A, (const T *)h.V, t, xs, y);
+    }
+    H3D_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
+    (void)tmp;
+    const int64_t nboxes = h.n_boxes;
+    const size_t es = h.elem();
+    std::vector<int> Rv(nboxes), ldv(nboxes), bs(nboxes), be(nboxes), R(nboxes), llo(nboxes), lhi(nboxes);
+    H3D_CUDA(cudaMemcpyAsync(Rv.data(), h.Rv, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaMemcpyAsync(ldv.data(), h.ldv, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaMemcpyAsync(bs.data(), h.box_start, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaMemcpyAsync(be.data(), h.box_end, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaMemcpyAsync(R.data(), h.R, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaMemcpyAsync(llo.data(), h.box_leaf_lo, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaMemcpyAsync(lhi.data(), h.box_leaf_hi, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaStreamSynchronize(s));
+
+    // gather tasks: coarse levels first (they are the longest)
+    std::vector<int4> tasks;
+    std::vector<int64_t> pbase;
+    std::vector<int> sbox, stask0, sntask;
+    std::vector<int64_t> spbase;
+    int64_t pel = 0;
+    for (int64_t g = 0; g < nboxes; ++g) {
+        if (Rv[g] == 0) continue;
+        const int n = be[g] - bs[g];
+        int rows = (int)std::max<int64_t>(1, kTaskElems / std::max(1, ldv[g]));
+        rows = std::min(rows, kTaskMaxRows);
+        int nt = (n + rows - 1) / rows;
+        if (nt == 2 && n <= kTaskMaxRows && (int64_t)n * ldv[g] <= 2 * kTaskElems) nt = 1;
+        if (nt == 1) {
+            tasks.push_back(make_int4((int)g, 0, n, 1));
+            pbase.push_back(-1);
+        } else {
+            const int per = (n + nt - 1) / nt;
+            sbox.push_back((int)g);
+            stask0.push_back((int)tasks.size());
+            sntask.push_back(nt);
+            spbase.push_back(pel);
+            for (int k = 0; k < nt; ++k) {
+                tasks.push_back(make_int4((int)g, k * per, std::min(n, (k + 1) * per), 0));
+                pbase.push_back(pel + (int64_t)k * ldv[g]);
+            }
+            pel += (int64_t)nt * ldv[g];
+        }
+    }
+    h.ngtask = (int)tasks.size();
+    h.gtask = h.mem.get<int4>(std::max<size_t>(tasks.size(), 1));
+    h.gtask_pbase = h.mem.get<int64_t>(std::max<size_t>(pbase.size(), 1));
+    if (!tasks.empty()) {
+        H3D_CUDA(cudaMemcpyAsync(h.gtask, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.gtask_pbase, pbase.data(), pbase.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
+    h.nsplit = (int)sbox.size();
+    h.split_box = h.mem.get<int>(std::max<size_t>(sbox.size(), 1));
+    h.split_task0 = h.mem.get<int>(std::max<size_t>(sbox.size(), 1));
+    h.split_ntask = h.mem.get<int>(std::max<size_t>(sbox.size(), 1));
+    h.split_pbase = h.mem.get<int64_t>(std::max<size_t>(sbox.size(), 1));
+    if (!sbox.empty()) {
+        H3D_CUDA(cudaMemcpyAsync(h.split_box, sbox.data(), sbox.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.split_task0, stask0.data(), sbox.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.split_ntask, sntask.data(), sbox.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.split_pbase, spbase.data(), sbox.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
+    h.partial_elems = pel;
+    h.partial = h.mem.alloc((size_t)std::max<int64_t>(pel, 4) * es);
+    h.t = h.mem.alloc((size_t)std::max<int64_t>(h.sum_rank, 4) * es);
+    h.xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * es);
+
+    // transpose partials: per level l < L, per leaf z, R of its ancestor
+    const int L = h.L, nleaf = h.nleaf;
+    std::vector<int> anc((size_t)std::max(1, L) * nleaf);
+    if (L > 0)
+        H3D_CUDA(cudaMemcpyAsync(anc.data(), h.leaf_anc, anc.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> tpb((size_t)std::max(1, L) * nleaf, 0);
+    int64_t tel = 0;
+    std::vector<int> tsb, tsl;
+    for (int l = 1; l < L; ++l) {
+        for (int z = 0; z < nleaf; ++z) {
+            tpb[(size_t)(l - 1) * nleaf + z] = tel;
+            tel += R[anc[(size_t)(l - 1) * nleaf + z]];
+        }
+        for (int64_t g = h.box_off[l]; g < h.box_off[l + 1]; ++g)
+            if (R[g] > 0) { tsb.push_back((int)g); tsl.push_back(l); }
+    }
+    h.tp_base = h.mem.get<int64_t>(tpb.size());
+    H3D_CUDA(cudaMemcpyAsync(h.tp_base, tpb.data(), tpb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    h.tpartial_elems = tel;
+    h.tpartial = h.mem.alloc((size_t)std::max<int64_t>(tel, 4) * es);
+    h.nsplit_T = (int)tsb.size();
+    h.tsplit_box = h.mem.get<int>(std::max<size_t>(tsb.size(), 1));
+    h.tsplit_level = h.mem.get<int>(std::max<size_t>(tsb.size(), 1));
+    if (!tsb.empty()) {
+        H3D_CUDA(cudaMemcpyAsync(h.tsplit_box, tsb.data(), tsb.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.tsplit_level, tsl.data(), tsl.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    H3D_CUDA(cudaStreamSynchronize(s));
+}
+
+void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s) {
+    const int64_t n = h.N;
+    for (int c = 0; c < nrhs; ++c) {
+        if (h.prec == H3D_FP64)
+            matvec_one<double>(h, (const double *)x + (size_t)c * n, (double *)y + (size_t)c * n, transpose, s);
+        else
+            matvec_one<float>(h, (const float *)x + (size_t)c * n, (float *)y + (size_t)c * n, transpose, s);
+    }
+}
+
+}  // namespace h3d
