@@ -1,0 +1,317 @@
+"""Benchmark: HODLR3D matrix-vector product time at N = 1,000,000 (uniform points
+in [-1,1]^3, Laplace 1/(4 pi r), leaf 128, ACA tolerance 1e-7, one RHS), FP32
+factors, with the plain FP64 form timed beside it.
+
+One step = one product y = A~ x through the C ABI (permutation, source-side
+gather V^T x, per-leaf near field + U t, inverse permutation) with x already in
+HBM.  The factors (~tens of GB) are far larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With --impl reference the CPU oracle's dense
+direct sum (O1) is timed on a bounded sample of rows on the host cores and
+scaled to a full product.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2307_16303_gb300 import inputs as I  # noqa: E402
+
+METRIC = "HODLR3D matvec ms @N=1M rel.err<=1e-6 (FP32 factors; plain FP64 beside it), %HBM peak"
+FALLBACK_HBM_GBS = 6800.0
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# of the unchanged kernel on this workload (None when not captured).
+NCU_TRAFFIC_BYTES: dict = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--N", type=int, default=1_000_000)
+    p.add_argument("--leaf", type=int, default=128)
+    p.add_argument("--tol", type=float, default=1e-7)
+    p.add_argument("--nrhs", type=int, default=1)
+    p.add_argument("--seed", type=int, default=3)
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    p.add_argument("--rows", type=int, default=10_000, help="sampled rows for the error / CPU baseline")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the baseline leg")
+    return p.parse_args()
+
+
+def workload(a):
+    return {"workload": f"uniform N={a.N} in [-1,1]^3, Laplace 1/(4 pi r), leaf {a.leaf}, tol {a.tol:g}, "
+                        f"nrhs {a.nrhs}, seed {a.seed}",
+            "N": a.N, "leaf_size": a.leaf, "tol": a.tol, "nrhs": a.nrhs, "kernel": "laplace",
+            "points": "uniform", "x": "N(0,1) fp32, seed 2", "l2": "inputs larger than L2 (factors >> 129 MB)"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """Sample nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 3 + k and r[3 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def time_steps(fn, steps, warmup, torch, dist=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    return e0.elapsed_time(e1) / steps
+
+
+def cpu_baseline(pts, x64, y_ours, a, budget_s):
+    """O1 on sampled rows: timed (scaled to a full product) and used for the error."""
+    from oracle import oracle as O
+    rows = I.sample_rows(a.N, a.rows, 4)
+    # size the sample to the CPU budget with a short probe
+    probe = rows[:64]
+    t0 = time.perf_counter()
+    O.direct_rows(pts, x64, probe)
+    tp = time.perf_counter() - t0
+    per_row = tp / len(probe)
+    S = int(min(len(rows), max(256, budget_s / max(per_row, 1e-9))))
+    rows = rows[:S]
+    t0 = time.perf_counter()
+    ref = O.direct_rows(pts, x64, rows)
+    t = time.perf_counter() - t0
+    ref = ref if ref.ndim == 2 else ref[:, None]
+    yr = y_ours[rows] if y_ours.ndim == 2 else y_ours[rows][:, None]
+    err = float(np.linalg.norm(yr - ref) / np.linalg.norm(ref))
+    full_ms = t * 1e3 * a.N / S
+    return {"value": round(full_ms, 3), "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"O1 FP64 direct sum on {S} seeded rows of the N={a.N} workload "
+                      f"({t:.1f} s), scaled by N/rows to one full dense product"}, err, S
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    pts = I.uniform(a.N, a.seed)
+    x = I.rhs_normal(a.N, a.nrhs, 2).astype(np.float32).astype(np.float64)
+    per_step_rows = 128
+    rng_rows = I.sample_rows(a.N, per_step_rows * (a.steps + a.warmup), 5)
+    times = []
+    for s in range(a.warmup + a.steps):
+        rows = rng_rows[s * per_step_rows:(s + 1) * per_step_rows]
+        t0 = time.perf_counter()
+        O.direct_rows(pts, x, rows)
+        dt = time.perf_counter() - t0
+        if s >= a.warmup:
+            times.append(dt * 1e3 * a.N / per_step_rows)
+    v = float(np.mean(times))
+    out = {"metric": METRIC, "value": round(v, 3), "unit": "ms", "n_gpus": a.gpus, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": round(v, 3), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload(a), "impl": "reference",
+           "cpu_baseline": {"value": round(v, 3), "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+                            "sample": f"O1 FP64 direct sum on {per_step_rows} seeded rows per step, "
+                                      f"scaled by N/rows to one full dense product"},
+           "e2e": {"value": round(v, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        dist = td
+    torch.cuda.set_device(local)
+    from paper_2307_16303_gb300.api import H3DMatrix, H3DError
+
+    # independent replica per rank (the product does not need a collective)
+    pts = I.uniform(a.N, a.seed + 1000 * rank)
+    xh = I.rhs_normal(a.N, a.nrhs, 2 + 1000 * rank).astype(np.float32)
+    dev_pts = torch.from_numpy(pts).cuda()
+    A = H3DMatrix(dev_pts, leaf_size=a.leaf, tol=a.tol, precision="fp32")
+    st = A.stats()
+    x = torch.from_numpy(np.ascontiguousarray(xh.T)).cuda()      # column-major N x nrhs
+    y = torch.empty_like(x)
+    nrhs = a.nrhs
+
+    def step():
+        A.matvec_raw(x.data_ptr(), y.data_ptr(), nrhs)
+
+    with Clocks(local) as clk:
+        ms = time_steps(step, a.steps, a.warmup, torch, dist)
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+
+    # per-kernel durations (CUDA events on the launching stream) over K more products
+    phases = np.zeros(4)
+    for _ in range(a.steps):
+        phases += np.array(A.matvec_profile(x.data_ptr(), y.data_ptr(), nrhs))
+    phases /= a.steps
+    names = ["k_permute_in", "k_gather", "k_reduce_partials", "k_leaf"]
+    s = 4
+    N = a.N
+    # algorithmic bytes per launch (one RHS): factor entries once, x / t / y once,
+    # FP32 local coordinates (16 B) and the permutation (4 B) per point
+    alg_bytes = {
+        "k_gather": s * st["v_entries"] + s * N + s * st["sum_rank"],
+        "k_leaf": s * st["u_entries"] + s * st["sum_rank"] + (2 * s + 16 + 4) * N,
+    }
+    dom = max(("k_gather", "k_leaf"), key=lambda k: phases[names.index(k)])
+    dom_ms = phases[names.index(dom)] / nrhs
+    peak, peak_kind = peaks()
+    achieved = alg_bytes[dom] / (dom_ms * 1e-3) / 1e9
+    total_bytes = s * (st["u_entries"] + st["v_entries"]) + (4 * s * nrhs + 20) * N
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "traffic": NCU_TRAFFIC_BYTES.get(dom), "alg_bytes_per_launch": int(alg_bytes[dom]),
+            "launch_ms": round(dom_ms, 4)}
+    phase_ms = {n: round(v / nrhs, 4) for n, v in zip(names, phases)}
+
+    # end to end through the host entry point (pinned buffers, copies inside)
+    xp = torch.from_numpy(np.asfortranarray(xh)).pin_memory() if nrhs > 1 else torch.from_numpy(xh[:, 0].copy()).pin_memory()
+    yp = torch.empty_like(xp).pin_memory()
+    def e2e_step():
+        A.matvec_host_ptr(xp.data_ptr(), yp.data_ptr(), nrhs)
+    for _ in range(max(3, a.warmup)):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / a.steps
+
+    y_host = y.cpu().numpy().T          # N x nrhs
+    if nrhs == 1:
+        y_host = y_host.reshape(-1)
+    A.free()
+    del A
+    torch.cuda.empty_cache()
+
+    fp64 = None
+    if not a.no_fp64:
+        try:
+            A64 = H3DMatrix(dev_pts, leaf_size=a.leaf, tol=a.tol, precision="fp64")
+            x64 = x.double()
+            y64 = torch.empty_like(x64)
+            f64 = time_steps(lambda: A64.matvec_raw(x64.data_ptr(), y64.data_ptr(), nrhs), a.steps, a.warmup,
+                             torch, None)
+            fp64 = {"ms": round(f64, 4), "build_ms": round(A64.stats()["build_ms"], 1),
+                    "factor_bytes": A64.stats()["factor_bytes"]}
+            A64.free()
+        except H3DError as e:
+            fp64 = {"ms": None, "error": str(e)}
+
+    out_cpu, err = None, None
+    if rank == 0:
+        out_cpu, err, nrows = cpu_baseline(pts, xh.astype(np.float64), y_host.astype(np.float64), a, a.cpu_seconds)
+
+    launches = st.get("launches_per_rhs", 4) * nrhs * a.steps
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    clk_s = clk.summary()
+    out = {
+        "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload(a),
+        "rel_err_sampled_rows": err, "fp64": fp64,
+        "speedup_vs_fp64": (round(fp64["ms"] / ms, 3) if fp64 and fp64.get("ms") else None),
+        "interactions_per_s": N * N * nrhs / (ms * 1e-3),
+        "matvec_alg_GBps": round(total_bytes / (ms * 1e-3) / 1e9, 1),
+        "roofline": roof, "phase_ms": phase_ms,
+        "cpu_baseline": out_cpu,
+        "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": 4 * N * nrhs,
+                "d2h_bytes_per_step": 4 * N * nrhs},
+        "gpu_launches": int(launches),
+        "clocks": clk_s,
+        "build": {"build_ms": round(st["build_ms"], 1), "depth": st["depth"], "n_blocks": st["n_blocks"],
+                  "max_rank": st["max_rank"], "factor_entries": st["factor_entries"],
+                  "factor_bytes": st["factor_bytes"], "device_bytes": st["device_bytes"],
+                  "near_interactions": st["near_interactions"]},
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -134,6 +134,8 @@ typedef struct {
     int max_rank;
     int64_t sum_rank;
     int64_t factor_entries;    /* sum over blocks of r (m + n)                      */
+    int64_t u_entries;         /* sum over blocks of r m (target-side factors)      */
+    int64_t v_entries;         /* sum over blocks of r n (source-side factors)      */
     int64_t factor_bytes;      /* stored factor bytes including padding             */
     int64_t near_interactions; /* sum over near pairs of m * n                      */
     int64_t device_bytes;      /* all device memory held by the handle              */
@@ -141,6 +143,15 @@ typedef struct {
 } h3d_stats;
 
 h3d_status h3d_get_stats(h3d_handle h, h3d_stats *s);
+
+/* h3d_matvec with per-phase timing, for profiling: the same kernels on `stream`,
+ * bracketed by CUDA events; synchronises the stream and writes the summed
+ * durations in milliseconds over all right-hand sides to phase_ms[0..nphase):
+ *   0 permutation of x, 1 source-side gather V^T x, 2 reduction of split
+ *   gathers, 3 per-leaf kernel (near field + target-side U t + permutation of y).
+ * phase_ms: host, nphase >= 1 (at most 4 entries are written).              */
+h3d_status h3d_matvec_profile(h3d_handle h, const void *x, void *y, int nrhs, void *stream,
+                              float *phase_ms, int nphase);
 
 /* Diagnostics (host outputs; sizes from h3d_get_stats; used by the tests).
  * Tree: perm[s] = original index of the s-th point in Morton order; keys[s] its

@@ -21,7 +21,8 @@ STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_
 
 # every entry point declared in include/h3d.h
 EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3d_matvec_host", "h3d_free",
-           "h3d_status_string", "h3d_get_stats", "h3d_export_tree", "h3d_export_lists", "h3d_export_pivots")
+           "h3d_status_string", "h3d_get_stats", "h3d_matvec_profile", "h3d_export_tree", "h3d_export_lists",
+           "h3d_export_pivots")
 
 
 class H3DError(RuntimeError):
@@ -41,6 +42,7 @@ class Stats(C.Structure):
                 ("leaf_size", C.c_int), ("tol", C.c_double), ("n_boxes", C.c_int64), ("n_leaves", C.c_int64),
                 ("n_blocks", C.c_int64), ("n_vertex_blocks", C.c_int64), ("n_near", C.c_int64),
                 ("max_rank", C.c_int), ("sum_rank", C.c_int64), ("factor_entries", C.c_int64),
+                ("u_entries", C.c_int64), ("v_entries", C.c_int64),
                 ("factor_bytes", C.c_int64), ("near_interactions", C.c_int64), ("device_bytes", C.c_int64),
                 ("build_ms", C.c_double)]
 
@@ -68,6 +70,7 @@ def lib():
             "h3d_free": (i32, [P]),
             "h3d_status_string": (C.c_char_p, [i32]),
             "h3d_get_stats": (i32, [P, C.POINTER(Stats)]),
+            "h3d_matvec_profile": (i32, [P, P, P, i32, P, C.POINTER(C.c_float), i32]),
             "h3d_export_tree": (i32, [P, P, P, P, P, P, P]),
             "h3d_export_lists": (i32, [P, P, P, P, P, P, P, P]),
             "h3d_export_pivots": (i32, [P, P, P, P]),
@@ -164,6 +167,14 @@ class H3DMatrix:
         st = fn(self._h, x_ptr, y_ptr, nrhs, _stream_ptr(stream))
         if st != 0:
             raise H3DError(st, "h3d_matvec")
+
+    def matvec_profile(self, x_ptr: int, y_ptr: int, nrhs: int, stream=None) -> list[float]:
+        """One product with per-phase CUDA-event timing (ms): permute, gather, reduce, leaf."""
+        ms = (C.c_float * 4)()
+        st = lib().h3d_matvec_profile(self._h, x_ptr, y_ptr, nrhs, _stream_ptr(stream), ms, 4)
+        if st != 0:
+            raise H3DError(st, "h3d_matvec_profile")
+        return list(ms)
 
     def matvec_host(self, x: np.ndarray, y: np.ndarray | None = None, stream=None) -> np.ndarray:
         """y = A~ x with host arrays (x: (N,) or column-major (N, nrhs))."""

@@ -542,9 +542,12 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget) {
         k_map_v<<<gridn(nblk), kThreads, 0, s>>>(h.blk_src, h.rank, h.cv, h.vcol0, h.tofs, nblk, h.map_v);
         H3D_LAUNCH_CHECK();
     }
-    h.factor_entries = 0;
-    for (int64_t b = 0; b < nblk; ++b)
-        h.factor_entries += (int64_t)rk[b] * ((bend[tgt[b]] - bstart[tgt[b]]) + (bend[src[b]] - bstart[src[b]]));
+    h.u_entries = h.v_entries = 0;
+    for (int64_t b = 0; b < nblk; ++b) {
+        h.u_entries += (int64_t)rk[b] * (bend[tgt[b]] - bstart[tgt[b]]);
+        h.v_entries += (int64_t)rk[b] * (bend[src[b]] - bstart[src[b]]);
+    }
+    h.factor_entries = h.u_entries + h.v_entries;
     tmp.free_one(scratch);
     tmp.free_one(flags);
 

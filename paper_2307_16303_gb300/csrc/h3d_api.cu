@@ -159,6 +159,32 @@ h3d_status h3d_matvec_host(h3d_handle hh, const void *x_host, void *y_host, int 
     });
 }
 
+h3d_status h3d_matvec_profile(h3d_handle hh, const void *x, void *y, int nrhs, void *stream, float *phase_ms,
+                              int nphase) {
+    if (!hh || !phase_ms || nphase < 1) return H3D_ERR_ARG;
+    Handle &h = hh->h;
+    if (!h.ok) return H3D_ERR_STATE;
+    if (!x || !y || nrhs < 1 || x == y) return H3D_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    std::vector<cudaEvent_t> ev((size_t)5 * nrhs, nullptr);
+    h3d_status st = guard([&] {
+        for (auto &e : ev) H3D_CUDA(cudaEventCreate(&e));
+        h3d::run_matvec(h, x, y, nrhs, false, s, ev.data());
+        H3D_CUDA(cudaStreamSynchronize(s));
+        float acc[4] = {0, 0, 0, 0};
+        for (int c = 0; c < nrhs; ++c)
+            for (int p = 0; p < 4; ++p) {
+                float ms = 0;
+                H3D_CUDA(cudaEventElapsedTime(&ms, ev[5 * c + p], ev[5 * c + p + 1]));
+                acc[p] += ms;
+            }
+        for (int p = 0; p < nphase && p < 4; ++p) phase_ms[p] = acc[p];
+    });
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    return st;
+}
+
 h3d_status h3d_free(h3d_handle hh) {
     if (!hh) return H3D_OK;
     cudaDeviceSynchronize();
@@ -184,6 +210,8 @@ h3d_status h3d_get_stats(h3d_handle hh, h3d_stats *st) {
     st->max_rank = h.max_rank;
     st->sum_rank = h.sum_rank;
     st->factor_entries = h.factor_entries;
+    st->u_entries = h.u_entries;
+    st->v_entries = h.v_entries;
     st->factor_bytes = (h.u_elems + h.v_elems) * (int64_t)h.elem();
     st->near_interactions = h.near_interactions;
     st->device_bytes = (int64_t)h.mem.total();

@@ -163,7 +163,7 @@ struct Handle {
     int *leaf_ld = nullptr;                       // per leaf: padded rows
     int64_t *leaf_lp = nullptr;                   // per leaf: prefix of padded rows (nleaf + 1)
     void *U = nullptr, *V = nullptr;
-    int64_t u_elems = 0, v_elems = 0, factor_entries = 0;
+    int64_t u_elems = 0, v_elems = 0, factor_entries = 0, u_entries = 0, v_entries = 0;
 
     // matvec work lists and scratch
     int ngtask = 0;                               // gather tasks
@@ -280,6 +280,7 @@ void build_tree(Handle &h, const double *points, cudaStream_t s, Arena &tmp);   
 void build_lists(Handle &h, cudaStream_t s, Arena &tmp);                         // h3d_tree.cu
 void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget);      // h3d_aca.cu
 void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp);                   // h3d_matvec.cu
-void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s);  // h3d_matvec.cu
+void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s,
+                cudaEvent_t *ev = nullptr);  // h3d_matvec.cu; ev: 5 events per rhs
 
 }  // namespace h3d

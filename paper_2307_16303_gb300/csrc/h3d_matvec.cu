@@ -520,21 +520,26 @@ struct TPlan {
 };
 
 template <class T>
-void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s) {
+void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s, cudaEvent_t *ev) {
     const int64_t n = h.N;
     T *xs = (T *)h.xs, *t = (T *)h.t;
+    if (ev) H3D_CUDA(cudaEventRecord(ev[0], s));
     k_permute_in<T><<<gridn(n, 256), 256, 0, s>>>(x, h.perm, n, xs);
+    if (ev) H3D_CUDA(cudaEventRecord(ev[1], s));
     LeafArgs A = leaf_args(h);
     if (!transpose) {
         if (h.ngtask > 0) {
             GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
             k_gather<T><<<h.ngtask, kGatherThreads, 0, s>>>(G, (const T *)h.V, xs, t, (T *)h.partial);
         }
+        if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
         if (h.nsplit > 0) {
             SplitArgs S{h.split_box, h.split_ntask, h.split_pbase, h.Rv, h.ldv, h.vcol0, h.map_v};
             k_reduce_partials<T><<<h.nsplit, 256, 0, s>>>(S, (const T *)h.partial, t);
         }
+        if (ev) H3D_CUDA(cudaEventRecord(ev[3], s));
         k_leaf<T><<<h.nleaf, kLeafThreads, 0, s>>>(A, (const T *)h.U, t, xs, y);
+        if (ev) H3D_CUDA(cudaEventRecord(ev[4], s));
     } else {
         if (h.nblk > 0) {
             k_leafT_gather<T><<<h.nleaf, kLeafThreads, 0, s>>>(A, (const T *)h.U, xs, t, (T *)h.tpartial);
@@ -648,13 +653,14 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     H3D_CUDA(cudaStreamSynchronize(s));
 }
 
-void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s) {
+void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s, cudaEvent_t *ev) {
     const int64_t n = h.N;
     for (int c = 0; c < nrhs; ++c) {
+        cudaEvent_t *e = ev ? ev + 5 * c : nullptr;
         if (h.prec == H3D_FP64)
-            matvec_one<double>(h, (const double *)x + (size_t)c * n, (double *)y + (size_t)c * n, transpose, s);
+            matvec_one<double>(h, (const double *)x + (size_t)c * n, (double *)y + (size_t)c * n, transpose, s, e);
         else
-            matvec_one<float>(h, (const float *)x + (size_t)c * n, (float *)y + (size_t)c * n, transpose, s);
+            matvec_one<float>(h, (const float *)x + (size_t)c * n, (float *)y + (size_t)c * n, transpose, s, e);
     }
 }
 
