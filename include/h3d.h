@@ -171,6 +171,31 @@ h3d_status h3d_export_lists(h3d_handle h, int *blk_level, int *blk_tgt, int *blk
  * row indices local to the target box, tau column indices local to the source. */
 h3d_status h3d_export_pivots(h3d_handle h, int *rank, int *sigma, int *tau);
 
+/* ---- Morton order without allocation (the paper has no counterpart) --------
+ * For callers that cannot allocate device memory (a host application that owns
+ * a fixed memory pool, a plugin that only receives pre-allocated buffers): the
+ * Morton keys and the stable Morton order of N points -- what the first two
+ * steps of h3d_build compute -- using only a fixed scratch area of
+ * H3D_NOALLOC_SCRATCH_BYTES that is a static device array inside the library.
+ * The call itself allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library routine).
+ *   points    device, N x 3 row-major FP64 (read only).
+ *   N         1 <= N <= H3D_NOALLOC_MAX_POINTS; larger N is rejected with
+ *             H3D_ERR_ARG (the scratch area has a fixed size).
+ *   lo, side  host; the domain cube [lo, lo + side]^3 (lo: 3 doubles).
+ *   keys_out  device, N uint64: the sorted 63-bit keys.
+ *   perm_out  device, N int32: perm_out[s] = original index of the s-th point.
+ *   stream    stream for all work; synchronised before return (to report a
+ *             point outside the cube as H3D_ERR_DOMAIN).
+ * The scratch array is held by every GPU that loads the library until the
+ * process exits and is shared by all calls: calls that overlap on the GPU race
+ * and must be serialised by the caller.  The first call on a device resolves
+ * the array's device address; make that first call before any stream capture. */
+#define H3D_NOALLOC_MAX_POINTS (1 << 20)
+#define H3D_NOALLOC_SCRATCH_BYTES (14 << 20)
+h3d_status h3d_morton_order_noalloc(const double *points, int64_t N, const double *lo, double side,
+                                    uint64_t *keys_out, int *perm_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

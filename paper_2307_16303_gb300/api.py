@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_
 # every entry point declared in include/h3d.h
 EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3d_matvec_host", "h3d_free",
            "h3d_status_string", "h3d_get_stats", "h3d_matvec_profile", "h3d_export_tree", "h3d_export_lists",
-           "h3d_export_pivots")
+           "h3d_export_pivots", "h3d_morton_order_noalloc")
 
 
 class H3DError(RuntimeError):
@@ -74,6 +74,7 @@ def lib():
             "h3d_export_tree": (i32, [P, P, P, P, P, P, P]),
             "h3d_export_lists": (i32, [P, P, P, P, P, P, P, P]),
             "h3d_export_pivots": (i32, [P, P, P, P]),
+            "h3d_morton_order_noalloc": (i32, [P, i64, P, f64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
