@@ -153,7 +153,7 @@ def cpu_baseline(pts, x64, y_ours, a, budget_s):
     full_ms = t * 1e3 * a.N / S
     return {"value": round(full_ms, 3), "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
             "sample": f"O1 FP64 direct sum on {S} seeded rows of the N={a.N} workload "
-                      f"({t:.1f} s), scaled by N/rows to one full dense product"}, err, S
+                      f"({t:.1f} s), scaled by N/rows to one full dense product"}, err, S, (rows, ref)
 
 
 def run_reference(a):
@@ -266,6 +266,7 @@ def main():
     torch.cuda.empty_cache()
 
     fp64 = None
+    y64_host = None
     if not a.no_fp64:
         try:
             A64 = H3DMatrix(dev_pts, leaf_size=a.leaf, tol=a.tol, precision="fp64")
@@ -275,13 +276,20 @@ def main():
                              torch, None)
             fp64 = {"ms": round(f64, 4), "build_ms": round(A64.stats()["build_ms"], 1),
                     "factor_bytes": A64.stats()["factor_bytes"]}
+            y64_host = y64.cpu().numpy().T
+            if nrhs == 1:
+                y64_host = y64_host.reshape(-1)
             A64.free()
         except H3DError as e:
             fp64 = {"ms": None, "error": str(e)}
 
     out_cpu, err = None, None
     if rank == 0:
-        out_cpu, err, nrows = cpu_baseline(pts, xh.astype(np.float64), y_host.astype(np.float64), a, a.cpu_seconds)
+        out_cpu, err, nrows, ref_rows = cpu_baseline(pts, xh.astype(np.float64), y_host.astype(np.float64), a,
+                                                     a.cpu_seconds)
+        if fp64 is not None and fp64.get("ms") is not None:
+            yr = y64_host[ref_rows[0]] if y64_host.ndim == 2 else y64_host[ref_rows[0]][:, None]
+            fp64["rel_err_sampled_rows"] = float(np.linalg.norm(yr - ref_rows[1]) / np.linalg.norm(ref_rows[1]))
 
     launches = st.get("launches_per_rhs", 4) * nrhs * a.steps
     if rank != 0:

@@ -1,8 +1,9 @@
 // h3d_internal.cuh -- shared declarations of the CUDA HODLR3D library.
 //
 // Data layout in HBM (all indices refer to points in Morton order):
-//   points     px/py/pz: FP64 SoA, sorted; ploc: float4 per point, FP32 offset
-//              from the centre of its leaf box (near field in FP32).
+//   points     px/py/pz: FP64 SoA, sorted; ploc / ploc_lo: float4 per point,
+//              the offset from the centre of its leaf box as hi + lo FP32
+//              (near field in FP32).
 //   boxes      all non-empty boxes of all levels, level-major, Morton order
 //              inside a level; index g is "global", g - box_off[l] "level-local".
 //   blocks     admissible pairs (target X, source Y) of every level in
@@ -113,7 +114,7 @@ struct Handle {
 
     // points
     double *px = nullptr, *py = nullptr, *pz = nullptr;
-    float4 *ploc = nullptr;
+    float4 *ploc = nullptr, *ploc_lo = nullptr;
     int *perm = nullptr;         // sorted position -> original index
     uint64_t *keys = nullptr;    // sorted keys
 

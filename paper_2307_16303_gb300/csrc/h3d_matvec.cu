@@ -35,6 +35,26 @@ struct __align__(16) Pt4d {
 };
 __device__ __forceinline__ Pt4d make_pt4d(double x, double y, double z, double w) { return Pt4d{x, y, z, w}; }
 
+// Sum accumulator.  FP32 sums of hundreds of random-sign products lose about
+// u*sqrt(n/2) relative accuracy when added in sequence, so FP32 uses a
+// compensated (Kahan) sum; FP64 adds plainly.
+template <class T> struct Acc;
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float get() const { return s - c; }
+};
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
 template <class T> struct Vec;
 template <> struct Vec<float> {
     using type = float4;
@@ -88,9 +108,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs G, const T
     const int64_t vc0 = G.vcol0[Y];
     if (ncv >= kGatherThreads) {
         for (int cv = threadIdx.x; cv < ncv; cv += kGatherThreads) {
-            T acc[W];
-#pragma unroll
-            for (int e = 0; e < W; ++e) acc[e] = 0;
+            Acc<T> acc[W];
             const T *p = Vb + cv * W;
             int r = 0;
             for (; r + 4 <= nrows; r += 4) {
@@ -100,20 +118,20 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs G, const T
                 Vec<T>::get(v0, a0); Vec<T>::get(v1, a1); Vec<T>::get(v2, a2); Vec<T>::get(v3, a3);
 #pragma unroll
                 for (int e = 0; e < W; ++e)
-                    acc[e] += a0[e] * xsm[r] + a1[e] * xsm[r + 1] + a2[e] * xsm[r + 2] + a3[e] * xsm[r + 3];
+                    acc[e].add(a0[e] * xsm[r] + a1[e] * xsm[r + 1] + a2[e] * xsm[r + 2] + a3[e] * xsm[r + 3]);
             }
             for (; r < nrows; ++r) {
                 T a[W];
                 Vec<T>::get(ld_stream(p + (int64_t)r * ld), a);
 #pragma unroll
-                for (int e = 0; e < W; ++e) acc[e] += a[e] * xsm[r];
+                for (int e = 0; e < W; ++e) acc[e].add(a[e] * xsm[r]);
             }
 #pragma unroll
             for (int e = 0; e < W; ++e) {
                 const int c = cv * W + e;
                 if (c < RvY) {
-                    if (direct) t[G.map_v[vc0 + c]] = acc[e];
-                    else partial[pb + c] = acc[e];
+                    if (direct) t[G.map_v[vc0 + c]] = acc[e].get();
+                    else partial[pb + c] = acc[e].get();
                 }
             }
         }
@@ -122,9 +140,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs G, const T
     // few columns: split the rows over G groups, reduce in shared memory
     const int Gn = kGatherThreads / ncv;
     const int g = threadIdx.x / ncv, cv = threadIdx.x - g * ncv;
-    T acc[W];
-#pragma unroll
-    for (int e = 0; e < W; ++e) acc[e] = 0;
+    Acc<T> acc[W];
     if (g < Gn) {
         const T *p = Vb + cv * W;
         int r = g;
@@ -136,16 +152,16 @@ __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs G, const T
             Vec<T>::get(v0, a0); Vec<T>::get(v1, a1); Vec<T>::get(v2, a2); Vec<T>::get(v3, a3);
 #pragma unroll
             for (int e = 0; e < W; ++e)
-                acc[e] += a0[e] * xsm[r] + a1[e] * xsm[r + Gn] + a2[e] * xsm[r + 2 * Gn] + a3[e] * xsm[r + 3 * Gn];
+                acc[e].add(a0[e] * xsm[r] + a1[e] * xsm[r + Gn] + a2[e] * xsm[r + 2 * Gn] + a3[e] * xsm[r + 3 * Gn]);
         }
         for (; r < nrows; r += Gn) {
             T a[W];
             Vec<T>::get(ld_stream(p + (int64_t)r * ld), a);
 #pragma unroll
-            for (int e = 0; e < W; ++e) acc[e] += a[e] * xsm[r];
+            for (int e = 0; e < W; ++e) acc[e].add(a[e] * xsm[r]);
         }
 #pragma unroll
-        for (int e = 0; e < W; ++e) red[g * ld + cv * W + e] = acc[e];
+        for (int e = 0; e < W; ++e) red[g * ld + cv * W + e] = acc[e].get();
     }
     __syncthreads();
     for (int c = threadIdx.x; c < RvY; c += kGatherThreads) {
@@ -185,7 +201,7 @@ struct LeafArgs {
     const int64_t *leaf_lp, *ubase, *tbase;
     const int *near_ptr, *near_src;
     const unsigned char *near_dir;
-    const float4 *ploc;
+    const float4 *ploc, *ploc_lo;
     const double *px, *py, *pz;
     // transpose
     const int *Rv, *ldv;
@@ -201,17 +217,24 @@ __device__ void near_field(const LeafArgs &A, int z, int zs, int m, const T *__r
 template <>
 __device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const float *__restrict__ xs, float *outsm,
                                   float4 *srcf, Pt4d *, float *partsm) {
+    // Coordinates are offsets from the leaf centre split into hi + lo floats.
+    // A source point is moved into the target leaf's frame by the exact box
+    // offset shift = (c_Y - c_Z); Fast2Sum keeps the rounding error of hi +
+    // shift (|shift| >= |hi|), so differences keep full FP32 relative accuracy
+    // even for very close pairs.
     const int T_ = kLeafThreads;
     const int S = m <= T_ ? max(1, T_ / m) : 1;
     const int ntg = m <= T_ ? 1 : (m + T_ - 1) / T_;   // targets per thread when m > T
     const int s = m <= T_ ? threadIdx.x / m : 0;
     const int i0 = m <= T_ ? threadIdx.x - s * m : threadIdx.x;
     const bool active = m <= T_ ? (s < S) : true;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    float4 tl[4];
+    Acc<float> acc[4];
+    float4 th[4], tl[4];
     for (int q = 0; q < ntg && q < 4; ++q) {
         const int i = i0 + q * T_;
-        tl[q] = (active && i < m) ? A.ploc[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = active && i < m;
+        th[q] = ok ? A.ploc[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        tl[q] = ok ? A.ploc_lo[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const float kap = (float)A.kappa;
     for (int p = A.near_ptr[z]; p < A.near_ptr[z + 1]; ++p) {
@@ -222,28 +245,31 @@ __device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const
                     sz = (float)((d % 3 - 1) * A.hL);
         __syncthreads();
         for (int j = threadIdx.x; j < n; j += T_) {
-            const float4 q = A.ploc[ys + j];
-            srcf[j] = make_float4(q.x + sx, q.y + sy, q.z + sz, xs[ys + j]);
+            const float4 h = A.ploc[ys + j], l = A.ploc_lo[ys + j];
+            const float hx = h.x + sx, hy = h.y + sy, hz = h.z + sz;
+            const float ex = h.x - (hx - sx), ey = h.y - (hy - sy), ez = h.z - (hz - sz);
+            srcf[2 * j] = make_float4(hx, hy, hz, xs[ys + j]);
+            srcf[2 * j + 1] = make_float4(ex + l.x, ey + l.y, ez + l.z, 0.f);
         }
         __syncthreads();
         if (active) {
             for (int q = 0; q < ntg && q < 4; ++q) {
                 const int i = i0 + q * T_;
                 if (i >= m) break;
-                float a = 0.f;
                 for (int j = s; j < n; j += S) {
-                    const float4 sp = srcf[j];
-                    const float dx = tl[q].x - sp.x, dy = tl[q].y - sp.y, dz = tl[q].z - sp.z;
+                    const float4 sh = srcf[2 * j], sl = srcf[2 * j + 1];
+                    const float dx = (th[q].x - sh.x) + (tl[q].x - sl.x);
+                    const float dy = (th[q].y - sh.y) + (tl[q].y - sl.y);
+                    const float dz = (th[q].z - sh.z) + (tl[q].z - sl.z);
                     const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    a = fmaf(kernel_fast(A.kind, kap, d2), sp.w, a);
+                    acc[q].add(kernel_fast(A.kind, kap, d2) * sh.w);
                 }
-                acc[q] += a;
             }
         }
     }
     // reduce over source groups
     if (m <= T_) {
-        if (active) partsm[threadIdx.x] = acc[0];
+        if (active) partsm[threadIdx.x] = acc[0].get();
         __syncthreads();
         for (int i = threadIdx.x; i < m; i += T_) {
             float v = 0.f;
@@ -253,7 +279,7 @@ __device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const
     } else {
         for (int q = 0; q < ntg && q < 4; ++q) {
             const int i = i0 + q * T_;
-            if (i < m) outsm[i] = acc[q];
+            if (i < m) outsm[i] = acc[q].get();
         }
     }
     __syncthreads();
@@ -334,11 +360,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__re
 
     // far field: rows in vectors of W, columns split over Gc groups
     const int Gc = nr <= kLeafThreads ? kLeafThreads / nr : 1;
-    T acc[2][W];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int e = 0; e < W; ++e) acc[h][e] = 0;
+    Acc<T> acc[2][W];
     const int g = nr <= kLeafThreads ? threadIdx.x / nr : 0;
     const int rv0 = nr <= kLeafThreads ? threadIdx.x - g * nr : threadIdx.x;
     if (g < Gc) {
@@ -363,14 +385,14 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__re
                     T a0[W], a1[W], a2[W], a3[W];
                     Vec<T>::get(v0, a0); Vec<T>::get(v1, a1); Vec<T>::get(v2, a2); Vec<T>::get(v3, a3);
 #pragma unroll
-                    for (int e = 0; e < W; ++e) acc[h][e] += a0[e] * t0 + a1[e] * t1 + a2[e] * t2 + a3[e] * t3;
+                    for (int e = 0; e < W; ++e) acc[h][e].add(a0[e] * t0 + a1[e] * t1 + a2[e] * t2 + a3[e] * t3);
                 }
                 for (; c < RA; c += Gc) {
                     T a[W];
                     Vec<T>::get(ld_stream(p + (int64_t)c * ld), a);
                     const T tc = __ldg(tA + c);
 #pragma unroll
-                    for (int e = 0; e < W; ++e) acc[h][e] += a[e] * tc;
+                    for (int e = 0; e < W; ++e) acc[h][e].add(a[e] * tc);
                 }
             }
         }
@@ -379,7 +401,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__re
     if (Gc > 1) {
         if (g < Gc)
 #pragma unroll
-            for (int e = 0; e < W; ++e) red[g * ld + rv0 * W + e] = acc[0][e];
+            for (int e = 0; e < W; ++e) red[g * ld + rv0 * W + e] = acc[0][e].get();
         __syncthreads();
         for (int i = threadIdx.x; i < m; i += kLeafThreads) {
             T v = 0;
@@ -393,7 +415,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__re
             if (rv < nr)
 #pragma unroll
                 for (int e = 0; e < W; ++e)
-                    if (rv * W + e < m) outsm[rv * W + e] = acc[h][e];
+                    if (rv * W + e < m) outsm[rv * W + e] = acc[h][e].get();
         }
     }
     __syncthreads();
@@ -508,7 +530,7 @@ LeafArgs leaf_args(const Handle &h) {
     A.leaf_anc = h.leaf_anc; A.R = h.R; A.leaf_lo = h.box_leaf_lo;
     A.leaf_lp = h.leaf_lp; A.ubase = h.ubase; A.tbase = h.tbase;
     A.near_ptr = h.near_ptr; A.near_src = h.near_src; A.near_dir = h.near_dir;
-    A.ploc = h.ploc; A.px = h.px; A.py = h.py; A.pz = h.pz;
+    A.ploc = h.ploc; A.ploc_lo = h.ploc_lo; A.px = h.px; A.py = h.py; A.pz = h.pz;
     A.Rv = h.Rv; A.ldv = h.ldv; A.vbase = h.vbase; A.vcol0 = h.vcol0; A.map_v = h.map_v; A.tp_base = h.tp_base;
     return A;
 }

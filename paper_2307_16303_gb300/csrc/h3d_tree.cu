@@ -159,13 +159,17 @@ __global__ void k_ancestors(const int *__restrict__ parent, int64_t off_leaf, in
 __global__ void k_local_coords(const double *__restrict__ px, const double *__restrict__ py,
                                const double *__restrict__ pz, const int *__restrict__ point_leaf,
                                const uint64_t *__restrict__ box_key, int64_t off_leaf, int L, double lo0,
-                               double lo1, double lo2, double h, int64_t n, float4 *__restrict__ ploc) {
+                               double lo1, double lo2, double h, int64_t n, float4 *__restrict__ ploc,
+                               float4 *__restrict__ ploc_lo) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int x, y, z;
     box_coords(box_key[off_leaf + point_leaf[i]], L, x, y, z);
     const double cx = lo0 + (x + 0.5) * h, cy = lo1 + (y + 0.5) * h, cz = lo2 + (z + 0.5) * h;
-    ploc[i] = make_float4((float)(px[i] - cx), (float)(py[i] - cy), (float)(pz[i] - cz), 0.0f);
+    const double dx = px[i] - cx, dy = py[i] - cy, dz = pz[i] - cz;
+    const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+    ploc[i] = make_float4(hx, hy, hz, 0.0f);
+    ploc_lo[i] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -426,9 +430,10 @@ void build_tree(Handle &h, const double *points, cudaStream_t s, Arena &tmp) {
         H3D_LAUNCH_CHECK();
     }
     h.ploc = h.mem.get<float4>((size_t)n);
+    h.ploc_lo = h.mem.get<float4>((size_t)n);
     const double hL = h.side / (double)(1 << L);
     k_local_coords<<<grid_for(n), kT, 0, s>>>(h.px, h.py, h.pz, h.point_leaf, h.box_key, offL, L, h.lo[0],
-                                                h.lo[1], h.lo[2], hL, n, h.ploc);
+                                                h.lo[1], h.lo[2], hL, n, h.ploc, h.ploc_lo);
     H3D_LAUNCH_CHECK();
 }
 
