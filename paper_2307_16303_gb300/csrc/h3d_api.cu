@@ -100,6 +100,9 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
     h3d_status st = guard([&] {
         h3d::Arena tmp;
         h.d_err = h.mem.get<int>(1);
+        H3D_CUDA(cudaHostAlloc((void **)&h.h_async_err, sizeof(int), cudaHostAllocMapped));
+        *h.h_async_err = 0;
+        H3D_CUDA(cudaHostGetDevicePointer((void **)&h.d_async_err, h.h_async_err, 0));
         h3d::build_tree(h, points, s, tmp);
         h3d::build_lists(h, s, tmp);
         h3d::build_factors(h, s, tmp, o.workspace_bytes);
@@ -118,10 +121,16 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
     return H3D_OK;
 }
 
+static h3d_status async_error(const Handle &h) {
+    const int e = *(volatile int *)h.h_async_err;
+    return e ? (h3d_status)e : H3D_OK;
+}
+
 static h3d_status matvec_common(h3d_handle hh, const void *x, void *y, int nrhs, void *stream, bool transpose) {
     if (!hh) return H3D_ERR_ARG;
     Handle &h = hh->h;
     if (!h.ok) return H3D_ERR_STATE;
+    if (h3d_status e = async_error(h)) return e;
     if (!x || !y || nrhs < 1 || x == y) return H3D_ERR_ARG;
     return guard([&] { h3d::run_matvec(h, x, y, nrhs, transpose, as_stream(stream)); });
 }
@@ -172,7 +181,8 @@ h3d_status h3d_matvec_profile(h3d_handle hh, const void *x, void *y, int nrhs, v
         h3d::run_matvec(h, x, y, nrhs, false, s, ev.data());
         H3D_CUDA(cudaStreamSynchronize(s));
         float acc[4] = {0, 0, 0, 0};
-        for (int c = 0; c < nrhs; ++c)
+        const int passes = h3d::matvec_passes(h, nrhs, false);
+        for (int c = 0; c < passes; ++c)
             for (int p = 0; p < 4; ++p) {
                 float ms = 0;
                 H3D_CUDA(cudaEventElapsedTime(&ms, ev[5 * c + p], ev[5 * c + p + 1]));

@@ -111,6 +111,22 @@ struct Handle {
 
     Arena mem;          // everything the handle keeps
     int *d_err = nullptr;
+    // error word of the product kernels in mapped host memory: a kernel whose
+    // bounded wait gave up stores a status there, the next call reports it
+    int *h_async_err = nullptr, *d_async_err = nullptr;
+    // second stream for the near field, and the fork / join events
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    void *nearbuf = nullptr;                      // near-field result, Morton order (N)
+    // multi-RHS scratch: blocks of 8 columns, point-major
+    void *xs_mr = nullptr, *nearbuf_mr = nullptr, *t_mr = nullptr, *partial_mr = nullptr;
+    ~Handle() {
+        if (side_stream) cudaStreamSynchronize(side_stream);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side_stream) cudaStreamDestroy(side_stream);
+        if (h_async_err) cudaFreeHost(h_async_err);
+    }
 
     // points
     double *px = nullptr, *py = nullptr, *pz = nullptr;
@@ -235,9 +251,9 @@ __device__ __forceinline__ float kernel_fast(int kind, float kappa, float d2) {
     float ir = rsqrtf(d2);
     switch (kind) {
     case H3D_LAPLACE: return (float)H3D_INV4PI * ir;
-    case H3D_YUKAWA: return (float)H3D_INV4PI * __expf(-kappa * d2 * ir) * ir;
+    case H3D_YUKAWA: return (float)H3D_INV4PI * expf(-kappa * d2 * ir) * ir;
     case H3D_INV_R4: return (ir * ir) * (ir * ir);
-    default: return __cosf(d2 * ir) * ir;
+    default: return cosf(d2 * ir) * ir;
     }
 }
 
@@ -281,6 +297,7 @@ void build_tree(Handle &h, const double *points, cudaStream_t s, Arena &tmp);   
 void build_lists(Handle &h, cudaStream_t s, Arena &tmp);                         // h3d_tree.cu
 void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget);      // h3d_aca.cu
 void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp);                   // h3d_matvec.cu
+int matvec_passes(const Handle &h, int nrhs, bool transpose);  // kernel sequences one product launches
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s,
                 cudaEvent_t *ev = nullptr);  // h3d_matvec.cu; ev: 5 events per rhs
 

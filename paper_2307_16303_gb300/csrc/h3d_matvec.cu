@@ -19,6 +19,7 @@
 //   V rows of every ancestor source box times t'       (k_leafT)
 #include <algorithm>
 
+#include "h3d_async.cuh"
 #include "h3d_internal.cuh"
 
 namespace h3d {
@@ -206,6 +207,7 @@ struct LeafArgs {
     // transpose
     const int *Rv, *ldv;
     const int64_t *vbase, *vcol0, *map_v, *tp_base;
+    int *err;                         // device-visible error word (bounded waits that gave up)
 };
 
 // Near-field sum for targets of leaf z: out[i] = sum over near leaves of
@@ -214,6 +216,9 @@ template <class T>
 __device__ void near_field(const LeafArgs &A, int z, int zs, int m, const T *__restrict__ xs, T *outsm,
                            float4 *srcf, Pt4d *srcd, T *partsm);
 
+// Source points of consecutive near leaves are staged together until the
+// staging buffer (kMaxLeaf points) is full, so a CTA synchronises about
+// (sum of near-leaf sizes) / kMaxLeaf times instead of once per near leaf.
 template <>
 __device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const float *__restrict__ xs, float *outsm,
                                   float4 *srcf, Pt4d *, float *partsm) {
@@ -230,33 +235,50 @@ __device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const
     const bool active = m <= T_ ? (s < S) : true;
     Acc<float> acc[4];
     float4 th[4], tl[4];
-    for (int q = 0; q < ntg && q < 4; ++q) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
         const int i = i0 + q * T_;
-        const bool ok = active && i < m;
+        const bool ok = active && q < ntg && i < m;
         th[q] = ok ? A.ploc[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
         tl[q] = ok ? A.ploc_lo[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const float kap = (float)A.kappa;
-    for (int p = A.near_ptr[z]; p < A.near_ptr[z + 1]; ++p) {
-        const int y = A.near_src[p];
-        const int ys = A.box_start[A.offL + y], n = A.box_end[A.offL + y] - ys;
-        const int d = A.near_dir[p];
-        const float sx = (float)((d / 9 - 1) * A.hL), sy = (float)(((d / 3) % 3 - 1) * A.hL),
-                    sz = (float)((d % 3 - 1) * A.hL);
+    const int p1 = A.near_ptr[z + 1];
+    int p = A.near_ptr[z];
+    while (p < p1) {
+        // stage near leaves [p, pe) together
+        int pe = p, cnt = 0;
+        while (pe < p1) {
+            const int y = A.near_src[pe];
+            const int n = A.box_end[A.offL + y] - A.box_start[A.offL + y];
+            if (cnt + n > kMaxLeaf && cnt > 0) break;
+            cnt += n;
+            ++pe;
+        }
         __syncthreads();
-        for (int j = threadIdx.x; j < n; j += T_) {
-            const float4 h = A.ploc[ys + j], l = A.ploc_lo[ys + j];
-            const float hx = h.x + sx, hy = h.y + sy, hz = h.z + sz;
-            const float ex = h.x - (hx - sx), ey = h.y - (hy - sy), ez = h.z - (hz - sz);
-            srcf[2 * j] = make_float4(hx, hy, hz, xs[ys + j]);
-            srcf[2 * j + 1] = make_float4(ex + l.x, ey + l.y, ez + l.z, 0.f);
+        int base = 0;
+        for (int q = p; q < pe; ++q) {
+            const int y = A.near_src[q];
+            const int ys = A.box_start[A.offL + y], n = A.box_end[A.offL + y] - ys;
+            const int d = A.near_dir[q];
+            const float sx = (float)((d / 9 - 1) * A.hL), sy = (float)(((d / 3) % 3 - 1) * A.hL),
+                        sz = (float)((d % 3 - 1) * A.hL);
+            for (int j = threadIdx.x; j < n; j += T_) {
+                const float4 h = A.ploc[ys + j], l = A.ploc_lo[ys + j];
+                const float hx = h.x + sx, hy = h.y + sy, hz = h.z + sz;
+                const float ex = h.x - (hx - sx), ey = h.y - (hy - sy), ez = h.z - (hz - sz);
+                srcf[2 * (base + j)] = make_float4(hx, hy, hz, xs[ys + j]);
+                srcf[2 * (base + j) + 1] = make_float4(ex + l.x, ey + l.y, ez + l.z, 0.f);
+            }
+            base += n;
         }
         __syncthreads();
         if (active) {
-            for (int q = 0; q < ntg && q < 4; ++q) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
                 const int i = i0 + q * T_;
-                if (i >= m) break;
-                for (int j = s; j < n; j += S) {
+                if (q >= ntg || i >= m) break;
+                for (int j = s; j < cnt; j += S) {
                     const float4 sh = srcf[2 * j], sl = srcf[2 * j + 1];
                     const float dx = (th[q].x - sh.x) + (tl[q].x - sl.x);
                     const float dy = (th[q].y - sh.y) + (tl[q].y - sl.y);
@@ -266,8 +288,10 @@ __device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const
                 }
             }
         }
+        p = pe;
     }
     // reduce over source groups
+    __syncthreads();
     if (m <= T_) {
         if (active) partsm[threadIdx.x] = acc[0].get();
         __syncthreads();
@@ -277,9 +301,10 @@ __device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const
             outsm[i] = v;
         }
     } else {
-        for (int q = 0; q < ntg && q < 4; ++q) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
             const int i = i0 + q * T_;
-            if (i < m) outsm[i] = acc[q].get();
+            if (q < ntg && i < m) outsm[i] = acc[q].get();
         }
     }
     __syncthreads();
@@ -296,26 +321,42 @@ __device__ void near_field<double>(const LeafArgs &A, int z, int zs, int m, cons
     const bool active = m <= T_ ? (s < S) : true;
     double acc[4] = {0, 0, 0, 0};
     double tx[4], ty[4], tz[4];
-    for (int q = 0; q < ntg && q < 4; ++q) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
         const int i = i0 + q * T_;
-        const bool ok = active && i < m;
+        const bool ok = active && q < ntg && i < m;
         tx[q] = ok ? A.px[zs + i] : 0.0;
         ty[q] = ok ? A.py[zs + i] : 0.0;
         tz[q] = ok ? A.pz[zs + i] : 0.0;
     }
-    for (int p = A.near_ptr[z]; p < A.near_ptr[z + 1]; ++p) {
-        const int y = A.near_src[p];
-        const int ys = A.box_start[A.offL + y], n = A.box_end[A.offL + y] - ys;
+    const int p1 = A.near_ptr[z + 1];
+    int p = A.near_ptr[z];
+    while (p < p1) {
+        int pe = p, cnt = 0;
+        while (pe < p1) {
+            const int y = A.near_src[pe];
+            const int n = A.box_end[A.offL + y] - A.box_start[A.offL + y];
+            if (cnt + n > kMaxLeaf && cnt > 0) break;
+            cnt += n;
+            ++pe;
+        }
         __syncthreads();
-        for (int j = threadIdx.x; j < n; j += T_)
-            srcd[j] = make_pt4d(A.px[ys + j], A.py[ys + j], A.pz[ys + j], xs[ys + j]);
+        int base = 0;
+        for (int q = p; q < pe; ++q) {
+            const int y = A.near_src[q];
+            const int ys = A.box_start[A.offL + y], n = A.box_end[A.offL + y] - ys;
+            for (int j = threadIdx.x; j < n; j += T_)
+                srcd[base + j] = make_pt4d(A.px[ys + j], A.py[ys + j], A.pz[ys + j], xs[ys + j]);
+            base += n;
+        }
         __syncthreads();
         if (active) {
-            for (int q = 0; q < ntg && q < 4; ++q) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
                 const int i = i0 + q * T_;
-                if (i >= m) break;
+                if (q >= ntg || i >= m) break;
                 double a = 0.0;
-                for (int j = s; j < n; j += S) {
+                for (int j = s; j < cnt; j += S) {
                     const Pt4d sp = srcd[j];
                     const double dx = tx[q] - sp.x, dy = ty[q] - sp.y, dz = tz[q] - sp.z;
                     const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
@@ -324,7 +365,9 @@ __device__ void near_field<double>(const LeafArgs &A, int z, int zs, int m, cons
                 acc[q] += a;
             }
         }
+        p = pe;
     }
+    __syncthreads();
     if (m <= T_) {
         if (active) partsm[threadIdx.x] = acc[0];
         __syncthreads();
@@ -334,52 +377,131 @@ __device__ void near_field<double>(const LeafArgs &A, int z, int zs, int m, cons
             outsm[i] = v;
         }
     } else {
-        for (int q = 0; q < ntg && q < 4; ++q) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
             const int i = i0 + q * T_;
-            if (i < m) outsm[i] = acc[q];
+            if (q < ntg && i < m) outsm[i] = acc[q];
         }
     }
     __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-// A6 + A8 + A9: one CTA per leaf
+// A6 + A8 + A9: one CTA per leaf.
+//
+// Far field: for every level the leaf reads one contiguous U panel (ld x R_A,
+// column-major).  The panels of all levels are cut into chunks of whole
+// columns (<= kChunkBytes) and streamed through a ring of kStages shared-memory
+// buffers by bulk asynchronous copies (TMA) that complete on one mbarrier per
+// buffer; one elected thread issues the copies kStages-1 chunks ahead.  Threads
+// own W consecutive rows of a column group and accumulate U(rows, c) t_A(c)
+// from shared memory.  Then the near field and y = far + near in caller order.
+constexpr int kStages = 4;
+constexpr int kChunkBytes = 8192;
+constexpr size_t kLeafDynSmem = (size_t)kStages * kChunkBytes;
+
+struct ChunkPlan {
+    const void *panel[kMaxDepth + 1];
+    const void *tA[kMaxDepth + 1];
+    int R[kMaxDepth + 1];
+    int first[kMaxDepth + 2];   // first chunk of level l (l = 1..L), first[L+1] = total
+};
+
+template <class T>
+__device__ __forceinline__ void chunk_of(const ChunkPlan &P, int L, int k, int cpc, int &l, int &c0, int &nc) {
+    while (l < L && k >= P.first[l + 1]) ++l;
+    c0 = (k - P.first[l]) * cpc;
+    nc = min(cpc, P.R[l] - c0);
+}
+
 template <class T>
 __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__restrict__ U, const T *__restrict__ t,
-                                                       const T *__restrict__ xs, T *__restrict__ y) {
+                                                       const T *__restrict__ nearbuf, T *__restrict__ y) {
     constexpr int W = Vec<T>::W;
-    __shared__ T outsm[kMaxLeaf];
-    __shared__ T nearsm[kMaxLeaf];
+    extern __shared__ __align__(128) unsigned char stage[];   // kStages * kChunkBytes
+    __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ ChunkPlan P;
     __shared__ T red[kLeafThreads * W];
-    __shared__ __align__(16) unsigned char srcbuf[kMaxLeaf * 32];
     const int z = blockIdx.x;
     const int Zg = (int)(A.offL + z);
     const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
     const int ld = A.leaf_ld[z];
     const int nr = ld / W;
+    const int cpc = kChunkBytes / (ld * (int)sizeof(T));   // columns per chunk (ld <= 512)
+    const int L = A.L;
 
-    // far field: rows in vectors of W, columns split over Gc groups
+    // per-level panels, one thread per level, then the chunk prefix
+    if (threadIdx.x >= 1 && threadIdx.x <= L) {
+        const int l = threadIdx.x;
+        const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
+        const int RA = A.R[Ag];
+        P.panel[l] = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
+        P.tA[l] = t + A.tbase[Ag];
+        P.R[l] = RA;
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kStages; ++q) mbar_init(&bars[q], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int l = 1; l <= L; ++l) {
+            P.first[l] = acc;
+            acc += (P.R[l] + cpc - 1) / cpc;
+        }
+        P.first[L + 1] = acc;
+    }
+    __syncthreads();
+    const int nchunks = P.first[L + 1];
+
+    // one elected thread keeps the ring full
+    int pl = 1;
+    auto issue = [&](int k) {
+        int c0, nc;
+        chunk_of<T>(P, L, k, cpc, pl, c0, nc);
+        const uint32_t bytes = (uint32_t)(nc * ld * (int)sizeof(T));
+        uint64_t *bar = &bars[k % kStages];
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_copy_g2s(stage + (size_t)(k % kStages) * kChunkBytes,
+                      static_cast<const T *>(P.panel[pl]) + (int64_t)c0 * ld, bytes, bar);
+    };
+    if (threadIdx.x == 0)
+        for (int k = 0; k < min(kStages - 1, nchunks); ++k) issue(k);
+
     const int Gc = nr <= kLeafThreads ? kLeafThreads / nr : 1;
-    Acc<T> acc[2][W];
     const int g = nr <= kLeafThreads ? threadIdx.x / nr : 0;
     const int rv0 = nr <= kLeafThreads ? threadIdx.x - g * nr : threadIdx.x;
-    if (g < Gc) {
-        for (int l = 1; l <= A.L; ++l) {
-            const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
-            const int RA = A.R[Ag];
-            if (RA == 0) continue;
-            const T *panel = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
-            const T *tA = t + A.tbase[Ag];
+    Acc<T> acc[2][W];
+    int cl_level = 1;
+    for (int k = 0; k < nchunks; ++k) {
+        const bool ok = mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+        // every thread has finished chunk k-1 here, so its buffer may be refilled
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                *A.err = H3D_ERR_TIMEOUT;
+                for (int j = k; j < min(k + kStages - 1, nchunks); ++j)   // copies still in flight
+                    mbar_wait(&bars[j % kStages], (uint32_t)((j / kStages) & 1));
+            }
+            return;
+        }
+        if (threadIdx.x == 0 && k + kStages - 1 < nchunks) issue(k + kStages - 1);
+        int c0, nc;
+        chunk_of<T>(P, L, k, cpc, cl_level, c0, nc);
+        const T *sm = reinterpret_cast<const T *>(stage + (size_t)(k % kStages) * kChunkBytes);
+        const T *tA = static_cast<const T *>(P.tA[cl_level]) + c0;
+        if (g < Gc) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int rv = rv0 + h * kLeafThreads;
                 if (rv >= nr) break;
-                const T *p = panel + rv * W;
+                const T *p = sm + rv * W;
                 int c = g;
-                for (; c + 3 * Gc < RA; c += 4 * Gc) {
-                    typename Vec<T>::type v0 = ld_stream(p + (int64_t)c * ld), v1 = ld_stream(p + (int64_t)(c + Gc) * ld),
-                                          v2 = ld_stream(p + (int64_t)(c + 2 * Gc) * ld),
-                                          v3 = ld_stream(p + (int64_t)(c + 3 * Gc) * ld);
+                for (; c + 3 * Gc < nc; c += 4 * Gc) {
+                    typename Vec<T>::type v0 = *reinterpret_cast<const typename Vec<T>::type *>(p + c * ld),
+                                          v1 = *reinterpret_cast<const typename Vec<T>::type *>(p + (c + Gc) * ld),
+                                          v2 = *reinterpret_cast<const typename Vec<T>::type *>(p + (c + 2 * Gc) * ld),
+                                          v3 = *reinterpret_cast<const typename Vec<T>::type *>(p + (c + 3 * Gc) * ld);
                     const T t0 = __ldg(tA + c), t1 = __ldg(tA + c + Gc), t2 = __ldg(tA + c + 2 * Gc),
                             t3 = __ldg(tA + c + 3 * Gc);
                     T a0[W], a1[W], a2[W], a3[W];
@@ -387,9 +509,9 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__re
 #pragma unroll
                     for (int e = 0; e < W; ++e) acc[h][e].add(a0[e] * t0 + a1[e] * t1 + a2[e] * t2 + a3[e] * t3);
                 }
-                for (; c < RA; c += Gc) {
+                for (; c < nc; c += Gc) {
                     T a[W];
-                    Vec<T>::get(ld_stream(p + (int64_t)c * ld), a);
+                    Vec<T>::get(*reinterpret_cast<const typename Vec<T>::type *>(p + c * ld), a);
                     const T tc = __ldg(tA + c);
 #pragma unroll
                     for (int e = 0; e < W; ++e) acc[h][e].add(a[e] * tc);
@@ -397,7 +519,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__re
             }
         }
     }
-    // reduce over column groups into outsm (far part)
+    // reduce over column groups, add the near field, write in the caller's order
     if (Gc > 1) {
         if (g < Gc)
 #pragma unroll
@@ -406,7 +528,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__re
         for (int i = threadIdx.x; i < m; i += kLeafThreads) {
             T v = 0;
             for (int q = 0; q < Gc; ++q) v += red[q * ld + i];
-            outsm[i] = v;
+            y[A.perm[zs + i]] = v + nearbuf[zs + i];
         }
     } else {
 #pragma unroll
@@ -414,15 +536,27 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__re
             const int rv = rv0 + h * kLeafThreads;
             if (rv < nr)
 #pragma unroll
-                for (int e = 0; e < W; ++e)
-                    if (rv * W + e < m) outsm[rv * W + e] = acc[h][e].get();
+                for (int e = 0; e < W; ++e) {
+                    const int i = rv * W + e;
+                    if (i < m) y[A.perm[zs + i]] = acc[h][e].get() + nearbuf[zs + i];
+                }
         }
     }
-    __syncthreads();
-    // near field (red reused for the source-group partials), then y[perm] = near + far
-    near_field<T>(A, z, zs, m, xs, nearsm, reinterpret_cast<float4 *>(srcbuf), reinterpret_cast<Pt4d *>(srcbuf),
-                  red);
-    for (int i = threadIdx.x; i < m; i += kLeafThreads) y[A.perm[zs + i]] = outsm[i] + nearsm[i];
+}
+
+// A6: dense self / face / edge near field of one leaf per CTA, into nearbuf
+// (Morton order).  Runs on a second stream, overlapping the source-side gather.
+template <class T>
+__global__ void __launch_bounds__(kLeafThreads) k_near(LeafArgs A, const T *__restrict__ xs, T *__restrict__ nearbuf) {
+    __shared__ T outsm[kMaxLeaf];
+    __shared__ T partsm[kLeafThreads];
+    __shared__ __align__(16) unsigned char srcbuf[kMaxLeaf * 32];
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+    near_field<T>(A, z, zs, m, xs, outsm, reinterpret_cast<float4 *>(srcbuf), reinterpret_cast<Pt4d *>(srcbuf),
+                  partsm);
+    for (int i = threadIdx.x; i < m; i += kLeafThreads) nearbuf[zs + i] = outsm[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -478,14 +612,12 @@ __global__ void k_reduceT(ReduceTArgs S, const T *__restrict__ tpart, T *__restr
     }
 }
 
-// per leaf: near field + rows of every ancestor source box's V times t'
+// per leaf: rows of every ancestor source box's V times t', plus the near field
 template <class T>
 __global__ void __launch_bounds__(kLeafThreads) k_leafT(LeafArgs A, const T *__restrict__ V, const T *__restrict__ t,
-                                                        const T *__restrict__ xs, T *__restrict__ y) {
+                                                        const T *__restrict__ nearbuf, T *__restrict__ y) {
     __shared__ T outsm[kMaxLeaf];
-    __shared__ T nearsm[kMaxLeaf];
     __shared__ T tsm[2048];
-    __shared__ __align__(16) unsigned char srcbuf[kMaxLeaf * 32];
     const int z = blockIdx.x;
     const int Zg = (int)(A.offL + z);
     const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
@@ -514,9 +646,378 @@ __global__ void __launch_bounds__(kLeafThreads) k_leafT(LeafArgs A, const T *__r
         }
     }
     __syncthreads();
-    near_field<T>(A, z, zs, m, xs, nearsm, reinterpret_cast<float4 *>(srcbuf), reinterpret_cast<Pt4d *>(srcbuf),
-                  tsm);
-    for (int i = threadIdx.x; i < m; i += kLeafThreads) y[A.perm[zs + i]] = outsm[i] + nearsm[i];
+    for (int i = threadIdx.x; i < m; i += kLeafThreads) y[A.perm[zs + i]] = outsm[i] + nearbuf[zs + i];
+}
+
+// ===========================================================================
+// Several right-hand sides: blocks of kNQ columns per pass over the factors.
+// x, t, partials and the near field are point-major inside a block
+// (value (i, q) at i * kNQ + q), so every factor element streamed from HBM
+// feeds kNQ fused multiply-adds.  Leaves of up to kMaxLeafMR points.
+constexpr int kNQ = 8;
+constexpr int kMaxLeafMR = 256;
+constexpr int kRowChunk = 256;
+
+template <class T>
+__global__ void k_permute_in_mr(const T *__restrict__ x, int64_t n, int q0, int nq, const int *__restrict__ perm,
+                                T *__restrict__ xs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = perm[i];
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q) xs[i * kNQ + q] = q < nq ? x[(int64_t)(q0 + q) * n + o] : T(0);
+}
+
+// T_Y(c, q) = sum_r V_Y(r, c) x(r, q) over the task's rows
+template <class T>
+__global__ void __launch_bounds__(kGatherThreads) k_gather_mr(GatherArgs G, const T *__restrict__ V,
+                                                              const T *__restrict__ xs, T *__restrict__ t,
+                                                              T *__restrict__ partial) {
+    constexpr int W = Vec<T>::W;
+    __shared__ T xsm[kRowChunk * kNQ];
+    __shared__ T red[kGatherThreads * W];
+    const int4 task = G.task[blockIdx.x];
+    const int Y = task.x, r0 = task.y, r1 = task.z;
+    const int nrows = r1 - r0;
+    const int ld = G.ldv[Y], RvY = G.Rv[Y];
+    const int ncv = ld / W;
+    const T *Vb = V + G.vbase[Y] + (int64_t)r0 * ld;
+    const int64_t ys = (int64_t)G.box_start[Y] + r0;
+    const bool direct = task.w != 0;
+    const int64_t pb = G.pbase[blockIdx.x];
+    const int64_t vc0 = G.vcol0[Y];
+    const bool wide = ncv >= kGatherThreads;
+    const int Gn = wide ? 1 : kGatherThreads / ncv;
+    const int g = wide ? 0 : threadIdx.x / ncv;
+    for (int cvb = 0; cvb < (wide ? ncv : 1); cvb += kGatherThreads) {
+        const int cv = wide ? cvb + threadIdx.x : threadIdx.x - g * ncv;
+        const bool act = wide ? cv < ncv : g < Gn;
+        Acc<T> acc[W][kNQ];
+        for (int rc = 0; rc < nrows; rc += kRowChunk) {
+            const int nr = min(kRowChunk, nrows - rc);
+            __syncthreads();
+            for (int e = threadIdx.x; e < nr * kNQ; e += kGatherThreads) xsm[e] = xs[(ys + rc) * kNQ + e];
+            __syncthreads();
+            if (act) {
+                const T *p = Vb + (int64_t)rc * ld + cv * W;
+                int r = g;
+                // four rows per compensated add: 4 FMAs per (column, rhs), then one add
+                for (; r + 3 * Gn < nr; r += 4 * Gn) {
+                    T a0[W], a1[W], a2[W], a3[W];
+                    Vec<T>::get(ld_stream(p + (int64_t)r * ld), a0);
+                    Vec<T>::get(ld_stream(p + (int64_t)(r + Gn) * ld), a1);
+                    Vec<T>::get(ld_stream(p + (int64_t)(r + 2 * Gn) * ld), a2);
+                    Vec<T>::get(ld_stream(p + (int64_t)(r + 3 * Gn) * ld), a3);
+                    const T *x0 = xsm + r * kNQ, *x1 = x0 + Gn * kNQ, *x2 = x1 + Gn * kNQ, *x3 = x2 + Gn * kNQ;
+#pragma unroll
+                    for (int q = 0; q < kNQ; ++q)
+#pragma unroll
+                        for (int e = 0; e < W; ++e)
+                            acc[e][q].add(a0[e] * x0[q] + a1[e] * x1[q] + a2[e] * x2[q] + a3[e] * x3[q]);
+                }
+                for (; r < nr; r += Gn) {
+                    T a[W];
+                    Vec<T>::get(ld_stream(p + (int64_t)r * ld), a);
+                    const T *xr = xsm + r * kNQ;
+#pragma unroll
+                    for (int q = 0; q < kNQ; ++q)
+#pragma unroll
+                        for (int e = 0; e < W; ++e) acc[e][q].add(a[e] * xr[q]);
+                }
+            }
+        }
+        if (wide) {
+            if (act)
+#pragma unroll
+                for (int e = 0; e < W; ++e) {
+                    const int c = cv * W + e;
+                    if (c < RvY) {
+                        T *o = direct ? t + G.map_v[vc0 + c] * kNQ : partial + (pb + c) * kNQ;
+#pragma unroll
+                        for (int q = 0; q < kNQ; ++q) o[q] = acc[e][q].get();
+                    }
+                }
+        } else {
+            for (int q = 0; q < kNQ; ++q) {
+                if (act)
+#pragma unroll
+                    for (int e = 0; e < W; ++e) red[g * ld + cv * W + e] = acc[e][q].get();
+                __syncthreads();
+                for (int c = threadIdx.x; c < RvY; c += kGatherThreads) {
+                    T v = 0;
+                    for (int u = 0; u < Gn; ++u) v += red[u * ld + c];
+                    T *o = direct ? t + G.map_v[vc0 + c] * kNQ : partial + (pb + c) * kNQ;
+                    o[q] = v;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+template <class T>
+__global__ void k_reduce_partials_mr(SplitArgs S, const T *__restrict__ partial, T *__restrict__ t) {
+    const int q = blockIdx.x;
+    const int Y = S.box[q], nt = S.ntask[q], ld = S.ldv[Y], R = S.Rv[Y];
+    const int64_t pb = S.pbase[q], vc0 = S.vcol0[Y];
+    for (int e = threadIdx.x; e < R * kNQ; e += blockDim.x) {
+        const int c = e / kNQ, j = e - c * kNQ;
+        T v = 0;
+        for (int k = 0; k < nt; ++k) v += partial[(pb + (int64_t)k * ld + c) * kNQ + j];
+        t[S.map_v[vc0 + c] * kNQ + j] = v;
+    }
+}
+
+// near field of one leaf for kNQ right-hand sides, into nearbuf (point-major)
+template <class T>
+__global__ void __launch_bounds__(kLeafThreads) k_near_mr(LeafArgs A, const T *__restrict__ xs, T *__restrict__ nearbuf) {
+    __shared__ __align__(16) float4 srcf[kMaxLeafMR * 2];          // FP32: hi, lo coordinates
+    __shared__ __align__(16) Pt4d srcd[sizeof(T) == 8 ? kMaxLeafMR : 1];
+    __shared__ T xsrc[kMaxLeafMR * kNQ];
+    __shared__ T part[kLeafThreads * kNQ];
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+    const int T_ = kLeafThreads;
+    const int S = m <= T_ ? max(1, T_ / m) : 1;
+    const int ntg = m <= T_ ? 1 : (m + T_ - 1) / T_;   // at most 2 for m <= 256
+    const int s = m <= T_ ? threadIdx.x / m : 0;
+    const int i0 = m <= T_ ? threadIdx.x - s * m : threadIdx.x;
+    const bool active = m <= T_ ? (s < S) : true;
+    Acc<T> acc[2][kNQ];
+    float4 th[2], tl[2];
+    double tx[2], ty[2], tz[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int i = i0 + q * T_;
+        const bool ok = active && q < ntg && i < m;
+        if (sizeof(T) == 4) {
+            th[q] = ok ? A.ploc[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            tl[q] = ok ? A.ploc_lo[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            tx[q] = ok ? A.px[zs + i] : 0.0;
+            ty[q] = ok ? A.py[zs + i] : 0.0;
+            tz[q] = ok ? A.pz[zs + i] : 0.0;
+        }
+    }
+    const float kap = (float)A.kappa;
+    const int p1 = A.near_ptr[z + 1];
+    int p = A.near_ptr[z];
+    while (p < p1) {
+        // stage near leaves [p, pe) together (up to kMaxLeafMR points)
+        int pe = p, cnt = 0;
+        while (pe < p1) {
+            const int y = A.near_src[pe];
+            const int n = A.box_end[A.offL + y] - A.box_start[A.offL + y];
+            if (cnt + n > kMaxLeafMR && cnt > 0) break;
+            cnt += n;
+            ++pe;
+        }
+        __syncthreads();
+        int base = 0;
+        for (int pq = p; pq < pe; ++pq) {
+            const int y = A.near_src[pq];
+            const int ys = A.box_start[A.offL + y], n = A.box_end[A.offL + y] - ys;
+            const int d = A.near_dir[pq];
+            const float sx = (float)((d / 9 - 1) * A.hL), sy = (float)(((d / 3) % 3 - 1) * A.hL),
+                        sz = (float)((d % 3 - 1) * A.hL);
+            for (int j = threadIdx.x; j < n; j += T_) {
+                if (sizeof(T) == 4) {
+                    const float4 h = A.ploc[ys + j], l = A.ploc_lo[ys + j];
+                    const float hx = h.x + sx, hy = h.y + sy, hz = h.z + sz;
+                    srcf[2 * (base + j)] = make_float4(hx, hy, hz, 0.f);
+                    srcf[2 * (base + j) + 1] = make_float4((h.x - (hx - sx)) + l.x, (h.y - (hy - sy)) + l.y,
+                                                           (h.z - (hz - sz)) + l.z, 0.f);
+                } else {
+                    srcd[base + j] = make_pt4d(A.px[ys + j], A.py[ys + j], A.pz[ys + j], 0.0);
+                }
+            }
+            for (int e = threadIdx.x; e < n * kNQ; e += T_) xsrc[base * kNQ + e] = xs[(int64_t)ys * kNQ + e];
+            base += n;
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int i = i0 + q * T_;
+                if (q >= ntg || i >= m) break;
+                for (int j = s; j < cnt; j += S) {
+                    T kij;
+                    if (sizeof(T) == 4) {
+                        const float4 sh = srcf[2 * j], sl = srcf[2 * j + 1];
+                        const float dx = (th[q].x - sh.x) + (tl[q].x - sl.x);
+                        const float dy = (th[q].y - sh.y) + (tl[q].y - sl.y);
+                        const float dz = (th[q].z - sh.z) + (tl[q].z - sl.z);
+                        kij = (T)kernel_fast(A.kind, kap, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                    } else {
+                        const Pt4d sp = srcd[j];
+                        const double dx = tx[q] - sp.x, dy = ty[q] - sp.y, dz = tz[q] - sp.z;
+                        kij = (T)kernel_fast(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)));
+                    }
+                    const T *xj = xsrc + j * kNQ;
+#pragma unroll
+                    for (int u = 0; u < kNQ; ++u) acc[q][u].add(kij * xj[u]);
+                }
+            }
+        }
+        p = pe;
+    }
+    __syncthreads();
+    if (m <= T_) {
+        if (active)
+#pragma unroll
+            for (int u = 0; u < kNQ; ++u) part[threadIdx.x * kNQ + u] = acc[0][u].get();
+        __syncthreads();
+        for (int e = threadIdx.x; e < m * kNQ; e += T_) {
+            const int i = e / kNQ, u = e - i * kNQ;
+            T v = 0;
+            for (int g = 0; g < S; ++g) v += part[(g * m + i) * kNQ + u];
+            nearbuf[(int64_t)(zs + i) * kNQ + u] = v;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i = i0 + q * T_;
+            if (q < ntg && i < m)
+#pragma unroll
+                for (int u = 0; u < kNQ; ++u) nearbuf[(int64_t)(zs + i) * kNQ + u] = acc[q][u].get();
+        }
+    }
+}
+
+// far field of one leaf for kNQ right-hand sides (TMA ring as k_leaf), plus the
+// near field, written to columns q0 .. q0+nq-1 of y in the caller's order
+template <class T>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf_mr(LeafArgs A, const T *__restrict__ U, const T *__restrict__ t,
+                                                          const T *__restrict__ nearbuf, T *__restrict__ y, int64_t n,
+                                                          int q0, int nq) {
+    constexpr int W = Vec<T>::W;
+    extern __shared__ __align__(128) unsigned char stage[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ ChunkPlan P;
+    __shared__ T red[kLeafThreads * W];
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+    const int ld = A.leaf_ld[z];
+    const int nr = ld / W;                                  // <= kLeafThreads for leaves <= kMaxLeafMR
+    const int cpc = kChunkBytes / (ld * (int)sizeof(T));
+    const int L = A.L;
+    if (threadIdx.x >= 1 && threadIdx.x <= L) {
+        const int l = threadIdx.x;
+        const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
+        const int RA = A.R[Ag];
+        P.panel[l] = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
+        P.tA[l] = t + A.tbase[Ag] * kNQ;
+        P.R[l] = RA;
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kStages; ++q) mbar_init(&bars[q], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int l = 1; l <= L; ++l) {
+            P.first[l] = acc;
+            acc += (P.R[l] + cpc - 1) / cpc;
+        }
+        P.first[L + 1] = acc;
+    }
+    __syncthreads();
+    const int nchunks = P.first[L + 1];
+    int pl = 1;
+    auto issue = [&](int k) {
+        int c0, nc;
+        chunk_of<T>(P, L, k, cpc, pl, c0, nc);
+        const uint32_t bytes = (uint32_t)(nc * ld * (int)sizeof(T));
+        uint64_t *bar = &bars[k % kStages];
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_copy_g2s(stage + (size_t)(k % kStages) * kChunkBytes,
+                      static_cast<const T *>(P.panel[pl]) + (int64_t)c0 * ld, bytes, bar);
+    };
+    if (threadIdx.x == 0)
+        for (int k = 0; k < min(kStages - 1, nchunks); ++k) issue(k);
+    const int Gc = kLeafThreads / nr;
+    const int g = threadIdx.x / nr;
+    const int rv = threadIdx.x - g * nr;
+    Acc<T> acc[W][kNQ];
+    int cl_level = 1;
+    for (int k = 0; k < nchunks; ++k) {
+        const bool ok = mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                *A.err = H3D_ERR_TIMEOUT;
+                for (int j = k; j < min(k + kStages - 1, nchunks); ++j)
+                    mbar_wait(&bars[j % kStages], (uint32_t)((j / kStages) & 1));
+            }
+            return;
+        }
+        if (threadIdx.x == 0 && k + kStages - 1 < nchunks) issue(k + kStages - 1);
+        int c0, nc;
+        chunk_of<T>(P, L, k, cpc, cl_level, c0, nc);
+        const T *sm = reinterpret_cast<const T *>(stage + (size_t)(k % kStages) * kChunkBytes) + rv * W;
+        const T *tA = static_cast<const T *>(P.tA[cl_level]) + (int64_t)c0 * kNQ;
+        if (g < Gc) {
+            int c = g;
+            // four columns per compensated add
+            for (; c + 3 * Gc < nc; c += 4 * Gc) {
+                T part[W][kNQ];
+#pragma unroll
+                for (int e = 0; e < W; ++e)
+#pragma unroll
+                    for (int u = 0; u < kNQ; ++u) part[e][u] = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int cj = c + j * Gc;
+                    T a[W];
+                    Vec<T>::get(*reinterpret_cast<const typename Vec<T>::type *>(sm + cj * ld), a);
+#pragma unroll
+                    for (int u = 0; u < kNQ; u += W) {
+                        T b[W];
+                        Vec<T>::get(__ldg(reinterpret_cast<const typename Vec<T>::type *>(tA + (int64_t)cj * kNQ + u)), b);
+#pragma unroll
+                        for (int e = 0; e < W; ++e)
+#pragma unroll
+                            for (int f = 0; f < W; ++f) part[e][u + f] = fma(a[e], b[f], part[e][u + f]);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < W; ++e)
+#pragma unroll
+                    for (int u = 0; u < kNQ; ++u) acc[e][u].add(part[e][u]);
+            }
+            for (; c < nc; c += Gc) {
+                T a[W];
+                Vec<T>::get(*reinterpret_cast<const typename Vec<T>::type *>(sm + c * ld), a);
+#pragma unroll
+                for (int u = 0; u < kNQ; u += W) {
+                    T b[W];
+                    Vec<T>::get(__ldg(reinterpret_cast<const typename Vec<T>::type *>(tA + (int64_t)c * kNQ + u)), b);
+#pragma unroll
+                    for (int e = 0; e < W; ++e)
+#pragma unroll
+                        for (int f = 0; f < W; ++f) acc[e][u + f].add(a[e] * b[f]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kNQ; ++u) {
+        if (u < nq) {   // nq is uniform over the CTA
+            if (g < Gc)
+#pragma unroll
+                for (int e = 0; e < W; ++e) red[g * ld + rv * W + e] = acc[e][u].get();
+            __syncthreads();
+            for (int i = threadIdx.x; i < m; i += kLeafThreads) {
+                T v = 0;
+                for (int q = 0; q < Gc; ++q) v += red[q * ld + i];
+                y[(int64_t)(q0 + u) * n + A.perm[zs + i]] = v + nearbuf[(int64_t)(zs + i) * kNQ + u];
+            }
+            __syncthreads();
+        }
+    }
 }
 
 unsigned gridn(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -532,6 +1033,7 @@ LeafArgs leaf_args(const Handle &h) {
     A.near_ptr = h.near_ptr; A.near_src = h.near_src; A.near_dir = h.near_dir;
     A.ploc = h.ploc; A.ploc_lo = h.ploc_lo; A.px = h.px; A.py = h.py; A.pz = h.pz;
     A.Rv = h.Rv; A.ldv = h.ldv; A.vbase = h.vbase; A.vcol0 = h.vcol0; A.map_v = h.map_v; A.tp_base = h.tp_base;
+    A.err = h.d_async_err;
     return A;
 }
 
@@ -549,6 +1051,12 @@ void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s, cud
     k_permute_in<T><<<gridn(n, 256), 256, 0, s>>>(x, h.perm, n, xs);
     if (ev) H3D_CUDA(cudaEventRecord(ev[1], s));
     LeafArgs A = leaf_args(h);
+    T *nearbuf = (T *)h.nearbuf;
+    // near field on the side stream, overlapping the factor streams
+    H3D_CUDA(cudaEventRecord(h.ev_fork, s));
+    H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
+    k_near<T><<<h.nleaf, kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
+    H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
     if (!transpose) {
         if (h.ngtask > 0) {
             GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
@@ -559,8 +1067,9 @@ void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s, cud
             SplitArgs S{h.split_box, h.split_ntask, h.split_pbase, h.Rv, h.ldv, h.vcol0, h.map_v};
             k_reduce_partials<T><<<h.nsplit, 256, 0, s>>>(S, (const T *)h.partial, t);
         }
+        H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
         if (ev) H3D_CUDA(cudaEventRecord(ev[3], s));
-        k_leaf<T><<<h.nleaf, kLeafThreads, 0, s>>>(A, (const T *)h.U, t, xs, y);
+        k_leaf<T><<<h.nleaf, kLeafThreads, kLeafDynSmem, s>>>(A, (const T *)h.U, t, nearbuf, y);
         if (ev) H3D_CUDA(cudaEventRecord(ev[4], s));
     } else {
         if (h.nblk > 0) {
@@ -571,8 +1080,37 @@ void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s, cud
                 k_reduceT<T><<<h.nsplit_T, 256, 0, s>>>(R, (const T *)h.tpartial, t);
             }
         }
-        k_leafT<T><<<h.nleaf, kLeafThreads, 0, s>>>(A, (const T *)h.V, t, xs, y);
+        H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
+        k_leafT<T><<<h.nleaf, kLeafThreads, 0, s>>>(A, (const T *)h.V, t, nearbuf, y);
     }
+    H3D_LAUNCH_CHECK();
+}
+
+template <class T>
+void matvec_mr(Handle &h, const T *x, T *y, int q0, int nq, cudaStream_t s, cudaEvent_t *ev) {
+    const int64_t n = h.N;
+    T *xs = (T *)h.xs_mr, *t = (T *)h.t_mr, *nearbuf = (T *)h.nearbuf_mr;
+    if (ev) H3D_CUDA(cudaEventRecord(ev[0], s));
+    k_permute_in_mr<T><<<gridn(n, 256), 256, 0, s>>>(x, n, q0, nq, h.perm, xs);
+    if (ev) H3D_CUDA(cudaEventRecord(ev[1], s));
+    LeafArgs A = leaf_args(h);
+    H3D_CUDA(cudaEventRecord(h.ev_fork, s));
+    H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
+    k_near_mr<T><<<h.nleaf, kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
+    H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
+    if (h.ngtask > 0) {
+        GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
+        k_gather_mr<T><<<h.ngtask, kGatherThreads, 0, s>>>(G, (const T *)h.V, xs, t, (T *)h.partial_mr);
+    }
+    if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
+    if (h.nsplit > 0) {
+        SplitArgs S{h.split_box, h.split_ntask, h.split_pbase, h.Rv, h.ldv, h.vcol0, h.map_v};
+        k_reduce_partials_mr<T><<<h.nsplit, 256, 0, s>>>(S, (const T *)h.partial_mr, t);
+    }
+    H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
+    if (ev) H3D_CUDA(cudaEventRecord(ev[3], s));
+    k_leaf_mr<T><<<h.nleaf, kLeafThreads, kLeafDynSmem, s>>>(A, (const T *)h.U, t, nearbuf, y, n, q0, nq);
+    if (ev) H3D_CUDA(cudaEventRecord(ev[4], s));
     H3D_LAUNCH_CHECK();
 }
 
@@ -580,6 +1118,10 @@ void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s, cud
 
 void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     (void)tmp;
+    H3D_CUDA(cudaFuncSetAttribute(k_leaf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
+    H3D_CUDA(cudaFuncSetAttribute(k_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
+    H3D_CUDA(cudaFuncSetAttribute(k_leaf_mr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
+    H3D_CUDA(cudaFuncSetAttribute(k_leaf_mr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
     const int64_t nboxes = h.n_boxes;
     const size_t es = h.elem();
     std::vector<int> Rv(nboxes), ldv(nboxes), bs(nboxes), be(nboxes), R(nboxes), llo(nboxes), lhi(nboxes);
@@ -643,6 +1185,19 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     h.partial = h.mem.alloc((size_t)std::max<int64_t>(pel, 4) * es);
     h.t = h.mem.alloc((size_t)std::max<int64_t>(h.sum_rank, 4) * es);
     h.xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * es);
+    h.nearbuf = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * es);
+    if (h.leaf_size <= kMaxLeafMR) {   // scratch of the multi-RHS product (kNQ columns per pass)
+        h.xs_mr = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQ * es);
+        h.nearbuf_mr = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQ * es);
+        h.t_mr = h.mem.alloc((size_t)std::max<int64_t>(h.sum_rank, 4) * kNQ * es);
+        h.partial_mr = h.mem.alloc((size_t)std::max<int64_t>(pel, 4) * kNQ * es);
+    }
+    // highest priority: the near-field CTAs are dispatched ahead of the gather's
+    int prio_lo = 0, prio_hi = 0;
+    H3D_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    H3D_CUDA(cudaStreamCreateWithPriority(&h.side_stream, cudaStreamNonBlocking, prio_hi));
+    H3D_CUDA(cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming));
+    H3D_CUDA(cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming));
 
     // transpose partials: per level l < L, per leaf z, R of its ancestor
     const int L = h.L, nleaf = h.nleaf;
@@ -675,8 +1230,22 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     H3D_CUDA(cudaStreamSynchronize(s));
 }
 
+int matvec_passes(const Handle &h, int nrhs, bool transpose) {
+    if (nrhs > 1 && !transpose && h.leaf_size <= kMaxLeafMR) return (nrhs + kNQ - 1) / kNQ;
+    return nrhs;
+}
+
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s, cudaEvent_t *ev) {
     const int64_t n = h.N;
+    if (nrhs > 1 && !transpose && h.leaf_size <= kMaxLeafMR) {
+        for (int q0 = 0, b = 0; q0 < nrhs; q0 += kNQ, ++b) {
+            const int nq = std::min(kNQ, nrhs - q0);
+            cudaEvent_t *e = ev ? ev + 5 * b : nullptr;
+            if (h.prec == H3D_FP64) matvec_mr<double>(h, (const double *)x, (double *)y, q0, nq, s, e);
+            else matvec_mr<float>(h, (const float *)x, (float *)y, q0, nq, s, e);
+        }
+        return;
+    }
     for (int c = 0; c < nrhs; ++c) {
         cudaEvent_t *e = ev ? ev + 5 * c : nullptr;
         if (h.prec == H3D_FP64)

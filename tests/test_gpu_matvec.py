@@ -178,3 +178,29 @@ def test_error_statuses():
         A.matvec(torch.zeros(500, dtype=torch.float64, device="cuda"))  # fp32 handle
     # the handle stays usable after a rejected call
     assert np.isfinite(gpu_apply(A, np.ones(500, np.float32))).all()
+
+
+@pytest.mark.parametrize("nrhs", [2, 8, 11])
+def test_multi_rhs_fp64_matches_frozen_oracle(nrhs):
+    # several right-hand sides share one pass over the factors (blocks of 8)
+    pts = I.uniform(15000, 91)
+    A = H(pts, leaf_size=40, tol=1e-8, precision="fp64")
+    o = O.Oracle(pts, leaf_size=40, tol=1e-8).set_pivots(*A.export_pivots())
+    x = I.rhs_normal(15000, nrhs, 92)
+    yg = gpu_apply(A, x)
+    yo = o.matvec(x)
+    assert yg.shape == (15000, nrhs)
+    for c in range(nrhs):
+        assert rel(yg[:, c], yo[:, c]) <= 1e-12
+
+
+def test_multi_rhs_fp32_matches_single_rhs_and_direct():
+    pts = I.uniform(30000, 93)
+    A = H(pts, leaf_size=64, tol=1e-7, precision="fp32")
+    x = I.rhs_normal(30000, 10, 94).astype(np.float32)
+    Y = gpu_apply(A, x)
+    ref = O.direct(pts, x.astype(np.float64))
+    assert rel(Y, ref) <= 1e-6
+    for c in (0, 7, 9):
+        y1 = gpu_apply(A, np.ascontiguousarray(x[:, c]))
+        assert rel(Y[:, c], y1) <= 1e-6
