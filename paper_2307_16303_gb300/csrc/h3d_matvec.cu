@@ -278,14 +278,21 @@ __device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const
             for (int q = 0; q < 4; ++q) {
                 const int i = i0 + q * T_;
                 if (q >= ntg || i >= m) break;
-                for (int j = s; j < cnt; j += S) {
+                auto term = [&](int j) {
                     const float4 sh = srcf[2 * j], sl = srcf[2 * j + 1];
                     const float dx = (th[q].x - sh.x) + (tl[q].x - sl.x);
                     const float dy = (th[q].y - sh.y) + (tl[q].y - sl.y);
                     const float dz = (th[q].z - sh.z) + (tl[q].z - sl.z);
                     const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    acc[q].add(kernel_fast(A.kind, kap, d2) * sh.w);
+                    return kernel_fast(A.kind, kap, d2) * sh.w;
+                };
+                int j = s;
+                // four independent interactions per compensated add (ILP)
+                for (; j + 3 * S < cnt; j += 4 * S) {
+                    const float a0 = term(j), a1 = term(j + S), a2 = term(j + 2 * S), a3 = term(j + 3 * S);
+                    acc[q].add((a0 + a1) + (a2 + a3));
                 }
+                for (; j < cnt; j += S) acc[q].add(term(j));
             }
         }
         p = pe;
