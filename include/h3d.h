@@ -65,6 +65,17 @@ typedef enum {
     H3D_FP32 = 1
 } h3d_precision;
 
+/* Which same-level box pairs are stored as low-rank blocks.  HODLR3D is the
+ * paper's format (Def. admh3d); the other two are its comparison formats on the
+ * same octree: the H-matrix with the strong condition max(diam) <= eta dist,
+ * eta = sqrt(3) (Sec. 2.2, Eq. adm: only pairs sharing no boundary), and HODLR,
+ * which compresses every off-diagonal pair (Sec. 2.3).                       */
+typedef enum {
+    H3D_ADM_HODLR3D = 0,   /* vertex-sharing and well-separated pairs            */
+    H3D_ADM_STRONG = 1,    /* well-separated pairs only (H-matrix, eta = sqrt 3) */
+    H3D_ADM_WEAK = 2       /* every off-diagonal pair (HODLR)                    */
+} h3d_admissibility;
+
 typedef struct {
     int precision;          /* h3d_precision, default H3D_FP32                          */
     double kappa;           /* Yukawa decay, default 1.0                                 */
@@ -72,6 +83,7 @@ typedef struct {
     double lo[3];           /* lower corner of the domain cube, default (-1,-1,-1)       */
     double side;            /* edge length of the domain cube, default 2.0               */
     int64_t workspace_bytes;/* device scratch budget for the build; 0 = automatic        */
+    int admissibility;      /* h3d_admissibility, default H3D_ADM_HODLR3D                */
 } h3d_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -162,8 +174,9 @@ h3d_status h3d_export_tree(h3d_handle h, int64_t *perm, uint64_t *keys, int *nbo
                            uint64_t *box_key, int64_t *box_start, int64_t *box_end);
 
 /* Lists: admissible blocks in (level, target, source) order with level-local
- * box indices and class 3 = vertex, 4 = well separated; near pairs (leaf
- * level) in (target, source) order with class 0 = self, 1 = face, 2 = edge.  */
+ * box indices and class 1 = face, 2 = edge (weak admissibility only), 3 =
+ * vertex, 4 = well separated; near pairs (leaf level) in (target, source) order
+ * with class 0 = self, 1 = face, 2 = edge, 3 = vertex (strong only).        */
 h3d_status h3d_export_lists(h3d_handle h, int *blk_level, int *blk_tgt, int *blk_src, int *blk_cls,
                             int *near_tgt, int *near_src, int *near_cls);
 

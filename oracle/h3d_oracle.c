@@ -16,6 +16,10 @@
  *   - vertex/edge/face neighbours, clan and interaction list        (Table "Notations")
  *   - HODLR3D admissibility: distinct same-level clusters that share
  *     nothing or only a vertex are compressed                       (Definition "admh3d")
+ *   - the paper's comparison formats on the same octree: the H-matrix
+ *     with the strong condition max(diam) <= eta dist, eta = sqrt(3)
+ *     (Sec. 2.2, Eq. adm), and HODLR, which compresses every
+ *     off-diagonal block (Sec. 2.3)
  *   - partially pivoted ACA of every admissible pair, giving pivots
  *     sigma (rows) and tau (columns) with
  *     K(X,Y) ~ K(X,tau) K(sigma,tau)^{-1} K(sigma,Y)                 (Sec. 4.1, Eq. prank)
@@ -59,6 +63,21 @@
 enum { KER_LAPLACE = 0, KER_YUKAWA = 1, KER_INV_R4 = 2, KER_COS_R = 3 };
 enum { ST_OK = 0, ST_ARG = 1, ST_DOMAIN = 2, ST_OOM = 3, ST_RANK = 5, ST_DEPTH = 8 };
 enum { CLS_SELF = 0, CLS_FACE = 1, CLS_EDGE = 2, CLS_VERTEX = 3, CLS_FAR = 4 };
+enum { ADM_HODLR3D = 0, ADM_STRONG = 1, ADM_WEAK = 2 };
+
+/* Is a pair of distinct same-level boxes of class `cls` admissible?
+ *   HODLR3D (Def. admh3d): they share no boundary or only a vertex.
+ *   strong (Eq. adm with eta = sqrt(3)): two cubes of side h have diameter
+ *     h sqrt(3), so the condition holds iff dist >= h, i.e. no shared boundary.
+ *   weak (HODLR): every off-diagonal pair.                                   */
+static int admissible(int cls, int mode)
+{
+    switch (mode) {
+    case ADM_STRONG: return cls == CLS_FAR;
+    case ADM_WEAK:   return cls != CLS_SELF;
+    default:         return cls == CLS_VERTEX || cls == CLS_FAR;
+    }
+}
 
 #define MAX_DEPTH 21
 
@@ -198,7 +217,7 @@ typedef struct {
 typedef struct {
     int kind;
     double kappa, tol, lo[3], side;
-    int leaf_size, rank_cap;
+    int leaf_size, rank_cap, adm;
     int64_t N;
     int L;
     double *pts;          /* sorted points, N x 3                               */
@@ -282,10 +301,12 @@ static int build_lists(h3do_t *h)
                 if (j == i) continue;
                 pj[0] = co[3 * j] >> 1; pj[1] = co[3 * j + 1] >> 1; pj[2] = co[3 * j + 2] >> 1;
                 pc = pair_class(pi, pj);
-                /* clan: siblings, or children of the parent's edge/face neighbours */
-                if (!(pc == CLS_SELF || pc == CLS_FACE || pc == CLS_EDGE)) continue;
+                /* pairs whose parents were admissible are covered by a coarser
+                 * block; for HODLR3D the rest is the clan: siblings and children
+                 * of the parent's edge / face neighbours (Table Notations) */
+                if (admissible(pc, h->adm)) continue;
                 cls = pair_class(co + 3 * i, co + 3 * j);
-                if (cls == CLS_VERTEX || cls == CLS_FAR) {
+                if (admissible(cls, h->adm)) {
                     st |= ivec_push(&bl, l); st |= ivec_push(&bt, i);
                     st |= ivec_push(&bs, j); st |= ivec_push(&bc, cls);
                 }
@@ -303,7 +324,7 @@ static int build_lists(h3do_t *h)
         for (int i = 0; i < nb && st == ST_OK; ++i)
             for (int j = 0; j < nb && st == ST_OK; ++j) {
                 int cls = pair_class(co + 3 * i, co + 3 * j);
-                if (cls == CLS_SELF || cls == CLS_FACE || cls == CLS_EDGE) {
+                if (cls == CLS_SELF || !admissible(cls, h->adm)) {
                     st |= ivec_push(&nt, i); st |= ivec_push(&ns, j); st |= ivec_push(&nc, cls);
                 }
             }
@@ -328,8 +349,17 @@ void h3do_free(h3do_t *h)
 }
 
 /* Build the tree (Alg. 1, first two steps): keys, order, depth, boxes, lists. */
+h3do_t *h3do_create_adm(const double *pts, int64_t N, int kind, double kappa, int leaf_size,
+                        double tol, int rank_cap, const double *lo, double side, int adm, int *status);
+
 h3do_t *h3do_create(const double *pts, int64_t N, int kind, double kappa, int leaf_size,
                     double tol, int rank_cap, const double *lo, double side, int *status)
+{
+    return h3do_create_adm(pts, N, kind, kappa, leaf_size, tol, rank_cap, lo, side, ADM_HODLR3D, status);
+}
+
+h3do_t *h3do_create_adm(const double *pts, int64_t N, int kind, double kappa, int leaf_size,
+                        double tol, int rank_cap, const double *lo, double side, int adm, int *status)
 {
     h3do_t *h;
     kv_t *kv = NULL;
@@ -337,8 +367,10 @@ h3do_t *h3do_create(const double *pts, int64_t N, int kind, double kappa, int le
     int st = ST_OK;
     *status = ST_ARG;
     if (N < 1 || leaf_size < 1 || !(tol >= 0.0) || rank_cap < 1 || kind < 0 || kind > 3) return NULL;
+    if (adm < 0 || adm > 2) return NULL;
     h = (h3do_t *)calloc(1, sizeof(h3do_t));
     if (!h) { *status = ST_OOM; return NULL; }
+    h->adm = adm;
     h->kind = kind; h->kappa = kappa; h->tol = tol; h->leaf_size = leaf_size; h->rank_cap = rank_cap;
     h->N = N; h->side = side;
     for (int d = 0; d < 3; ++d) h->lo[d] = lo[d];

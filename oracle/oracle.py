@@ -11,7 +11,9 @@ Functions and the passage of arXiv 2307.16303 each one follows:
   y_i = sum_{j != i} f(|r_i - r_j|) x_j.
 * :func:`morton` -- Sec. 2.1 recursive subdivision of B = [-1, 1]^3.
 * :class:`Oracle` -- Alg. 1 (tree, interaction lists, ACA pivots, Sec. 4.1
-  Eq. prank) and Alg. 2 (matrix-vector product and its transpose).
+  Eq. prank) and Alg. 2 (matrix-vector product and its transpose); with
+  ``admissibility="strong"`` / ``"weak"`` the paper's comparison formats on the
+  same octree (H-matrix with eta = sqrt(3), Eq. adm; HODLR, Sec. 2.3).
 
 Pins (tests under ``tests/`` marked ``not gpu``) fix each function against
 something other than itself: closed-form potentials of symmetric point sets,
@@ -36,6 +38,7 @@ _SRC = os.path.join(_HERE, "h3d_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libh3d_oracle.so")
 
 KERNELS = {"laplace": 0, "yukawa": 1, "inv_r4": 2, "cos_r": 3}
+ADMISSIBILITY = {"hodlr3d": 0, "strong": 1, "weak": 2}
 STATUS = {0: "ok", 1: "bad argument", 2: "point outside the domain", 3: "out of memory",
           5: "ACA rank cap reached", 8: "tree deeper than 21 levels"}
 CLS_NAMES = {0: "self", 1: "face", 2: "edge", 3: "vertex", 4: "far"}
@@ -77,6 +80,7 @@ def _load():
             "h3do_num_threads": (i32, []),
             "h3do_morton": (i32, [P, i64, P, f64, P]),
             "h3do_create": (P, [P, i64, i32, f64, i32, f64, i32, P, f64, C.POINTER(C.c_int)]),
+            "h3do_create_adm": (P, [P, i64, i32, f64, i32, f64, i32, P, f64, i32, C.POINTER(C.c_int)]),
             "h3do_free": (None, [P]),
             "h3do_depth": (i32, [P]),
             "h3do_num_blocks": (i64, [P]),
@@ -171,17 +175,19 @@ class Oracle:
     """
 
     def __init__(self, points, kernel: str = "laplace", leaf_size: int = 64, tol: float = 1e-7,
-                 rank_cap: int = 512, kappa: float = 1.0, lo=(-1.0, -1.0, -1.0), side: float = 2.0):
+                 rank_cap: int = 512, kappa: float = 1.0, lo=(-1.0, -1.0, -1.0), side: float = 2.0,
+                 admissibility: str = "hodlr3d"):
         lib = _load()
         self.points = np.ascontiguousarray(points, dtype=np.float64)
         self.N = self.points.shape[0]
         lo_a = np.ascontiguousarray(lo, dtype=np.float64)
         st = C.c_int(0)
-        self._h = lib.h3do_create(_ptr(self.points), self.N, KERNELS[kernel], kappa, leaf_size, tol,
-                                  rank_cap, _ptr(lo_a), side, C.byref(st))
+        self._h = lib.h3do_create_adm(_ptr(self.points), self.N, KERNELS[kernel], kappa, leaf_size, tol,
+                                      rank_cap, _ptr(lo_a), side, ADMISSIBILITY[admissibility], C.byref(st))
         if not self._h:
             raise OracleError(st.value)
         self.kernel, self.kappa, self.leaf_size, self.tol = kernel, kappa, leaf_size, tol
+        self.admissibility = admissibility
         self.L = lib.h3do_depth(self._h)
         self.n_blocks = lib.h3do_num_blocks(self._h)
         self.n_near = lib.h3do_num_near(self._h)

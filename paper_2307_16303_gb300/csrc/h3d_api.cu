@@ -50,6 +50,7 @@ void h3d_default_options(h3d_options *opt) {
     opt->lo[0] = opt->lo[1] = opt->lo[2] = -1.0;
     opt->side = 2.0;
     opt->workspace_bytes = 0;
+    opt->admissibility = H3D_ADM_HODLR3D;
 }
 
 const char *h3d_status_string(h3d_status s) {
@@ -81,6 +82,7 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(o.lo[d])) return H3D_ERR_ARG;
     if (!(o.kappa >= 0.0) || !std::isfinite(o.kappa)) return H3D_ERR_ARG;
+    if (o.admissibility < H3D_ADM_HODLR3D || o.admissibility > H3D_ADM_WEAK) return H3D_ERR_ARG;
     if (!is_device_ptr(points)) return H3D_ERR_ARG;
 
     h3d_handle_s *hs = new (std::nothrow) h3d_handle_s;
@@ -91,6 +93,7 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
     h.prec = o.precision;
     h.leaf_size = leaf_size;
     h.rank_cap = o.rank_cap;
+    h.adm = o.admissibility;
     h.tol = tol;
     h.kappa = o.kappa;
     h.side = o.side;

@@ -105,7 +105,7 @@ class Arena {
 struct Handle {
     // parameters
     int64_t N = 0;
-    int kernel = H3D_LAPLACE, prec = H3D_FP32, leaf_size = 0, rank_cap = kMaxRank;
+    int kernel = H3D_LAPLACE, prec = H3D_FP32, leaf_size = 0, rank_cap = kMaxRank, adm = H3D_ADM_HODLR3D;
     double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
     int L = 0;
 

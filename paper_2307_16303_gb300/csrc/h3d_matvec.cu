@@ -551,19 +551,25 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__re
     }
 }
 
-// A6: dense self / face / edge near field of one leaf per CTA, into nearbuf
-// (Morton order).  Runs on a second stream, overlapping the source-side gather.
+// A6: dense self / face / edge near field into nearbuf (Morton order).  A
+// persistent grid of kNearCtasPerSm CTAs per SM walks the leaves; it runs on a
+// high-priority second stream next to the memory-bound source-side gather,
+// taking only a few warp slots per SM so that both proceed together.
+constexpr int kNearCtasPerSm = 2;
+
 template <class T>
 __global__ void __launch_bounds__(kLeafThreads) k_near(LeafArgs A, const T *__restrict__ xs, T *__restrict__ nearbuf) {
     __shared__ T outsm[kMaxLeaf];
     __shared__ T partsm[kLeafThreads];
     __shared__ __align__(16) unsigned char srcbuf[kMaxLeaf * 32];
-    const int z = blockIdx.x;
-    const int Zg = (int)(A.offL + z);
-    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
-    near_field<T>(A, z, zs, m, xs, outsm, reinterpret_cast<float4 *>(srcbuf), reinterpret_cast<Pt4d *>(srcbuf),
-                  partsm);
-    for (int i = threadIdx.x; i < m; i += kLeafThreads) nearbuf[zs + i] = outsm[i];
+    for (int z = blockIdx.x; z < A.nleaf; z += gridDim.x) {
+        const int Zg = (int)(A.offL + z);
+        const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+        near_field<T>(A, z, zs, m, xs, outsm, reinterpret_cast<float4 *>(srcbuf), reinterpret_cast<Pt4d *>(srcbuf),
+                      partsm);
+        for (int i = threadIdx.x; i < m; i += kLeafThreads) nearbuf[zs + i] = outsm[i];
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1062,7 +1068,10 @@ void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s, cud
     // near field on the side stream, overlapping the factor streams
     H3D_CUDA(cudaEventRecord(h.ev_fork, s));
     H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
-    k_near<T><<<h.nleaf, kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
+    // FP32: a small persistent grid that hides under the gather; FP64 (whose near
+    // field is bound by the FP64 pipe, not hidden by anything): every leaf at once
+    const int near_grid = sizeof(T) == 4 ? std::min(h.nleaf, kNearCtasPerSm * num_sms()) : h.nleaf;
+    k_near<T><<<near_grid, kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
     H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
     if (!transpose) {
         if (h.ngtask > 0) {

@@ -190,9 +190,24 @@ __device__ __forceinline__ int pair_class(int dx, int dy, int dz) {
     return (dx != 0) + (dy != 0) + (dz != 0);
 }
 
-// Interaction list of box i at level l (l >= 1): writes up to 151 sorted
-// level-local indices with their class; returns the count.
-__device__ int interaction_list(const uint64_t *__restrict__ bkey, int nb, int level, int i, int *out,
+// Admissibility of two distinct same-level boxes of class cls (0 self, 1 face,
+// 2 edge, 3 vertex, 4 well separated):
+//   HODLR3D (Def. admh3d): vertex or well separated;
+//   strong, eta = sqrt(3) (Eq. adm): well separated only;
+//   weak (HODLR on the octree): every distinct pair.
+__device__ __forceinline__ bool is_admissible(int cls, int mode) {
+    if (mode == H3D_ADM_STRONG) return cls == 4;
+    if (mode == H3D_ADM_WEAK) return cls != 0;
+    return cls == 3 || cls == 4;
+}
+
+// Interaction list of box i at level l (l >= 1): the children of the parent's
+// neighbours whose pair with the parent was not admissible (for HODLR3D the
+// clan: siblings and children of the parent's edge / face neighbours) that are
+// admissible themselves.  Writes up to 215 sorted level-local indices with their
+// class; returns the count.
+constexpr int kMaxIList = 216;
+__device__ int interaction_list(const uint64_t *__restrict__ bkey, int nb, int level, int i, int mode, int *out,
                                 unsigned char *cls_out) {
     int x, y, z;
     box_coords(bkey[i], level, x, y, z);
@@ -202,13 +217,14 @@ __device__ int interaction_list(const uint64_t *__restrict__ bkey, int nb, int l
     for (int dx = -1; dx <= 1; ++dx)
         for (int dy = -1; dy <= 1; ++dy)
             for (int dz = -1; dz <= 1; ++dz) {
-                if ((dx != 0) + (dy != 0) + (dz != 0) == 3) continue;  // parent's vertex neighbours
+                const int pcls = (dx != 0) + (dy != 0) + (dz != 0);
+                if (pcls != 0 && is_admissible(pcls, mode)) continue;  // covered at the parent level
                 const int qx = px + dx, qy = py + dy, qz = pz + dz;
                 if (qx < 0 || qy < 0 || qz < 0 || qx >= np || qy >= np || qz >= np) continue;
                 for (int c = 0; c < 8; ++c) {
                     const int cx = 2 * qx + ((c >> 2) & 1), cy = 2 * qy + ((c >> 1) & 1), cz = 2 * qz + (c & 1);
                     const int cls = pair_class(cx - x, cy - y, cz - z);
-                    if (cls != 3 && cls != 4) continue;
+                    if (cls == 0 || !is_admissible(cls, mode)) continue;
                     const int j = find_box(bkey, nb, box_key_of(cx, cy, cz, level));
                     if (j < 0) continue;
                     if (out) {
@@ -228,20 +244,20 @@ __device__ int interaction_list(const uint64_t *__restrict__ bkey, int nb, int l
     return cnt;
 }
 
-__global__ void k_ilist_count(const uint64_t *__restrict__ bkey, int nb, int level, int *__restrict__ cnt) {
+__global__ void k_ilist_count(const uint64_t *__restrict__ bkey, int nb, int level, int mode, int *__restrict__ cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
-    cnt[i] = interaction_list(bkey, nb, level, i, nullptr, nullptr);
+    cnt[i] = interaction_list(bkey, nb, level, i, mode, nullptr, nullptr);
 }
 
-__global__ void k_ilist_fill(const uint64_t *__restrict__ bkey, int nb, int level, int64_t off_box,
+__global__ void k_ilist_fill(const uint64_t *__restrict__ bkey, int nb, int level, int mode, int64_t off_box,
                              const int64_t *__restrict__ bptr, int *__restrict__ tgt, int *__restrict__ src,
                              unsigned char *__restrict__ cls, unsigned char *__restrict__ lev) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
-    int js[160];
-    unsigned char cs[160];
-    const int n = interaction_list(bkey, nb, level, i, js, cs);
+    int js[kMaxIList];
+    unsigned char cs[kMaxIList];
+    const int n = interaction_list(bkey, nb, level, i, mode, js, cs);
     const int64_t o = bptr[off_box + i];
     for (int k = 0; k < n; ++k) {
         tgt[o + k] = (int)(off_box + i);
@@ -251,8 +267,9 @@ __global__ void k_ilist_fill(const uint64_t *__restrict__ bkey, int nb, int leve
     }
 }
 
-// Near list of leaf i: self, face and edge neighbours, sorted.
-__device__ int near_list(const uint64_t *__restrict__ bkey, int nb, int level, int i, int *out,
+// Near list of leaf i: itself and the neighbours whose pair is not admissible
+// (HODLR3D: self, face and edge neighbours), sorted.
+__device__ int near_list(const uint64_t *__restrict__ bkey, int nb, int level, int i, int mode, int *out,
                          unsigned char *cls_out, unsigned char *dir_out) {
     int x, y, z;
     box_coords(bkey[i], level, x, y, z);
@@ -262,7 +279,7 @@ __device__ int near_list(const uint64_t *__restrict__ bkey, int nb, int level, i
         for (int dy = -1; dy <= 1; ++dy)
             for (int dz = -1; dz <= 1; ++dz) {
                 const int cls = (dx != 0) + (dy != 0) + (dz != 0);
-                if (cls == 3) continue;
+                if (cls != 0 && is_admissible(cls, mode)) continue;
                 const int cx = x + dx, cy = y + dy, cz = z + dz;
                 if (cx < 0 || cy < 0 || cz < 0 || cx >= n1 || cy >= n1 || cz >= n1) continue;
                 const int j = find_box(bkey, nb, box_key_of(cx, cy, cz, level));
@@ -284,19 +301,20 @@ __device__ int near_list(const uint64_t *__restrict__ bkey, int nb, int level, i
     return cnt;
 }
 
-__global__ void k_near_count(const uint64_t *__restrict__ bkey, int nb, int level, int *__restrict__ cnt) {
+__global__ void k_near_count(const uint64_t *__restrict__ bkey, int nb, int level, int mode, int *__restrict__ cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
-    cnt[i] = near_list(bkey, nb, level, i, nullptr, nullptr, nullptr);
+    cnt[i] = near_list(bkey, nb, level, i, mode, nullptr, nullptr, nullptr);
 }
 
-__global__ void k_near_fill(const uint64_t *__restrict__ bkey, int nb, int level, const int64_t *__restrict__ nptr,
-                            int *__restrict__ src, unsigned char *__restrict__ cls, unsigned char *__restrict__ dir) {
+__global__ void k_near_fill(const uint64_t *__restrict__ bkey, int nb, int level, int mode,
+                            const int64_t *__restrict__ nptr, int *__restrict__ src, unsigned char *__restrict__ cls,
+                            unsigned char *__restrict__ dir) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
-    int js[19];
-    unsigned char cs[19], ds[19];
-    const int n = near_list(bkey, nb, level, i, js, cs, ds);
+    int js[27];
+    unsigned char cs[27], ds[27];
+    const int n = near_list(bkey, nb, level, i, mode, js, cs, ds);
     const int64_t o = nptr[i];
     for (int k = 0; k < n; ++k) {
         src[o + k] = js[k];
@@ -444,7 +462,7 @@ void build_lists(Handle &h, cudaStream_t s, Arena &tmp) {
     int *cnt = tmp.get<int>((size_t)nboxes + 1);
     H3D_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)nboxes + 1) * sizeof(int), s));
     for (int l = 1; l <= L; ++l) {
-        k_ilist_count<<<grid_for(h.nbox[l]), kT, 0, s>>>(h.box_key + h.box_off[l], h.nbox[l], l,
+        k_ilist_count<<<grid_for(h.nbox[l]), kT, 0, s>>>(h.box_key + h.box_off[l], h.nbox[l], l, h.adm,
                                                           cnt + h.box_off[l]);
         H3D_LAUNCH_CHECK();
     }
@@ -462,7 +480,8 @@ void build_lists(Handle &h, cudaStream_t s, Arena &tmp) {
     h.blk_lev = h.mem.get<unsigned char>((size_t)std::max<int64_t>(nblk, 1));
     h.blk_partner = h.mem.get<int>((size_t)std::max<int64_t>(nblk, 1));
     for (int l = 1; l <= L; ++l) {
-        k_ilist_fill<<<grid_for(h.nbox[l], 128), 128, 0, s>>>(h.box_key + h.box_off[l], h.nbox[l], l, h.box_off[l],
+        k_ilist_fill<<<grid_for(h.nbox[l], 128), 128, 0, s>>>(h.box_key + h.box_off[l], h.nbox[l], l, h.adm,
+                                                              h.box_off[l],
                                                               h.tgt_ptr, h.blk_tgt, h.blk_src, h.blk_cls, h.blk_lev);
         H3D_LAUNCH_CHECK();
     }
@@ -475,7 +494,7 @@ void build_lists(Handle &h, cudaStream_t s, Arena &tmp) {
     const int64_t offL = h.box_off[L];
     int *ncnt = tmp.get<int>((size_t)nleaf + 1);
     H3D_CUDA(cudaMemsetAsync(ncnt, 0, ((size_t)nleaf + 1) * sizeof(int), s));
-    k_near_count<<<grid_for(nleaf), kT, 0, s>>>(h.box_key + offL, nleaf, L, ncnt);
+    k_near_count<<<grid_for(nleaf), kT, 0, s>>>(h.box_key + offL, nleaf, L, h.adm, ncnt);
     H3D_LAUNCH_CHECK();
     int64_t *nptr64 = tmp.get<int64_t>((size_t)nleaf + 1);
     h.nnear = scan_exclusive(ncnt, nptr64, nleaf + 1, s, tmp);
@@ -485,7 +504,7 @@ void build_lists(Handle &h, cudaStream_t s, Arena &tmp) {
     h.near_src = h.mem.get<int>((size_t)h.nnear);
     h.near_cls = h.mem.get<unsigned char>((size_t)h.nnear);
     h.near_dir = h.mem.get<unsigned char>((size_t)h.nnear);
-    k_near_fill<<<grid_for(nleaf), kT, 0, s>>>(h.box_key + offL, nleaf, L, nptr64, h.near_src, h.near_cls,
+    k_near_fill<<<grid_for(nleaf), kT, 0, s>>>(h.box_key + offL, nleaf, L, h.adm, nptr64, h.near_src, h.near_cls,
                                                  h.near_dir);
     H3D_LAUNCH_CHECK();
     int64_t *nsz = tmp.get<int64_t>((size_t)nleaf + 1);

@@ -204,3 +204,27 @@ def test_multi_rhs_fp32_matches_single_rhs_and_direct():
     for c in (0, 7, 9):
         y1 = gpu_apply(A, np.ascontiguousarray(x[:, c]))
         assert rel(Y[:, c], y1) <= 1e-6
+
+
+@pytest.mark.parametrize("mode", ["strong", "weak"])
+def test_variants_fp64_frozen_and_fp32_error(mode):
+    pts = I.uniform(12000, 95)
+    A = H(pts, leaf_size=40, tol=1e-8, precision="fp64", admissibility=mode)
+    o = O.Oracle(pts, leaf_size=40, tol=1e-8, admissibility=mode).set_pivots(*A.export_pivots())
+    x = I.rhs_normal(12000, 1, 96)[:, 0]
+    assert rel(gpu_apply(A, x), o.matvec(x)) <= 1e-12
+    assert rel(gpu_apply(A, x, transpose=True), o.matvec(x, transpose=True)) <= 1e-12
+    A32 = H(pts, leaf_size=40, tol=1e-7, precision="fp32", admissibility=mode)
+    assert rel(gpu_apply(A32, x.astype(np.float32)), O.direct(pts, x)) <= 1e-6
+
+
+@pytest.mark.parametrize("kern", ["inv_r4", "cos_r"])
+def test_paper_kernels_fp64_frozen(kern):
+    # the paper's other kernels, 1/r^4 and cos(r)/r (Sec. 3.1, Sec. 5.1)
+    pts = I.uniform(6000, 97)
+    A = H(pts, leaf_size=32, tol=1e-8, precision="fp64", kernel=kern)
+    o = O.Oracle(pts, leaf_size=32, tol=1e-8, kernel=kern).set_pivots(*A.export_pivots())
+    x = I.rhs_normal(6000, 1, 98)[:, 0]
+    assert rel(gpu_apply(A, x), o.matvec(x)) <= 1e-12
+    err = rel(gpu_apply(A, x), O.direct(pts, x, kernel=kern))
+    assert err <= 1e-5

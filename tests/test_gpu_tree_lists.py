@@ -54,3 +54,17 @@ def test_lists_bit_exact(built, name):
         assert np.array_equal(g[k], r[k]), k
     s = A.stats()
     assert s["n_blocks"] == o.n_blocks and s["n_near"] == o.n_near
+
+
+@pytest.mark.parametrize("mode", ["strong", "weak"])
+@pytest.mark.parametrize("name", ["grid16", "uniform20k", "sphere", "duplicates"])
+def test_variant_lists_bit_exact(mode, name):
+    # the paper's comparison formats on the same octree (H-matrix eta = sqrt 3, HODLR)
+    import torch
+    from paper_2307_16303_gb300.api import H3DMatrix
+    pts, leaf = {c[0]: (c[1], c[2]) for c in CASES}[name]
+    A = H3DMatrix(torch.from_numpy(pts).cuda(), leaf_size=leaf, tol=1e-5, precision="fp32", admissibility=mode)
+    o = O.Oracle(pts, leaf_size=leaf, tol=1e-5, admissibility=mode)
+    g, r = A.export_lists(), o.lists()
+    for k in ("level", "tgt", "src", "cls", "near_tgt", "near_src", "near_cls"):
+        assert np.array_equal(g[k], r[k]), k

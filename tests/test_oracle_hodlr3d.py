@@ -83,3 +83,24 @@ def test_multiple_rhs_columns_independent():
     Y = o.matvec(X)
     for c in range(3):
         assert np.array_equal(Y[:, c], o.matvec(X[:, c]))
+
+
+@pytest.mark.parametrize("mode", ["strong", "weak"])
+def test_variants_full_rank_equal_dense_and_track_tol(mode):
+    p = I.uniform(2500, 71)
+    x = I.rhs_uniform(2500, 1, 72)[:, 0]
+    y = O.direct(p, x)
+    o = O.Oracle(p, leaf_size=24, tol=0.0, admissibility=mode).compress()
+    assert rel(o.matvec(x), y) <= 1e-12
+    e5 = rel(O.Oracle(p, leaf_size=24, tol=1e-5, admissibility=mode).compress().matvec(x), y)
+    e8 = rel(O.Oracle(p, leaf_size=24, tol=1e-8, admissibility=mode).compress().matvec(x), y)
+    assert e8 < e5 < 1e-3
+
+
+def test_rank_ordering_of_formats():
+    # the paper's Figs. oneOverR_2 etc.: HODLR's maximum rank exceeds HODLR3D's,
+    # which exceeds the strong-admissibility H-matrix's
+    p = I.uniform(8000, 73)
+    mx = {m: O.Oracle(p, leaf_size=32, tol=1e-7, admissibility=m).compress().pivots()[0].max()
+          for m in ("weak", "hodlr3d", "strong")}
+    assert mx["weak"] > mx["hodlr3d"] > mx["strong"]

@@ -164,3 +164,84 @@ def test_lists_symmetric():
     assert fwd == set(zip(li["level"], li["src"], li["tgt"], li["cls"]))
     nf = set(zip(li["near_tgt"], li["near_src"]))
     assert nf == set(zip(li["near_src"], li["near_tgt"]))
+
+
+# --- the paper's comparison formats (H-matrix eta = sqrt(3), HODLR) ---------------
+
+def _strong_admissible(a, b):
+    """Eq. adm with eta = sqrt(3) for unit cubes at integer corners a, b:
+    max(diam) = sqrt(3) <= sqrt(3) * dist  <=>  dist^2 >= 1 (exact in integers)."""
+    dist2 = sum(max(0, abs(a[k] - b[k]) - 1) ** 2 for k in range(3))
+    return dist2 >= 1
+
+
+def _brute_lists_mode(tree, adm):
+    L = tree["L"]
+    off = np.concatenate([[0], np.cumsum(tree["nbox"])])
+    blocks, near = set(), set()
+    for l in range(1, L + 1):
+        keys = [int(k) for k in tree["box_key"][off[l]:off[l + 1]]]
+        co = [_coords(k, l) for k in keys]
+        par = [tuple(c >> 1 for c in p) for p in co]
+        for i in range(len(keys)):
+            for j in range(len(keys)):
+                if i == j:
+                    continue
+                if par[i] != par[j] and adm(par[i], par[j]):
+                    continue   # covered by the parents' block
+                if adm(co[i], co[j]):
+                    blocks.add((l, keys[i], keys[j]))
+    keys = [int(k) for k in tree["box_key"][off[L]:off[L + 1]]]
+    co = [_coords(k, L) for k in keys]
+    for i in range(len(keys)):
+        for j in range(len(keys)):
+            if i == j or not adm(co[i], co[j]):
+                near.add((keys[i], keys[j]))
+    return blocks, near
+
+
+MODES = {"strong": _strong_admissible, "weak": lambda a, b: a != b}
+
+
+@pytest.mark.parametrize("mode", ["strong", "weak"])
+@pytest.mark.parametrize("pts,leaf", [(I.grid(8), 8), (I.uniform(900, 35), 12), (I.sphere(1200, 36) * 0.99, 14)])
+def test_variant_lists_match_definitions(mode, pts, leaf):
+    o = O.Oracle(pts, leaf_size=leaf, admissibility=mode)
+    t, li = o.tree(), o.lists()
+    off = np.concatenate([[0], np.cumsum(t["nbox"])])
+    bk = t["box_key"]
+    blocks = {(int(l), int(bk[off[l] + a]), int(bk[off[l] + b])) for l, a, b in zip(li["level"], li["tgt"], li["src"])}
+    near = {(int(bk[off[o.L] + a]), int(bk[off[o.L] + b])) for a, b in zip(li["near_tgt"], li["near_src"])}
+    bb, bn = _brute_lists_mode(t, MODES[mode])
+    assert blocks == bb and near == bn
+
+
+def test_variant_counts_from_paper_tables():
+    rows = [ln.split() for ln in open(os.path.join(HERE, "golden", "paper_block_counts_variants.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert rows[0] == ["format", "L", "dense", "vertex", "edge_plus_face", "far"]
+    for fmt, L, dense, vert, ef, far in rows[1:]:
+        L = int(L)
+        o = O.Oracle(I.grid(2 ** (L + 1)), leaf_size=8, admissibility=fmt)
+        assert o.L == L
+        li = o.lists()
+        assert o.n_near == int(dense)
+        assert int(np.sum(li["cls"] == 3)) == int(vert)
+        assert int(np.sum((li["cls"] == 1) | (li["cls"] == 2))) == int(ef)
+        assert int(np.sum(li["cls"] == 4)) == int(far)
+
+
+@pytest.mark.parametrize("mode", ["strong", "weak"])
+def test_variant_covers_every_entry_once(mode):
+    pts = I.uniform(600, 37)
+    o = O.Oracle(pts, leaf_size=9, admissibility=mode)
+    t, li = o.tree(), o.lists()
+    off = np.concatenate([[0], np.cumsum(t["nbox"])])
+    cover = np.zeros((600, 600), np.int32)
+    for a, b in zip(li["near_tgt"], li["near_src"]):
+        ia, ib = off[o.L] + a, off[o.L] + b
+        cover[t["box_start"][ia]:t["box_end"][ia], t["box_start"][ib]:t["box_end"][ib]] += 1
+    for l, a, b in zip(li["level"], li["tgt"], li["src"]):
+        ia, ib = off[l] + a, off[l] + b
+        cover[t["box_start"][ia]:t["box_end"][ia], t["box_start"][ib]:t["box_end"][ib]] += 1
+    assert cover.min() == 1 and cover.max() == 1
