@@ -227,8 +227,9 @@ def main():
         phases += np.array(A.matvec_profile(x.data_ptr(), y.data_ptr(), nrhs))
     phases /= a.steps
     # factors are streamed once per pass; a pass covers up to 8 right-hand sides
-    passes = 1 if nrhs == 1 else (nrhs + 7) // 8
-    rhs_per_pass = min(nrhs, 8)
+    per = 32 if (nrhs > 8 and a.leaf <= 128) else 8
+    passes = (nrhs + per - 1) // per
+    rhs_per_pass = min(nrhs, per)
     names = ["k_permute_in", "k_gather", "k_reduce_partials", "k_leaf"]
     s = 4
     N = a.N

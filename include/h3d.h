@@ -110,8 +110,12 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
  * low-rank blocks of every level.
  *   x  device, N x nrhs in the caller's order (read only).
  *   y  device, N x nrhs, overwritten (not accumulated).  Must not alias x.
- *   nrhs >= 1.
- * Allocates nothing; enqueues kernels on `stream` and returns.               */
+ *   nrhs >= 1.  Several right-hand sides share each pass over the factors (up
+ *   to 8 per pass, or 32 for FP32 handles with leaf_size <= 128).
+ * Enqueues kernels on `stream` and returns.  Allocates nothing, except that the
+ * first call with nrhs > 8 on an FP32 handle allocates (and keeps) the scratch
+ * of the 32-column passes after synchronising `stream`; make that first call
+ * before capturing products into a CUDA graph.                               */
 h3d_status h3d_matvec(h3d_handle h, const void *x, void *y, int nrhs, void *stream);
 
 /* y = A~^T x: the same blocks with the roles of the two factors exchanged (the

@@ -120,6 +120,10 @@ struct Handle {
     void *nearbuf = nullptr;                      // near-field result, Morton order (N)
     // multi-RHS scratch: blocks of 8 columns, point-major
     void *xs_mr = nullptr, *nearbuf_mr = nullptr, *t_mr = nullptr, *partial_mr = nullptr;
+    // 32-column FP32 scratch, allocated by the first product with more than 8 columns
+    void *xs_w = nullptr, *nearbuf_w = nullptr, *t_w = nullptr, *partial_w = nullptr;
+    int ntc_items = 0;                            // tensor-core gather work items (task, column block)
+    int2 *tc_items = nullptr;
     ~Handle() {
         if (side_stream) cudaStreamSynchronize(side_stream);
         if (ev_fork) cudaEventDestroy(ev_fork);

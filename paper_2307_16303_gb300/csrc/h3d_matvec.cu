@@ -1033,6 +1033,641 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf_mr(LeafArgs A, const T *_
     }
 }
 
+// ===========================================================================
+// Wide blocks: kNQW = 32 right-hand sides per pass (nrhs > kNQ), FP32, leaves
+// of up to kMaxLeafW points.  One thread owns one factor row / column and all
+// 32 right-hand sides (compensated sums over groups of four products).
+constexpr int kNQW = 32;
+constexpr int kMaxLeafW = 128;
+
+__global__ void k_permute_in_w(const float *__restrict__ x, int64_t n, int q0, int nq, const int *__restrict__ perm,
+                               float *__restrict__ xs) {
+    // thread per (point, rhs): coalesced writes of the point-major block
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * kNQW) return;
+    const int64_t i = e / kNQW;
+    const int q = (int)(e - i * kNQW);
+    xs[e] = q < nq ? x[(int64_t)(q0 + q) * n + perm[i]] : 0.f;
+}
+
+// T_Y(c, :) = sum_r V_Y(r, c) x(r, :) on CUDA cores, one column per thread
+__global__ void __launch_bounds__(kGatherThreads) k_gather_w(GatherArgs G, const float *__restrict__ V,
+                                                             const float *__restrict__ xs, float *__restrict__ t,
+                                                             float *__restrict__ partial) {
+    constexpr int RC = 64;   // rows staged per chunk
+    __shared__ __align__(16) float xsm[RC * kNQW];
+    const int4 task = G.task[blockIdx.x];
+    const int Y = task.x, r0 = task.y, r1 = task.z;
+    const int nrows = r1 - r0;
+    const int ld = G.ldv[Y], RvY = G.Rv[Y];
+    const float *Vb = V + G.vbase[Y] + (int64_t)r0 * ld;
+    const int64_t ys = (int64_t)G.box_start[Y] + r0;
+    const bool direct = task.w != 0;
+    const int64_t pb = G.pbase[blockIdx.x];
+    const int64_t vc0 = G.vcol0[Y];
+    for (int cb = 0; cb < RvY; cb += kGatherThreads) {
+        const int c = cb + threadIdx.x;
+        const bool act = c < RvY;
+        Acc<float> acc[kNQW];
+        for (int rc = 0; rc < nrows; rc += RC) {
+            const int nr = min(RC, nrows - rc);
+            __syncthreads();
+            for (int e = threadIdx.x; e < nr * kNQW; e += kGatherThreads) xsm[e] = xs[(ys + rc) * kNQW + e];
+            __syncthreads();
+            if (act) {
+                const float *p = Vb + (int64_t)rc * ld + c;
+                int r = 0;
+                for (; r + 4 <= nr; r += 4) {
+                    const float a0 = __ldcs(p + (int64_t)r * ld), a1 = __ldcs(p + (int64_t)(r + 1) * ld),
+                                a2 = __ldcs(p + (int64_t)(r + 2) * ld), a3 = __ldcs(p + (int64_t)(r + 3) * ld);
+                    const float4 *x0 = reinterpret_cast<const float4 *>(xsm + r * kNQW);
+#pragma unroll
+                    for (int u = 0; u < kNQW / 4; ++u) {
+                        const float4 b0 = x0[u], b1 = x0[u + kNQW / 4], b2 = x0[u + kNQW / 2], b3 = x0[u + 3 * kNQW / 4];
+                        acc[4 * u + 0].add(a0 * b0.x + a1 * b1.x + a2 * b2.x + a3 * b3.x);
+                        acc[4 * u + 1].add(a0 * b0.y + a1 * b1.y + a2 * b2.y + a3 * b3.y);
+                        acc[4 * u + 2].add(a0 * b0.z + a1 * b1.z + a2 * b2.z + a3 * b3.z);
+                        acc[4 * u + 3].add(a0 * b0.w + a1 * b1.w + a2 * b2.w + a3 * b3.w);
+                    }
+                }
+                for (; r < nr; ++r) {
+                    const float a = __ldcs(p + (int64_t)r * ld);
+#pragma unroll
+                    for (int u = 0; u < kNQW; ++u) acc[u].add(a * xsm[r * kNQW + u]);
+                }
+            }
+        }
+        if (act) {
+            float *o = direct ? t + G.map_v[vc0 + c] * kNQW : partial + (pb + c) * kNQW;
+#pragma unroll
+            for (int u = 0; u < kNQW; u += 4)
+                *reinterpret_cast<float4 *>(o + u) = make_float4(acc[u].get(), acc[u + 1].get(), acc[u + 2].get(),
+                                                                 acc[u + 3].get());
+        }
+    }
+}
+
+__global__ void k_reduce_partials_w(SplitArgs S, const float *__restrict__ partial, float *__restrict__ t) {
+    const int q = blockIdx.x;
+    const int Y = S.box[q], nt = S.ntask[q], ld = S.ldv[Y], R = S.Rv[Y];
+    const int64_t pb = S.pbase[q], vc0 = S.vcol0[Y];
+    for (int e = threadIdx.x; e < R * kNQW; e += blockDim.x) {
+        const int c = e / kNQW, j = e - c * kNQW;
+        float v = 0.f;
+        for (int k = 0; k < nt; ++k) v += partial[(pb + (int64_t)k * ld + c) * kNQW + j];
+        t[S.map_v[vc0 + c] * kNQW + j] = v;
+    }
+}
+
+// near field for 32 right-hand sides: one thread per (target, source group)
+__global__ void __launch_bounds__(kLeafThreads) k_near_w(LeafArgs A, const float *__restrict__ xs,
+                                                         float *__restrict__ nearbuf) {
+    constexpr int CAP = 128;   // staged sources per pass
+    __shared__ __align__(16) float4 srcf[CAP * 2];
+    __shared__ __align__(16) float xsrc[CAP * kNQW];
+    __shared__ float part[kLeafThreads * kNQW / 4];   // reduction in four slices of 8 right-hand sides
+    for (int z = blockIdx.x; z < A.nleaf; z += gridDim.x) {
+        const int Zg = (int)(A.offL + z);
+        const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+        const int T_ = kLeafThreads;
+        const int S = max(1, T_ / m);          // m <= kMaxLeafW = T_
+        const int s = threadIdx.x / m, i = threadIdx.x - s * m;
+        const bool active = s < S;
+        Acc<float> acc[kNQW];
+        const float4 th = active ? A.ploc[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 tl = active ? A.ploc_lo[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float kap = (float)A.kappa;
+        const int p1 = A.near_ptr[z + 1];
+        int p = A.near_ptr[z];
+        while (p < p1) {
+            int pe = p, cnt = 0;
+            while (pe < p1) {
+                const int y = A.near_src[pe];
+                const int nn = A.box_end[A.offL + y] - A.box_start[A.offL + y];
+                if (cnt + nn > CAP && cnt > 0) break;
+                cnt += nn;
+                ++pe;
+            }
+            __syncthreads();
+            int base = 0;
+            for (int pq = p; pq < pe; ++pq) {
+                const int y = A.near_src[pq];
+                const int ys = A.box_start[A.offL + y], nn = A.box_end[A.offL + y] - ys;
+                const int d = A.near_dir[pq];
+                const float sx = (float)((d / 9 - 1) * A.hL), sy = (float)(((d / 3) % 3 - 1) * A.hL),
+                            sz = (float)((d % 3 - 1) * A.hL);
+                for (int j = threadIdx.x; j < nn; j += T_) {
+                    const float4 h = A.ploc[ys + j], l = A.ploc_lo[ys + j];
+                    const float hx = h.x + sx, hy = h.y + sy, hz = h.z + sz;
+                    srcf[2 * (base + j)] = make_float4(hx, hy, hz, 0.f);
+                    srcf[2 * (base + j) + 1] = make_float4((h.x - (hx - sx)) + l.x, (h.y - (hy - sy)) + l.y,
+                                                           (h.z - (hz - sz)) + l.z, 0.f);
+                }
+                for (int e = threadIdx.x; e < nn * kNQW; e += T_) xsrc[base * kNQW + e] = xs[(int64_t)ys * kNQW + e];
+                base += nn;
+            }
+            __syncthreads();
+            if (active) {
+                for (int j = s; j < cnt; j += S) {
+                    const float4 sh = srcf[2 * j], sl = srcf[2 * j + 1];
+                    const float dx = (th.x - sh.x) + (tl.x - sl.x);
+                    const float dy = (th.y - sh.y) + (tl.y - sl.y);
+                    const float dz = (th.z - sh.z) + (tl.z - sl.z);
+                    const float kij = kernel_fast(A.kind, kap, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+                    const float4 *xj = reinterpret_cast<const float4 *>(xsrc + j * kNQW);
+#pragma unroll
+                    for (int u = 0; u < kNQW / 4; ++u) {
+                        const float4 b = xj[u];
+                        acc[4 * u].add(kij * b.x);
+                        acc[4 * u + 1].add(kij * b.y);
+                        acc[4 * u + 2].add(kij * b.z);
+                        acc[4 * u + 3].add(kij * b.w);
+                    }
+                }
+            }
+            p = pe;
+        }
+#pragma unroll
+        for (int sl4 = 0; sl4 < 4; ++sl4) {
+            __syncthreads();
+            if (active)
+#pragma unroll
+                for (int u = 0; u < 8; ++u) part[threadIdx.x * 8 + u] = acc[sl4 * 8 + u].get();
+            __syncthreads();
+            for (int e = threadIdx.x; e < m * 8; e += T_) {
+                const int ii = e / 8, u = e - ii * 8;
+                float v = 0.f;
+                for (int g = 0; g < S; ++g) v += part[(g * m + ii) * 8 + u];
+                nearbuf[(int64_t)(zs + ii) * kNQW + sl4 * 8 + u] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// far field for 32 right-hand sides: U panels through the TMA ring as k_leaf;
+// one thread per (row, column group), all 32 right-hand sides
+__global__ void __launch_bounds__(kLeafThreads) k_leaf_w(LeafArgs A, const float *__restrict__ U,
+                                                         const float *__restrict__ t, const float *__restrict__ nearbuf,
+                                                         float *__restrict__ y, int64_t n, int q0, int nq) {
+    extern __shared__ __align__(128) unsigned char stage[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ ChunkPlan P;
+    __shared__ float red[kLeafThreads * 8];
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+    const int ld = A.leaf_ld[z];                            // <= kMaxLeafW
+    const int cpc = kChunkBytes / (ld * (int)sizeof(float));
+    const int L = A.L;
+    if (threadIdx.x >= 1 && threadIdx.x <= L) {
+        const int l = threadIdx.x;
+        const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
+        const int RA = A.R[Ag];
+        P.panel[l] = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
+        P.tA[l] = t + A.tbase[Ag] * kNQW;
+        P.R[l] = RA;
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kStages; ++q) mbar_init(&bars[q], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int l = 1; l <= L; ++l) {
+            P.first[l] = acc;
+            acc += (P.R[l] + cpc - 1) / cpc;
+        }
+        P.first[L + 1] = acc;
+    }
+    __syncthreads();
+    const int nchunks = P.first[L + 1];
+    int pl = 1;
+    auto issue = [&](int k) {
+        int c0, nc;
+        chunk_of<float>(P, L, k, cpc, pl, c0, nc);
+        const uint32_t bytes = (uint32_t)(nc * ld * (int)sizeof(float));
+        uint64_t *bar = &bars[k % kStages];
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_copy_g2s(stage + (size_t)(k % kStages) * kChunkBytes,
+                      static_cast<const float *>(P.panel[pl]) + (int64_t)c0 * ld, bytes, bar);
+    };
+    if (threadIdx.x == 0)
+        for (int k = 0; k < min(kStages - 1, nchunks); ++k) issue(k);
+    const int Gc = kLeafThreads / ld;
+    const int g = threadIdx.x / ld, i = threadIdx.x - g * ld;
+    Acc<float> acc[kNQW];
+    int cl_level = 1;
+    for (int k = 0; k < nchunks; ++k) {
+        const bool ok = mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                *A.err = H3D_ERR_TIMEOUT;
+                for (int j = k; j < min(k + kStages - 1, nchunks); ++j)
+                    mbar_wait(&bars[j % kStages], (uint32_t)((j / kStages) & 1));
+            }
+            return;
+        }
+        if (threadIdx.x == 0 && k + kStages - 1 < nchunks) issue(k + kStages - 1);
+        int c0, nc;
+        chunk_of<float>(P, L, k, cpc, cl_level, c0, nc);
+        const float *sm = reinterpret_cast<const float *>(stage + (size_t)(k % kStages) * kChunkBytes) + i;
+        const float *tA = static_cast<const float *>(P.tA[cl_level]) + (int64_t)c0 * kNQW;
+        if (g < Gc) {
+            int c = g;
+            for (; c + 3 * Gc < nc; c += 4 * Gc) {
+                const float a0 = sm[c * ld], a1 = sm[(c + Gc) * ld], a2 = sm[(c + 2 * Gc) * ld],
+                            a3 = sm[(c + 3 * Gc) * ld];
+                const float4 *b0 = reinterpret_cast<const float4 *>(tA + (int64_t)c * kNQW);
+                const float4 *b1 = reinterpret_cast<const float4 *>(tA + (int64_t)(c + Gc) * kNQW);
+                const float4 *b2 = reinterpret_cast<const float4 *>(tA + (int64_t)(c + 2 * Gc) * kNQW);
+                const float4 *b3 = reinterpret_cast<const float4 *>(tA + (int64_t)(c + 3 * Gc) * kNQW);
+#pragma unroll
+                for (int u = 0; u < kNQW / 4; ++u) {
+                    const float4 v0 = __ldg(b0 + u), v1 = __ldg(b1 + u), v2 = __ldg(b2 + u), v3 = __ldg(b3 + u);
+                    acc[4 * u].add(a0 * v0.x + a1 * v1.x + a2 * v2.x + a3 * v3.x);
+                    acc[4 * u + 1].add(a0 * v0.y + a1 * v1.y + a2 * v2.y + a3 * v3.y);
+                    acc[4 * u + 2].add(a0 * v0.z + a1 * v1.z + a2 * v2.z + a3 * v3.z);
+                    acc[4 * u + 3].add(a0 * v0.w + a1 * v1.w + a2 * v2.w + a3 * v3.w);
+                }
+            }
+            for (; c < nc; c += Gc) {
+                const float a = sm[c * ld];
+                const float4 *b = reinterpret_cast<const float4 *>(tA + (int64_t)c * kNQW);
+#pragma unroll
+                for (int u = 0; u < kNQW / 4; ++u) {
+                    const float4 v = __ldg(b + u);
+                    acc[4 * u].add(a * v.x);
+                    acc[4 * u + 1].add(a * v.y);
+                    acc[4 * u + 2].add(a * v.z);
+                    acc[4 * u + 3].add(a * v.w);
+                }
+            }
+        }
+    }
+    // reduce over column groups in four slices of 8 right-hand sides
+#pragma unroll
+    for (int sl4 = 0; sl4 < 4; ++sl4) {
+        __syncthreads();
+        if (g < Gc)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) red[(g * ld + i) * 8 + u] = acc[sl4 * 8 + u].get();
+        __syncthreads();
+        for (int e = threadIdx.x; e < m * 8; e += kLeafThreads) {
+            const int ii = e / 8, u = e - ii * 8, q = sl4 * 8 + u;
+            if (q >= nq) continue;
+            float v = 0.f;
+            for (int gg = 0; gg < Gc; ++gg) v += red[(gg * ld + ii) * 8 + u];
+            y[(int64_t)(q0 + q) * n + A.perm[zs + ii]] = v + nearbuf[(int64_t)(zs + ii) * kNQW + q];
+        }
+    }
+}
+
+// ===========================================================================
+// Source-side gather of 32 right-hand sides on the tensor cores (tcgen05,
+// kind::tf32, 3xTF32 split precision):
+//   T_Y(c, q) = sum_r V_Y(r, c) x(r, q)  as  D[M = c][N = q] += A[M][K = r] B[K][N].
+// A work item is one gather task (source box, row range) and a tile of 128
+// columns.  Per K step of 8 rows every thread loads V and x, splits each value
+// into tf32 hi + lo (the tensor core truncates FP32 operands to tf32, so both
+// parts are rounded here) and writes them into K-major core-matrix layout (8 rows
+// x 16 bytes per core matrix; LBO = 128 B along K, SBO = 256 B along M or N) in one
+// of two shared-memory buffers; one thread issues the MMAs and commits them to the
+// buffer's mbarrier, which the threads wait on (bounded) before refilling it.
+// Accumulation: the tensor core's FP32 accumulation is biased (its error grows
+// about one ulp per accumulated MMA), so the main products hi*hi go to one of two
+// TMEM accumulators that is restarted every kTcGroup K steps and drained into a
+// compensated FP32 sum in registers while the other one is filled; the small
+// corrections hi*lo + lo*hi (2^-11 of the main term) accumulate in a third TMEM
+// accumulator over the whole item.  The CTAs are persistent and keep their TMEM
+// allocation for the whole launch.
+constexpr int kTcThreads = 128;
+constexpr int kTcGroup = 4;                           // K steps per drained accumulator
+constexpr int kTcAOp = 4096;                          // one A operand: 128 rows x 8 k, tf32
+constexpr int kTcBOp = 1024;                          // one B operand: 32 columns x 8 k
+constexpr int kTcBuf = 2 * kTcAOp + 2 * kTcBOp;       // hi and lo of A and B
+constexpr size_t kTcDynSmem = 2 * (size_t)kTcBuf + 128;
+constexpr int kTcCtasPerSm = 3;
+constexpr int kTcCols = 128;
+
+__global__ void __launch_bounds__(kTcThreads) k_gather_tc(GatherArgs G, const int2 *__restrict__ items, int nitems,
+                                                          const float *__restrict__ V, const float *__restrict__ xs,
+                                                          float *__restrict__ t, float *__restrict__ partial,
+                                                          int *err) {
+    extern __shared__ unsigned char dsm_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    unsigned char *dsm = dsm_raw + ((128 - (smem_addr(dsm_raw) & 127)) & 127);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tmem_alloc(&tmem_base, 128);   // main[0], main[1], corrections, unused
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t tlane = (uint32_t)(warp << 5) << 16;   // this warp's TMEM lanes
+    const uint32_t idesc = umma_idesc_tf32(128, kNQW);
+    uint32_t issued[2] = {0u, 0u}, waited[2] = {0u, 0u};
+    int step = 0;
+    bool failed = false;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 w = items[it];
+        const int4 task = G.task[w.x];
+        const int Y = task.x, r0 = task.y, r1 = task.z;
+        const int ld = G.ldv[Y], RvY = G.Rv[Y];
+        const int c_lo = w.y * kTcCols;
+        const int ncols = min(kTcCols, RvY - c_lo);
+        const float *Vb = V + G.vbase[Y] + (int64_t)r0 * ld + c_lo;
+        const int64_t xrow0 = (int64_t)G.box_start[Y] + r0;
+        const int nrows = r1 - r0;
+        const int nsteps = (nrows + 7) >> 3;
+        const int ngroups = (nsteps + kTcGroup - 1) / kTcGroup;
+        Acc<float> acc[kNQW];
+        auto drain = [&](int grp) {   // add main accumulator of group grp into the register sums
+            float v[32];
+            tmem_ld32(tmem + tlane + 32u * (uint32_t)(grp & 1), v);
+#pragma unroll
+            for (int q = 0; q < kNQW; ++q) acc[q].add(v[q]);
+        };
+        for (int s = 0; s < nsteps; ++s, ++step) {
+            const int b = step & 1;
+            unsigned char *buf = dsm + b * kTcBuf;
+            if (issued[b] != waited[b]) {   // the MMAs that read this buffer must be done
+                const bool ok = mbar_wait(&mbar[b], waited[b] & 1u);
+                ++waited[b];
+                if (__syncthreads_or(!ok)) { failed = true; break; }
+                tc_fence_after();
+            }
+            const int grp = s / kTcGroup;
+            // the accumulator this group reuses held group grp-2, complete by now
+            if (s % kTcGroup == 0 && grp >= 2) drain(grp - 2);
+            const int rk = s << 3;
+            {   // A: 8 rows x 128 columns of V, one column per thread
+                const bool colok = tid < ncols;
+                float hi[8], lo[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int r = rk + k;
+                    const float v = (colok && r < nrows) ? __ldcs(Vb + (int64_t)r * ld + tid) : 0.f;
+                    split_tf32(v, hi[k], lo[k]);
+                }
+                unsigned char *ah = buf + ((tid >> 3) << 8) + ((tid & 7) << 4);
+                *reinterpret_cast<float4 *>(ah) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<float4 *>(ah + 128) = make_float4(hi[4], hi[5], hi[6], hi[7]);
+                *reinterpret_cast<float4 *>(ah + kTcAOp) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                *reinterpret_cast<float4 *>(ah + kTcAOp + 128) = make_float4(lo[4], lo[5], lo[6], lo[7]);
+            }
+            {   // B: 8 rows x 32 right-hand sides of x, two values per thread
+                const int n = tid & 31, k0 = (tid >> 5) << 1;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const int k = k0 + kk, r = rk + k;
+                    const float v = r < nrows ? xs[(xrow0 + r) * kNQW + n] : 0.f;
+                    float h, l;
+                    split_tf32(v, h, l);
+                    const int off = ((n >> 3) << 8) + ((k >> 2) << 7) + ((n & 7) << 4) + ((k & 3) << 2);
+                    *reinterpret_cast<float *>(buf + 2 * kTcAOp + off) = h;
+                    *reinterpret_cast<float *>(buf + 2 * kTcAOp + kTcBOp + off) = l;
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                const uint32_t abase = smem_addr(buf), bbase = abase + 2 * kTcAOp;
+                const uint64_t ahd = umma_desc(abase, 128, 256), ald = umma_desc(abase + kTcAOp, 128, 256);
+                const uint64_t bh = umma_desc(bbase, 128, 256), bl = umma_desc(bbase + kTcBOp, 128, 256);
+                umma_tf32(tmem + 32u * (uint32_t)(grp & 1), ahd, bh, idesc, s % kTcGroup ? 1u : 0u);
+                umma_tf32(tmem + 64u, ahd, bl, idesc, s > 0 ? 1u : 0u);
+                umma_tf32(tmem + 64u, ald, bh, idesc, 1u);
+                umma_commit(&mbar[b]);
+            }
+            ++issued[b];
+        }
+        if (failed) break;
+        bool ok = true;
+        for (int bb = 0; bb < 2; ++bb)
+            while (waited[bb] != issued[bb]) {
+                ok = mbar_wait(&mbar[bb], waited[bb] & 1u) && ok;
+                ++waited[bb];
+            }
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        tc_fence_after();
+        if (ngroups >= 2) drain(ngroups - 2);
+        drain(ngroups - 1);
+        {
+            float v[32];
+            tmem_ld32(tmem + tlane + 64u, v);
+#pragma unroll
+            for (int q = 0; q < kNQW; ++q) acc[q].add(v[q]);
+        }
+        const int m = (warp << 5) + lane;
+        if (m < ncols) {
+            const int c = c_lo + m;
+            float *o = task.w ? t + G.map_v[G.vcol0[Y] + c] * kNQW : partial + (G.pbase[w.x] + c) * kNQW;
+#pragma unroll
+            for (int q = 0; q < kNQW; q += 4)
+                *reinterpret_cast<float4 *>(o + q) =
+                    make_float4(acc[q].get(), acc[q + 1].get(), acc[q + 2].get(), acc[q + 3].get());
+        }
+        tc_fence_before();
+        __syncthreads();   // accumulators read before the next item overwrites them
+        tc_fence_after();
+    }
+    if (failed && tid == 0) *err = H3D_ERR_TIMEOUT;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// Far field of one leaf for 32 right-hand sides on the tensor cores:
+//   y(rows, q) = sum over levels of U_panel(rows, c) t_A(c, q)
+// as D[M = 128 rows (the leaf's rows, the rest zero)][N = 32] += A[M][K = c] B[K][N].
+// The U panels arrive through the same TMA ring as in k_leaf; per K step of 8
+// columns the threads split U (transposed into K-major) and t into tf32 hi + lo
+// operands; accumulation as in k_gather_tc (drained main accumulators, one
+// correction accumulator).  Then far + near in the caller's order.
+constexpr size_t kLeafTcDynSmem = kLeafDynSmem + 2 * (size_t)kTcBuf + 128;
+
+__global__ void __launch_bounds__(kTcThreads) k_leaf_tc(LeafArgs A, const float *__restrict__ U,
+                                                        const float *__restrict__ t, const float *__restrict__ nearbuf,
+                                                        float *__restrict__ y, int64_t n, int q0, int nq) {
+    extern __shared__ __align__(128) unsigned char stage[];   // TMA ring, then the operand buffers
+    __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ ChunkPlan P;
+    __shared__ uint32_t tmem_base;
+    unsigned char *ops_raw = stage + kLeafDynSmem;
+    unsigned char *ops = ops_raw + ((128 - (smem_addr(ops_raw) & 127)) & 127);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
+    const int ld = A.leaf_ld[z];                               // <= kMaxLeafW = 128
+    const int cpc = kChunkBytes / (ld * (int)sizeof(float));
+    const int L = A.L;
+    if (warp == 0) tmem_alloc(&tmem_base, 128);
+    if (tid >= 1 && tid <= L) {
+        const int l = tid;
+        const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
+        const int RA = A.R[Ag];
+        P.panel[l] = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
+        P.tA[l] = t + A.tbase[Ag] * kNQW;
+        P.R[l] = RA;
+    }
+    if (tid == 0) {
+        for (int q = 0; q < kStages; ++q) mbar_init(&bars[q], 1);
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_fence_init();
+    }
+    // rows >= ld of the A operands stay zero
+    for (int e = tid; e < 2 * kTcBuf / 16; e += kTcThreads)
+        reinterpret_cast<float4 *>(ops)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+        int acc = 0;
+        for (int l = 1; l <= L; ++l) {
+            P.first[l] = acc;
+            acc += (P.R[l] + cpc - 1) / cpc;
+        }
+        P.first[L + 1] = acc;
+    }
+    __syncthreads();
+    const uint32_t tmem = tmem_base;
+    const uint32_t tlane = (uint32_t)(warp << 5) << 16;
+    const uint32_t idesc = umma_idesc_tf32(128, kNQW);
+    const int nchunks = P.first[L + 1];
+    int pl = 1;
+    auto issue = [&](int k) {
+        int c0, nc;
+        chunk_of<float>(P, L, k, cpc, pl, c0, nc);
+        const uint32_t bytes = (uint32_t)(nc * ld * (int)sizeof(float));
+        uint64_t *bar = &bars[k % kStages];
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_copy_g2s(stage + (size_t)(k % kStages) * kChunkBytes,
+                      static_cast<const float *>(P.panel[pl]) + (int64_t)c0 * ld, bytes, bar);
+    };
+    if (tid == 0)
+        for (int k = 0; k < min(kStages - 1, nchunks); ++k) issue(k);
+    Acc<float> acc[kNQW];
+    auto drain = [&](int grp) {
+        float v[32];
+        tmem_ld32(tmem + tlane + 32u * (uint32_t)(grp & 1), v);
+#pragma unroll
+        for (int q = 0; q < kNQW; ++q) acc[q].add(v[q]);
+    };
+    uint32_t issued[2] = {0u, 0u}, waited[2] = {0u, 0u};
+    int s = 0, cl_level = 1;
+    bool failed = false;
+    for (int k = 0; k < nchunks && !failed; ++k) {
+        const bool okc = mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
+        if (__syncthreads_or(!okc)) { failed = true; break; }
+        if (tid == 0 && k + kStages - 1 < nchunks) issue(k + kStages - 1);
+        int c0, nc;
+        chunk_of<float>(P, L, k, cpc, cl_level, c0, nc);
+        const float *sm = reinterpret_cast<const float *>(stage + (size_t)(k % kStages) * kChunkBytes);
+        const float *tA = static_cast<const float *>(P.tA[cl_level]) + (int64_t)c0 * kNQW;
+        const int nks = (nc + 7) >> 3;
+        for (int ks = 0; ks < nks; ++ks, ++s) {
+            const int b = s & 1;
+            unsigned char *buf = ops + b * kTcBuf;
+            if (issued[b] != waited[b]) {
+                const bool ok = mbar_wait(&mbar[b], waited[b] & 1u);
+                ++waited[b];
+                if (__syncthreads_or(!ok)) { failed = true; break; }
+                tc_fence_after();
+            }
+            const int grp = s / kTcGroup;
+            if (s % kTcGroup == 0 && grp >= 2) drain(grp - 2);
+            const int cb = ks << 3;
+            if (tid < ld) {   // A: row tid, 8 columns
+                float hi[8], lo[8];
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const int c = cb + kk;
+                    split_tf32(c < nc ? sm[c * ld + tid] : 0.f, hi[kk], lo[kk]);
+                }
+                unsigned char *ah = buf + ((tid >> 3) << 8) + ((tid & 7) << 4);
+                *reinterpret_cast<float4 *>(ah) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<float4 *>(ah + 128) = make_float4(hi[4], hi[5], hi[6], hi[7]);
+                *reinterpret_cast<float4 *>(ah + kTcAOp) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+                *reinterpret_cast<float4 *>(ah + kTcAOp + 128) = make_float4(lo[4], lo[5], lo[6], lo[7]);
+            }
+            {   // B: 8 columns x 32 right-hand sides of t, two values per thread
+                const int nn = tid & 31, k0 = (tid >> 5) << 1;
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const int kq = k0 + kk, c = cb + kq;
+                    const float v = c < nc ? __ldg(tA + (int64_t)c * kNQW + nn) : 0.f;
+                    float h, l;
+                    split_tf32(v, h, l);
+                    const int off = ((nn >> 3) << 8) + ((kq >> 2) << 7) + ((nn & 7) << 4) + ((kq & 3) << 2);
+                    *reinterpret_cast<float *>(buf + 2 * kTcAOp + off) = h;
+                    *reinterpret_cast<float *>(buf + 2 * kTcAOp + kTcBOp + off) = l;
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                const uint32_t abase = smem_addr(buf), bbase = abase + 2 * kTcAOp;
+                const uint64_t ahd = umma_desc(abase, 128, 256), ald = umma_desc(abase + kTcAOp, 128, 256);
+                const uint64_t bh = umma_desc(bbase, 128, 256), bl = umma_desc(bbase + kTcBOp, 128, 256);
+                umma_tf32(tmem + 32u * (uint32_t)(grp & 1), ahd, bh, idesc, s % kTcGroup ? 1u : 0u);
+                umma_tf32(tmem + 64u, ahd, bl, idesc, s > 0 ? 1u : 0u);
+                umma_tf32(tmem + 64u, ald, bh, idesc, 1u);
+                umma_commit(&mbar[b]);
+            }
+            ++issued[b];
+        }
+    }
+    if (!failed) {
+        bool ok = true;
+        for (int bb = 0; bb < 2; ++bb)
+            while (waited[bb] != issued[bb]) {
+                ok = mbar_wait(&mbar[bb], waited[bb] & 1u) && ok;
+                ++waited[bb];
+            }
+        failed = __syncthreads_or(!ok);
+    }
+    if (!failed) {
+        tc_fence_after();
+        if (s > 0) {
+            const int ngroups = (s + kTcGroup - 1) / kTcGroup;
+            if (ngroups >= 2) drain(ngroups - 2);
+            drain(ngroups - 1);
+            float v[32];
+            tmem_ld32(tmem + tlane + 64u, v);
+#pragma unroll
+            for (int q = 0; q < kNQW; ++q) acc[q].add(v[q]);
+        }
+        const int i = tid;
+        if (i < m) {
+            const int64_t o = A.perm[zs + i];
+#pragma unroll
+            for (int q = 0; q < kNQW; ++q)
+                if (q < nq) y[(int64_t)(q0 + q) * n + o] = acc[q].get() + nearbuf[(int64_t)(zs + i) * kNQW + q];
+        }
+    } else if (tid == 0) {
+        *A.err = H3D_ERR_TIMEOUT;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
 unsigned gridn(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 LeafArgs leaf_args(const Handle &h) {
@@ -1102,6 +1737,50 @@ void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s, cud
     H3D_LAUNCH_CHECK();
 }
 
+void matvec_wide(Handle &h, const float *x, float *y, int q0, int nq, cudaStream_t s, cudaEvent_t *ev) {
+    const int64_t n = h.N;
+    float *xs = (float *)h.xs_w, *t = (float *)h.t_w, *nearbuf = (float *)h.nearbuf_w;
+    if (ev) H3D_CUDA(cudaEventRecord(ev[0], s));
+    k_permute_in_w<<<gridn(n * kNQW, 256), 256, 0, s>>>(x, n, q0, nq, h.perm, xs);
+    if (ev) H3D_CUDA(cudaEventRecord(ev[1], s));
+    LeafArgs A = leaf_args(h);
+    H3D_CUDA(cudaEventRecord(h.ev_fork, s));
+    H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
+    k_near_w<<<std::min(h.nleaf, 2 * kNearCtasPerSm * num_sms()), kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
+    H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
+    if (h.ntc_items > 0) {
+        GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
+        const int grid = std::min(h.ntc_items, kTcCtasPerSm * num_sms());
+        k_gather_tc<<<grid, kTcThreads, kTcDynSmem, s>>>(G, h.tc_items, h.ntc_items, (const float *)h.V, xs, t,
+                                                         (float *)h.partial_w, h.d_async_err);
+    }
+    if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
+    if (h.nsplit > 0) {
+        SplitArgs S{h.split_box, h.split_ntask, h.split_pbase, h.Rv, h.ldv, h.vcol0, h.map_v};
+        k_reduce_partials_w<<<h.nsplit, 256, 0, s>>>(S, (const float *)h.partial_w, t);
+    }
+    H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
+    if (ev) H3D_CUDA(cudaEventRecord(ev[3], s));
+    k_leaf_tc<<<h.nleaf, kTcThreads, kLeafTcDynSmem, s>>>(A, (const float *)h.U, t, nearbuf, y, n, q0, nq);
+    if (ev) H3D_CUDA(cudaEventRecord(ev[4], s));
+    H3D_LAUNCH_CHECK();
+}
+
+// scratch of the 32-column path, allocated by the first product that needs it
+void ensure_wide_scratch(Handle &h, cudaStream_t s) {
+    if (h.xs_w) return;
+    H3D_CUDA(cudaStreamSynchronize(s));
+    const size_t es = sizeof(float);
+    h.xs_w = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQW * es);
+    h.nearbuf_w = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQW * es);
+    h.t_w = h.mem.alloc((size_t)std::max<int64_t>(h.sum_rank, 4) * kNQW * es);
+    h.partial_w = h.mem.alloc((size_t)std::max<int64_t>(h.partial_elems, 4) * kNQW * es);
+}
+
+bool use_wide(const Handle &h, int nrhs, bool transpose) {
+    return nrhs > kNQ && !transpose && h.prec == H3D_FP32 && h.leaf_size <= kMaxLeafW;
+}
+
 template <class T>
 void matvec_mr(Handle &h, const T *x, T *y, int q0, int nq, cudaStream_t s, cudaEvent_t *ev) {
     const int64_t n = h.N;
@@ -1138,6 +1817,9 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     H3D_CUDA(cudaFuncSetAttribute(k_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
     H3D_CUDA(cudaFuncSetAttribute(k_leaf_mr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
     H3D_CUDA(cudaFuncSetAttribute(k_leaf_mr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
+    H3D_CUDA(cudaFuncSetAttribute(k_leaf_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
+    H3D_CUDA(cudaFuncSetAttribute(k_gather_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcDynSmem));
+    H3D_CUDA(cudaFuncSetAttribute(k_leaf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafTcDynSmem));
     const int64_t nboxes = h.n_boxes;
     const size_t es = h.elem();
     std::vector<int> Rv(nboxes), ldv(nboxes), bs(nboxes), be(nboxes), R(nboxes), llo(nboxes), lhi(nboxes);
@@ -1185,6 +1867,18 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     if (!tasks.empty()) {
         H3D_CUDA(cudaMemcpyAsync(h.gtask, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
         H3D_CUDA(cudaMemcpyAsync(h.gtask_pbase, pbase.data(), pbase.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
+    // tensor-core gather work items: (task, block of kTcCols columns)
+    {
+        std::vector<int2> items;
+        for (size_t q = 0; q < tasks.size(); ++q) {
+            const int nb = (Rv[tasks[q].x] + kTcCols - 1) / kTcCols;
+            for (int cb = 0; cb < nb; ++cb) items.push_back(make_int2((int)q, cb));
+        }
+        h.ntc_items = (int)items.size();
+        h.tc_items = h.mem.get<int2>(std::max<size_t>(items.size(), 1));
+        if (!items.empty())
+            H3D_CUDA(cudaMemcpyAsync(h.tc_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     }
     h.nsplit = (int)sbox.size();
     h.split_box = h.mem.get<int>(std::max<size_t>(sbox.size(), 1));
@@ -1247,12 +1941,19 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
 }
 
 int matvec_passes(const Handle &h, int nrhs, bool transpose) {
+    if (use_wide(h, nrhs, transpose)) return (nrhs + kNQW - 1) / kNQW;
     if (nrhs > 1 && !transpose && h.leaf_size <= kMaxLeafMR) return (nrhs + kNQ - 1) / kNQ;
     return nrhs;
 }
 
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s, cudaEvent_t *ev) {
     const int64_t n = h.N;
+    if (use_wide(h, nrhs, transpose)) {
+        ensure_wide_scratch(h, s);
+        for (int q0 = 0, b = 0; q0 < nrhs; q0 += kNQW, ++b)
+            matvec_wide(h, (const float *)x, (float *)y, q0, std::min(kNQW, nrhs - q0), s, ev ? ev + 5 * b : nullptr);
+        return;
+    }
     if (nrhs > 1 && !transpose && h.leaf_size <= kMaxLeafMR) {
         for (int q0 = 0, b = 0; q0 < nrhs; q0 += kNQ, ++b) {
             const int nq = std::min(kNQ, nrhs - q0);

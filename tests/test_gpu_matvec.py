@@ -228,3 +228,16 @@ def test_paper_kernels_fp64_frozen(kern):
     assert rel(gpu_apply(A, x), o.matvec(x)) <= 1e-12
     err = rel(gpu_apply(A, x), O.direct(pts, x, kernel=kern))
     assert err <= 1e-5
+
+
+def test_wide_blocks_of_32_columns():
+    # more than 8 columns on an FP32 handle: passes of 32 right-hand sides (the
+    # last one partial), checked column by column against the one-column product
+    pts = I.uniform(25000, 99)
+    A = H(pts, leaf_size=64, tol=1e-7, precision="fp32")
+    x = I.rhs_normal(25000, 40, 100).astype(np.float32)
+    Y = gpu_apply(A, x)
+    ref = O.direct(pts, x[:, :3].astype(np.float64))
+    assert rel(Y[:, :3], ref) <= 1e-6
+    for c in (0, 17, 31, 32, 39):
+        assert rel(Y[:, c], gpu_apply(A, np.ascontiguousarray(x[:, c]))) <= 1e-6
