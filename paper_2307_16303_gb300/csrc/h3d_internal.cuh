@@ -102,6 +102,17 @@ class Arena {
 
 // ----------------------------------------------------------------------------
 // the handle
+// One tensor-core gather work item: rows [r0, r0 + nrows) of source box Y's V
+// factor, columns [c_lo, c_lo + 128), against 32 right-hand sides.  The V tile is
+// read through box Y's 2-D TMA tensor map.
+struct TcGatherItem {
+    int64_t x;                // first row of the permuted right-hand sides
+    int64_t o;                // first output row: map_v offset (to t) or partial row (to partial)
+    int tmap;                 // tensor map of the box's V factor
+    int c_lo, r0;             // first column and row (within the box) of the tile
+    int nrows, ncols, to_t;   // rows, valid columns, output kind
+};
+
 struct Handle {
     // parameters
     int64_t N = 0;
@@ -122,8 +133,16 @@ struct Handle {
     void *xs_mr = nullptr, *nearbuf_mr = nullptr, *t_mr = nullptr, *partial_mr = nullptr;
     // 32-column FP32 scratch, allocated by the first product with more than 8 columns
     void *xs_w = nullptr, *nearbuf_w = nullptr, *t_w = nullptr, *partial_w = nullptr;
-    int ntc_items = 0;                            // tensor-core gather work items (task, column block)
-    int2 *tc_items = nullptr;
+    // tensor-core (32-column) work lists, resolved at plan time
+    int ntc_items = 0;                            // gather: (task, block of 128 columns)
+    struct TcGatherItem *tc_items = nullptr;
+    int nsplit_w = 0;                             // gather: boxes split into row tasks (32-column path)
+    int *split_box_w = nullptr, *split_ntask_w = nullptr;
+    int64_t *split_pbase_w = nullptr;
+    int64_t partial_elems_w = 0;
+    void *tc_tmaps = nullptr;                     // gather: one 2-D tensor map (CUtensorMap) per source box
+    int ntc_tiles = 0;                            // far field: sibling leaves packed into 128 rows
+    int2 *tc_tiles = nullptr;                     // (first leaf, number of leaves)
     ~Handle() {
         if (side_stream) cudaStreamSynchronize(side_stream);
         if (ev_fork) cudaEventDestroy(ev_fork);

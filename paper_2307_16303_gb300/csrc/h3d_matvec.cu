@@ -19,6 +19,9 @@
 //   V rows of every ancestor source box times t'       (k_leafT)
 #include <algorithm>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "h3d_async.cuh"
 #include "h3d_internal.cuh"
 
@@ -30,6 +33,9 @@ constexpr int kGatherThreads = 256;
 constexpr int kLeafThreads = 128;
 constexpr int64_t kTaskElems = 1 << 18;   // factor entries streamed by one gather task
 constexpr int kTaskMaxRows = 2048;
+// 32-column path: rows per gather task (the partial sums of split boxes cost
+// 32 columns of traffic each, so its tasks are tall)
+constexpr int kTaskRowsW = 4096;
 
 struct __align__(16) Pt4d {
     double x, y, z, w;
@@ -1035,8 +1041,9 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf_mr(LeafArgs A, const T *_
 
 // ===========================================================================
 // Wide blocks: kNQW = 32 right-hand sides per pass (nrhs > kNQ), FP32, leaves
-// of up to kMaxLeafW points.  One thread owns one factor row / column and all
-// 32 right-hand sides (compensated sums over groups of four products).
+// of up to kMaxLeafW points.  Right-hand sides, t and the near field are kept
+// point-major (32 values per point / column); the factor products run on the
+// tensor cores (k_tc_stream below), the near field on CUDA cores.
 constexpr int kNQW = 32;
 constexpr int kMaxLeafW = 128;
 
@@ -1048,63 +1055,6 @@ __global__ void k_permute_in_w(const float *__restrict__ x, int64_t n, int q0, i
     const int64_t i = e / kNQW;
     const int q = (int)(e - i * kNQW);
     xs[e] = q < nq ? x[(int64_t)(q0 + q) * n + perm[i]] : 0.f;
-}
-
-// T_Y(c, :) = sum_r V_Y(r, c) x(r, :) on CUDA cores, one column per thread
-__global__ void __launch_bounds__(kGatherThreads) k_gather_w(GatherArgs G, const float *__restrict__ V,
-                                                             const float *__restrict__ xs, float *__restrict__ t,
-                                                             float *__restrict__ partial) {
-    constexpr int RC = 64;   // rows staged per chunk
-    __shared__ __align__(16) float xsm[RC * kNQW];
-    const int4 task = G.task[blockIdx.x];
-    const int Y = task.x, r0 = task.y, r1 = task.z;
-    const int nrows = r1 - r0;
-    const int ld = G.ldv[Y], RvY = G.Rv[Y];
-    const float *Vb = V + G.vbase[Y] + (int64_t)r0 * ld;
-    const int64_t ys = (int64_t)G.box_start[Y] + r0;
-    const bool direct = task.w != 0;
-    const int64_t pb = G.pbase[blockIdx.x];
-    const int64_t vc0 = G.vcol0[Y];
-    for (int cb = 0; cb < RvY; cb += kGatherThreads) {
-        const int c = cb + threadIdx.x;
-        const bool act = c < RvY;
-        Acc<float> acc[kNQW];
-        for (int rc = 0; rc < nrows; rc += RC) {
-            const int nr = min(RC, nrows - rc);
-            __syncthreads();
-            for (int e = threadIdx.x; e < nr * kNQW; e += kGatherThreads) xsm[e] = xs[(ys + rc) * kNQW + e];
-            __syncthreads();
-            if (act) {
-                const float *p = Vb + (int64_t)rc * ld + c;
-                int r = 0;
-                for (; r + 4 <= nr; r += 4) {
-                    const float a0 = __ldcs(p + (int64_t)r * ld), a1 = __ldcs(p + (int64_t)(r + 1) * ld),
-                                a2 = __ldcs(p + (int64_t)(r + 2) * ld), a3 = __ldcs(p + (int64_t)(r + 3) * ld);
-                    const float4 *x0 = reinterpret_cast<const float4 *>(xsm + r * kNQW);
-#pragma unroll
-                    for (int u = 0; u < kNQW / 4; ++u) {
-                        const float4 b0 = x0[u], b1 = x0[u + kNQW / 4], b2 = x0[u + kNQW / 2], b3 = x0[u + 3 * kNQW / 4];
-                        acc[4 * u + 0].add(a0 * b0.x + a1 * b1.x + a2 * b2.x + a3 * b3.x);
-                        acc[4 * u + 1].add(a0 * b0.y + a1 * b1.y + a2 * b2.y + a3 * b3.y);
-                        acc[4 * u + 2].add(a0 * b0.z + a1 * b1.z + a2 * b2.z + a3 * b3.z);
-                        acc[4 * u + 3].add(a0 * b0.w + a1 * b1.w + a2 * b2.w + a3 * b3.w);
-                    }
-                }
-                for (; r < nr; ++r) {
-                    const float a = __ldcs(p + (int64_t)r * ld);
-#pragma unroll
-                    for (int u = 0; u < kNQW; ++u) acc[u].add(a * xsm[r * kNQW + u]);
-                }
-            }
-        }
-        if (act) {
-            float *o = direct ? t + G.map_v[vc0 + c] * kNQW : partial + (pb + c) * kNQW;
-#pragma unroll
-            for (int u = 0; u < kNQW; u += 4)
-                *reinterpret_cast<float4 *>(o + u) = make_float4(acc[u].get(), acc[u + 1].get(), acc[u + 2].get(),
-                                                                 acc[u + 3].get());
-        }
-    }
 }
 
 __global__ void k_reduce_partials_w(SplitArgs S, const float *__restrict__ partial, float *__restrict__ t) {
@@ -1205,467 +1155,512 @@ __global__ void __launch_bounds__(kLeafThreads) k_near_w(LeafArgs A, const float
     }
 }
 
-// far field for 32 right-hand sides: U panels through the TMA ring as k_leaf;
-// one thread per (row, column group), all 32 right-hand sides
-__global__ void __launch_bounds__(kLeafThreads) k_leaf_w(LeafArgs A, const float *__restrict__ U,
-                                                         const float *__restrict__ t, const float *__restrict__ nearbuf,
-                                                         float *__restrict__ y, int64_t n, int q0, int nq) {
-    extern __shared__ __align__(128) unsigned char stage[];
-    __shared__ __align__(8) uint64_t bars[kStages];
-    __shared__ ChunkPlan P;
-    __shared__ float red[kLeafThreads * 8];
-    const int z = blockIdx.x;
-    const int Zg = (int)(A.offL + z);
-    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
-    const int ld = A.leaf_ld[z];                            // <= kMaxLeafW
-    const int cpc = kChunkBytes / (ld * (int)sizeof(float));
-    const int L = A.L;
-    if (threadIdx.x >= 1 && threadIdx.x <= L) {
-        const int l = threadIdx.x;
-        const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
-        const int RA = A.R[Ag];
-        P.panel[l] = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
-        P.tA[l] = t + A.tbase[Ag] * kNQW;
-        P.R[l] = RA;
-    }
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < kStages; ++q) mbar_init(&bars[q], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int l = 1; l <= L; ++l) {
-            P.first[l] = acc;
-            acc += (P.R[l] + cpc - 1) / cpc;
-        }
-        P.first[L + 1] = acc;
-    }
-    __syncthreads();
-    const int nchunks = P.first[L + 1];
-    int pl = 1;
-    auto issue = [&](int k) {
-        int c0, nc;
-        chunk_of<float>(P, L, k, cpc, pl, c0, nc);
-        const uint32_t bytes = (uint32_t)(nc * ld * (int)sizeof(float));
-        uint64_t *bar = &bars[k % kStages];
-        mbar_arrive_expect_tx(bar, bytes);
-        bulk_copy_g2s(stage + (size_t)(k % kStages) * kChunkBytes,
-                      static_cast<const float *>(P.panel[pl]) + (int64_t)c0 * ld, bytes, bar);
-    };
-    if (threadIdx.x == 0)
-        for (int k = 0; k < min(kStages - 1, nchunks); ++k) issue(k);
-    const int Gc = kLeafThreads / ld;
-    const int g = threadIdx.x / ld, i = threadIdx.x - g * ld;
-    Acc<float> acc[kNQW];
-    int cl_level = 1;
-    for (int k = 0; k < nchunks; ++k) {
-        const bool ok = mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) {
-                *A.err = H3D_ERR_TIMEOUT;
-                for (int j = k; j < min(k + kStages - 1, nchunks); ++j)
-                    mbar_wait(&bars[j % kStages], (uint32_t)((j / kStages) & 1));
-            }
-            return;
-        }
-        if (threadIdx.x == 0 && k + kStages - 1 < nchunks) issue(k + kStages - 1);
-        int c0, nc;
-        chunk_of<float>(P, L, k, cpc, cl_level, c0, nc);
-        const float *sm = reinterpret_cast<const float *>(stage + (size_t)(k % kStages) * kChunkBytes) + i;
-        const float *tA = static_cast<const float *>(P.tA[cl_level]) + (int64_t)c0 * kNQW;
-        if (g < Gc) {
-            int c = g;
-            for (; c + 3 * Gc < nc; c += 4 * Gc) {
-                const float a0 = sm[c * ld], a1 = sm[(c + Gc) * ld], a2 = sm[(c + 2 * Gc) * ld],
-                            a3 = sm[(c + 3 * Gc) * ld];
-                const float4 *b0 = reinterpret_cast<const float4 *>(tA + (int64_t)c * kNQW);
-                const float4 *b1 = reinterpret_cast<const float4 *>(tA + (int64_t)(c + Gc) * kNQW);
-                const float4 *b2 = reinterpret_cast<const float4 *>(tA + (int64_t)(c + 2 * Gc) * kNQW);
-                const float4 *b3 = reinterpret_cast<const float4 *>(tA + (int64_t)(c + 3 * Gc) * kNQW);
-#pragma unroll
-                for (int u = 0; u < kNQW / 4; ++u) {
-                    const float4 v0 = __ldg(b0 + u), v1 = __ldg(b1 + u), v2 = __ldg(b2 + u), v3 = __ldg(b3 + u);
-                    acc[4 * u].add(a0 * v0.x + a1 * v1.x + a2 * v2.x + a3 * v3.x);
-                    acc[4 * u + 1].add(a0 * v0.y + a1 * v1.y + a2 * v2.y + a3 * v3.y);
-                    acc[4 * u + 2].add(a0 * v0.z + a1 * v1.z + a2 * v2.z + a3 * v3.z);
-                    acc[4 * u + 3].add(a0 * v0.w + a1 * v1.w + a2 * v2.w + a3 * v3.w);
-                }
-            }
-            for (; c < nc; c += Gc) {
-                const float a = sm[c * ld];
-                const float4 *b = reinterpret_cast<const float4 *>(tA + (int64_t)c * kNQW);
-#pragma unroll
-                for (int u = 0; u < kNQW / 4; ++u) {
-                    const float4 v = __ldg(b + u);
-                    acc[4 * u].add(a * v.x);
-                    acc[4 * u + 1].add(a * v.y);
-                    acc[4 * u + 2].add(a * v.z);
-                    acc[4 * u + 3].add(a * v.w);
-                }
-            }
-        }
-    }
-    // reduce over column groups in four slices of 8 right-hand sides
-#pragma unroll
-    for (int sl4 = 0; sl4 < 4; ++sl4) {
-        __syncthreads();
-        if (g < Gc)
-#pragma unroll
-            for (int u = 0; u < 8; ++u) red[(g * ld + i) * 8 + u] = acc[sl4 * 8 + u].get();
-        __syncthreads();
-        for (int e = threadIdx.x; e < m * 8; e += kLeafThreads) {
-            const int ii = e / 8, u = e - ii * 8, q = sl4 * 8 + u;
-            if (q >= nq) continue;
-            float v = 0.f;
-            for (int gg = 0; gg < Gc; ++gg) v += red[(gg * ld + ii) * 8 + u];
-            y[(int64_t)(q0 + q) * n + A.perm[zs + ii]] = v + nearbuf[(int64_t)(zs + ii) * kNQW + q];
-        }
-    }
-}
-
 // ===========================================================================
-// Source-side gather of 32 right-hand sides on the tensor cores (tcgen05,
-// kind::tf32, 3xTF32 split precision):
-//   T_Y(c, q) = sum_r V_Y(r, c) x(r, q)  as  D[M = c][N = q] += A[M][K = r] B[K][N].
-// A work item is one gather task (source box, row range) and a tile of 128
-// columns.  Per K step of 8 rows every thread loads V and x, splits each value
-// into tf32 hi + lo (the tensor core truncates FP32 operands to tf32, so both
-// parts are rounded here) and writes them into K-major core-matrix layout (8 rows
-// x 16 bytes per core matrix; LBO = 128 B along K, SBO = 256 B along M or N) in one
-// of two shared-memory buffers; one thread issues the MMAs and commits them to the
-// buffer's mbarrier, which the threads wait on (bounded) before refilling it.
-// Accumulation: the tensor core's FP32 accumulation is biased (its error grows
-// about one ulp per accumulated MMA), so the main products hi*hi go to one of two
-// TMEM accumulators that is restarted every kTcGroup K steps and drained into a
-// compensated FP32 sum in registers while the other one is filled; the small
-// corrections hi*lo + lo*hi (2^-11 of the main term) accumulate in a third TMEM
-// accumulator over the whole item.  The CTAs are persistent and keep their TMEM
-// allocation for the whole launch.
-constexpr int kTcThreads = 128;
-constexpr int kTcGroup = 4;                           // K steps per drained accumulator
-constexpr int kTcAOp = 4096;                          // one A operand: 128 rows x 8 k, tf32
-constexpr int kTcBOp = 1024;                          // one B operand: 32 columns x 8 k
-constexpr int kTcBuf = 2 * kTcAOp + 2 * kTcBOp;       // hi and lo of A and B
-constexpr size_t kTcDynSmem = 2 * (size_t)kTcBuf + 128;
-constexpr int kTcCtasPerSm = 3;
-constexpr int kTcCols = 128;
+// Factor products of 32 right-hand sides on the tensor cores (tcgen05,
+// kind::tf32, 3xTF32 split precision): one warp-specialised persistent kernel
+// for both sides of the far field.
+//   gather (kLeaf = false): T_Y(c, q) = sum_r V_Y(r, c) x(r, q), i.e.
+//     D[M = 128 columns c of V][N] += A[M][K = rows r] B[K][N];
+//     a work item is one gather task (source box, row range) x 128 columns.
+//   leaf (kLeaf = true): y(i, q) = sum over levels, columns c of U_panel(i, c) t_A(c, q),
+//     D[M = 128 rows][N] += A[M][K = c] B[K][N], plus the near field.  A work item
+//     is a tile of sibling leaves (same parent) whose rows fit in 128: their
+//     ancestors at levels 1..L-1 are shared, so each of those panels' K range is
+//     one stage sequence for the whole tile (every leaf's rows stacked in M, one t
+//     chunk in B); each leaf's own level-L panel then runs with the other leaves'
+//     rows zero.
+// Each item is cut into stages of up to kTsK = 32 K values (4 MMA K steps).
+//  * warp 0, the producer, walks the items (descriptions of the next 32 gather
+//    items are loaded while the current ones are issued) and fills a ring of
+//    kTsSlots slots with TMA: the gather's V tile in one 2-D tensor copy from the
+//    source box's tensor map, the leaf's U chunks in one bulk copy per leaf, and
+//    the B tile (x or t rows, contiguous) in one bulk copy; full / empty mbarriers
+//    per slot.
+//  * warps 2-9, the converters, split each value into tf32 hi + lo (the tensor
+//    core truncates FP32 operands, so both parts are rounded here): A straight
+//    into tensor memory (lane = M row, one column per K value), B as one N = 64
+//    operand [hi | lo] of K-major core matrices in shared memory (8 rows x 16
+//    bytes; LBO 128 B along K, SBO 1024 B along N; K step j starts 256 B
+//    further).  They drain the accumulators of the stage two behind into
+//    registers.  Two warps share each quadrant of TMEM lanes: each converts half
+//    of the stage's K values and drains half of the 32 right-hand sides.
+//  * one thread of warp 1 issues a stage's MMAs, per K step
+//      A_hi x [B_hi | B_lo]  (N = 64) -> the stage's main | first correction
+//      A_lo x B_hi           (N = 32) -> the item's second correction,
+//    then commits them to the stage's operand mbarrier.
+// The tensor core's FP32 accumulation is biased (its error grows about one ulp per
+// accumulated MMA), so each stage's main accumulator goes into a compensated FP32
+// sum in registers as soon as the stage completes; the first correction is
+// summed plainly per stage and the second stays in TMEM for the whole item (both
+// are 2^-11 of the main term).
+// Every wait is bounded.  A wait that gives up raises the CTA's abort flag, every
+// role leaves its loop, copies and MMAs in flight are waited for (bounded), the
+// error word is set and TMEM is freed.
+constexpr int kTsConv = 256;                           // converter threads
+constexpr int kTsThreads = 64 + kTsConv;
+constexpr int kTsSlots = 8;
+constexpr int kTsK = 32;                               // K values per stage
+constexpr int kTsBOp = 32 * kTsK * 4;                  // B_hi or B_lo (32 x 32 tf32), 4 KB
+constexpr int kTsBBuf = 2 * kTsBOp;                    // [B_hi | B_lo] as one N = 64 operand
+constexpr int kTsSlotA = 128 * kTsK * 4;               // raw A tile
+constexpr int kTsSlotB = 32 * kTsK * 4;                // raw B tile
+constexpr int kTsSlot = kTsSlotA + kTsSlotB;
+constexpr size_t kTsDynSmem = (size_t)kTsSlots * kTsSlot + 2 * (size_t)kTsBBuf + 128;
+constexpr int kTcCols = 128;                           // gather: V columns per item
+constexpr int kTileLeaves = 8;                         // leaves per far-field tile (siblings)
+// tensor memory columns (512 allocated; one CTA per SM)
+constexpr uint32_t kTmMain = 0;     // 2 stage sets x 64: main (32) | first correction (32)
+constexpr uint32_t kTmCorr = 128;   // 2 item sets x 32: second correction
+constexpr uint32_t kTmA = 256;      // 2 stage sets x 64: A_hi (32) | A_lo (32)
 
-__global__ void __launch_bounds__(kTcThreads) k_gather_tc(GatherArgs G, const int2 *__restrict__ items, int nitems,
-                                                          const float *__restrict__ V, const float *__restrict__ xs,
-                                                          float *__restrict__ t, float *__restrict__ partial,
-                                                          int *err) {
-    extern __shared__ unsigned char dsm_raw[];
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ uint32_t tmem_base;
-    unsigned char *dsm = dsm_raw + ((128 - (smem_addr(dsm_raw) & 127)) & 127);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) tmem_alloc(&tmem_base, 128);   // main[0], main[1], corrections, unused
-    if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        mbar_fence_init();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_base;
-    const uint32_t tlane = (uint32_t)(warp << 5) << 16;   // this warp's TMEM lanes
-    const uint32_t idesc = umma_idesc_tf32(128, kNQW);
-    uint32_t issued[2] = {0u, 0u}, waited[2] = {0u, 0u};
-    int step = 0;
-    bool failed = false;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int2 w = items[it];
-        const int4 task = G.task[w.x];
-        const int Y = task.x, r0 = task.y, r1 = task.z;
-        const int ld = G.ldv[Y], RvY = G.Rv[Y];
-        const int c_lo = w.y * kTcCols;
-        const int ncols = min(kTcCols, RvY - c_lo);
-        const float *Vb = V + G.vbase[Y] + (int64_t)r0 * ld + c_lo;
-        const int64_t xrow0 = (int64_t)G.box_start[Y] + r0;
-        const int nrows = r1 - r0;
-        const int nsteps = (nrows + 7) >> 3;
-        const int ngroups = (nsteps + kTcGroup - 1) / kTcGroup;
-        Acc<float> acc[kNQW];
-        auto drain = [&](int grp) {   // add main accumulator of group grp into the register sums
-            float v[32];
-            tmem_ld32(tmem + tlane + 32u * (uint32_t)(grp & 1), v);
-#pragma unroll
-            for (int q = 0; q < kNQW; ++q) acc[q].add(v[q]);
-        };
-        for (int s = 0; s < nsteps; ++s, ++step) {
-            const int b = step & 1;
-            unsigned char *buf = dsm + b * kTcBuf;
-            if (issued[b] != waited[b]) {   // the MMAs that read this buffer must be done
-                const bool ok = mbar_wait(&mbar[b], waited[b] & 1u);
-                ++waited[b];
-                if (__syncthreads_or(!ok)) { failed = true; break; }
-                tc_fence_after();
-            }
-            const int grp = s / kTcGroup;
-            // the accumulator this group reuses held group grp-2, complete by now
-            if (s % kTcGroup == 0 && grp >= 2) drain(grp - 2);
-            const int rk = s << 3;
-            {   // A: 8 rows x 128 columns of V, one column per thread
-                const bool colok = tid < ncols;
-                float hi[8], lo[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int r = rk + k;
-                    const float v = (colok && r < nrows) ? __ldcs(Vb + (int64_t)r * ld + tid) : 0.f;
-                    split_tf32(v, hi[k], lo[k]);
-                }
-                unsigned char *ah = buf + ((tid >> 3) << 8) + ((tid & 7) << 4);
-                *reinterpret_cast<float4 *>(ah) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<float4 *>(ah + 128) = make_float4(hi[4], hi[5], hi[6], hi[7]);
-                *reinterpret_cast<float4 *>(ah + kTcAOp) = make_float4(lo[0], lo[1], lo[2], lo[3]);
-                *reinterpret_cast<float4 *>(ah + kTcAOp + 128) = make_float4(lo[4], lo[5], lo[6], lo[7]);
-            }
-            {   // B: 8 rows x 32 right-hand sides of x, two values per thread
-                const int n = tid & 31, k0 = (tid >> 5) << 1;
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const int k = k0 + kk, r = rk + k;
-                    const float v = r < nrows ? xs[(xrow0 + r) * kNQW + n] : 0.f;
-                    float h, l;
-                    split_tf32(v, h, l);
-                    const int off = ((n >> 3) << 8) + ((k >> 2) << 7) + ((n & 7) << 4) + ((k & 3) << 2);
-                    *reinterpret_cast<float *>(buf + 2 * kTcAOp + off) = h;
-                    *reinterpret_cast<float *>(buf + 2 * kTcAOp + kTcBOp + off) = l;
-                }
-            }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
-            if (tid == 0) {
-                const uint32_t abase = smem_addr(buf), bbase = abase + 2 * kTcAOp;
-                const uint64_t ahd = umma_desc(abase, 128, 256), ald = umma_desc(abase + kTcAOp, 128, 256);
-                const uint64_t bh = umma_desc(bbase, 128, 256), bl = umma_desc(bbase + kTcBOp, 128, 256);
-                umma_tf32(tmem + 32u * (uint32_t)(grp & 1), ahd, bh, idesc, s % kTcGroup ? 1u : 0u);
-                umma_tf32(tmem + 64u, ahd, bl, idesc, s > 0 ? 1u : 0u);
-                umma_tf32(tmem + 64u, ald, bh, idesc, 1u);
-                umma_commit(&mbar[b]);
-            }
-            ++issued[b];
-        }
-        if (failed) break;
-        bool ok = true;
-        for (int bb = 0; bb < 2; ++bb)
-            while (waited[bb] != issued[bb]) {
-                ok = mbar_wait(&mbar[bb], waited[bb] & 1u) && ok;
-                ++waited[bb];
-            }
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-        tc_fence_after();
-        if (ngroups >= 2) drain(ngroups - 2);
-        drain(ngroups - 1);
-        {
-            float v[32];
-            tmem_ld32(tmem + tlane + 64u, v);
-#pragma unroll
-            for (int q = 0; q < kNQW; ++q) acc[q].add(v[q]);
-        }
-        const int m = (warp << 5) + lane;
-        if (m < ncols) {
-            const int c = c_lo + m;
-            float *o = task.w ? t + G.map_v[G.vcol0[Y] + c] * kNQW : partial + (G.pbase[w.x] + c) * kNQW;
-#pragma unroll
-            for (int q = 0; q < kNQW; q += 4)
-                *reinterpret_cast<float4 *>(o + q) =
-                    make_float4(acc[q].get(), acc[q + 1].get(), acc[q + 2].get(), acc[q + 3].get());
-        }
-        tc_fence_before();
-        __syncthreads();   // accumulators read before the next item overwrites them
-        tc_fence_after();
-    }
-    if (failed && tid == 0) *err = H3D_ERR_TIMEOUT;
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 128);
+struct TsArgs {
+    const TcGatherItem *gitems;
+    const unsigned char *tmaps;   // CUtensorMap[], 128 bytes each
+    const int2 *tiles;
+    const float *V, *xs;
+    float *t, *partial;
+    const int64_t *map_v;
+    LeafArgs A;
+    const float *U, *tl, *nearbuf;
+    float *y;
+    int64_t n;
+    int q0, nq;
+    int nitems;               // gather items or leaf tiles
+    int *err;
+};
+
+struct TsMeta {               // one per ring slot, written by the producer
+    int nk;                   // K values of the stage; 0: an item without far field; -1: end
+    int first, last;          // first / last stage of its item
+    int sel;                  // leaf: -1 = every row of the tile is live, else the one live leaf
+    int ncols, to_t;          // gather: valid columns, output to t (1) or partial (0)
+    int z0, nl;               // leaf: first leaf of the tile, leaves
+    int ld[kTileLeaves], off[kTileLeaves];   // leaf: rows and first tile row per leaf
+    int64_t idx[kTcCols];     // gather, last stage: output row per column
+};
+
+struct TsOpMeta {             // per operand buffer, converters -> MMA issuer
+    int nks, first, corr;     // K steps (-1: end), first stage of its item, correction set
+};
+
+// byte offset of element (row `n`, k) in a K-major operand of kTsK values
+__device__ __forceinline__ int kmajor_off(int n, int k) {
+    return ((n >> 3) << 10) + ((k >> 2) << 7) + ((n & 7) << 4) + ((k & 3) << 2);
 }
 
-// Far field of one leaf for 32 right-hand sides on the tensor cores:
-//   y(rows, q) = sum over levels of U_panel(rows, c) t_A(c, q)
-// as D[M = 128 rows (the leaf's rows, the rest zero)][N = 32] += A[M][K = c] B[K][N].
-// The U panels arrive through the same TMA ring as in k_leaf; per K step of 8
-// columns the threads split U (transposed into K-major) and t into tf32 hi + lo
-// operands; accumulation as in k_gather_tc (drained main accumulators, one
-// correction accumulator).  Then far + near in the caller's order.
-constexpr size_t kLeafTcDynSmem = kLeafDynSmem + 2 * (size_t)kTcBuf + 128;
-
-__global__ void __launch_bounds__(kTcThreads) k_leaf_tc(LeafArgs A, const float *__restrict__ U,
-                                                        const float *__restrict__ t, const float *__restrict__ nearbuf,
-                                                        float *__restrict__ y, int64_t n, int q0, int nq) {
-    extern __shared__ __align__(128) unsigned char stage[];   // TMA ring, then the operand buffers
-    __shared__ __align__(8) uint64_t bars[kStages];
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ ChunkPlan P;
+template <bool kLeaf>
+__global__ void __launch_bounds__(kTsThreads, 1) k_tc_stream(TsArgs P) {
+    extern __shared__ unsigned char dsm_raw[];
+    __shared__ __align__(8) uint64_t full[kTsSlots], empty[kTsSlots], opfull[2], opempty[2];
+    __shared__ TsMeta meta[kTsSlots];
+    __shared__ TsOpMeta opm[2];
+    __shared__ int abort_flag;
     __shared__ uint32_t tmem_base;
-    unsigned char *ops_raw = stage + kLeafDynSmem;
-    unsigned char *ops = ops_raw + ((128 - (smem_addr(ops_raw) & 127)) & 127);
+    // producer-private plan of the current leaf tile
+    __shared__ const float *pl_tl[kMaxDepth + 1], *pl_tL[kTileLeaves];
+    __shared__ int64_t pl_ub[kMaxDepth + 1], pl_lplo[kMaxDepth + 1], pl_lp[kTileLeaves], pl_ubL[kTileLeaves];
+    __shared__ int pl_R[kMaxDepth + 1], pl_RL[kTileLeaves], pl_ld[kTileLeaves], pl_off[kTileLeaves];
+    unsigned char *ring = dsm_raw + ((128 - (smem_addr(dsm_raw) & 127)) & 127);
+    unsigned char *bops = ring + (size_t)kTsSlots * kTsSlot;   // two [B_hi | B_lo] operands
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int z = blockIdx.x;
-    const int Zg = (int)(A.offL + z);
-    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
-    const int ld = A.leaf_ld[z];                               // <= kMaxLeafW = 128
-    const int cpc = kChunkBytes / (ld * (int)sizeof(float));
-    const int L = A.L;
-    if (warp == 0) tmem_alloc(&tmem_base, 128);
-    if (tid >= 1 && tid <= L) {
-        const int l = tid;
-        const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
-        const int RA = A.R[Ag];
-        P.panel[l] = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
-        P.tA[l] = t + A.tbase[Ag] * kNQW;
-        P.R[l] = RA;
-    }
-    if (tid == 0) {
-        for (int q = 0; q < kStages; ++q) mbar_init(&bars[q], 1);
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+    volatile int *abort = &abort_flag;
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
+    if (tid == 32) {
+        for (int i = 0; i < kTsSlots; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kTsConv / 32);   // one arrival per converter warp
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&opfull[i], kTsConv / 32);
+            mbar_init(&opempty[i], 1);
+        }
+        abort_flag = 0;
         mbar_fence_init();
     }
-    // rows >= ld of the A operands stay zero
-    for (int e = tid; e < 2 * kTcBuf / 16; e += kTcThreads)
-        reinterpret_cast<float4 *>(ops)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid == 0) {
-        int acc = 0;
-        for (int l = 1; l <= L; ++l) {
-            P.first[l] = acc;
-            acc += (P.R[l] + cpc - 1) / cpc;
-        }
-        P.first[L + 1] = acc;
-    }
-    __syncthreads();
     const uint32_t tmem = tmem_base;
-    const uint32_t tlane = (uint32_t)(warp << 5) << 16;
-    const uint32_t idesc = umma_idesc_tf32(128, kNQW);
-    const int nchunks = P.first[L + 1];
-    int pl = 1;
-    auto issue = [&](int k) {
-        int c0, nc;
-        chunk_of<float>(P, L, k, cpc, pl, c0, nc);
-        const uint32_t bytes = (uint32_t)(nc * ld * (int)sizeof(float));
-        uint64_t *bar = &bars[k % kStages];
-        mbar_arrive_expect_tx(bar, bytes);
-        bulk_copy_g2s(stage + (size_t)(k % kStages) * kChunkBytes,
-                      static_cast<const float *>(P.panel[pl]) + (int64_t)c0 * ld, bytes, bar);
-    };
-    if (tid == 0)
-        for (int k = 0; k < min(kStages - 1, nchunks); ++k) issue(k);
-    Acc<float> acc[kNQW];
-    auto drain = [&](int grp) {
-        float v[32];
-        tmem_ld32(tmem + tlane + 32u * (uint32_t)(grp & 1), v);
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        int s = 0;
+        bool ok = true;
+        auto acquire = [&](int slot) -> bool {   // wait until the converters released the slot
+            if (s < kTsSlots) return true;
+            return mbar_wait_or_abort(&empty[slot], (uint32_t)(((s / kTsSlots) - 1) & 1), abort);
+        };
+        if constexpr (!kLeaf) {
+            // lane j holds the description of item base + j * gridDim.x; the next 32
+            // are loaded while these are issued
+            const int G = gridDim.x;
+            TcGatherItem mine{}, nextb{};
+            int base = blockIdx.x;
+            if (base + lane * G < P.nitems) mine = P.gitems[base + lane * G];
+            for (; base < P.nitems && ok; base += 32 * G) {
+                if (base + 32 * G + lane * G < P.nitems) nextb = P.gitems[base + 32 * G + lane * G];
+                for (int j = 0; j < 32 && ok; ++j) {
+                    if (base + j * G >= P.nitems) break;
+                    const int64_t gx = __shfl_sync(0xffffffffu, mine.x, j);
+                    const int64_t go = __shfl_sync(0xffffffffu, mine.o, j);
+                    const int tmap = __shfl_sync(0xffffffffu, mine.tmap, j);
+                    const int c_lo = __shfl_sync(0xffffffffu, mine.c_lo, j);
+                    const int r0 = __shfl_sync(0xffffffffu, mine.r0, j);
+                    const int nrows = __shfl_sync(0xffffffffu, mine.nrows, j);
+                    const int ncols = __shfl_sync(0xffffffffu, mine.ncols, j);
+                    const int to_t = __shfl_sync(0xffffffffu, mine.to_t, j);
+                    const unsigned char *tm = P.tmaps + 128 * (size_t)tmap;
+                    const float *xsrc = P.xs + gx * kNQW;
+                    for (int r = 0; r < nrows; r += kTsK) {
+                        const int nk = min(kTsK, nrows - r), slot = s % kTsSlots;
+                        if (!(ok = acquire(slot))) break;
+                        TsMeta &M = meta[slot];
+                        const bool last = r + kTsK >= nrows;
+                        if (lane == 0) {
+                            M.nk = nk;
+                            M.first = r == 0;
+                            M.last = last;
+                            M.ncols = ncols;
+                            M.to_t = to_t;
+                        }
+                        if (last) {   // output rows: copied asynchronously, tracked by the slot's barrier
 #pragma unroll
-        for (int q = 0; q < kNQW; ++q) acc[q].add(v[q]);
-    };
-    uint32_t issued[2] = {0u, 0u}, waited[2] = {0u, 0u};
-    int s = 0, cl_level = 1;
-    bool failed = false;
-    for (int k = 0; k < nchunks && !failed; ++k) {
-        const bool okc = mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
-        if (__syncthreads_or(!okc)) { failed = true; break; }
-        if (tid == 0 && k + kStages - 1 < nchunks) issue(k + kStages - 1);
-        int c0, nc;
-        chunk_of<float>(P, L, k, cpc, cl_level, c0, nc);
-        const float *sm = reinterpret_cast<const float *>(stage + (size_t)(k % kStages) * kChunkBytes);
-        const float *tA = static_cast<const float *>(P.tA[cl_level]) + (int64_t)c0 * kNQW;
-        const int nks = (nc + 7) >> 3;
-        for (int ks = 0; ks < nks; ++ks, ++s) {
-            const int b = s & 1;
-            unsigned char *buf = ops + b * kTcBuf;
-            if (issued[b] != waited[b]) {
-                const bool ok = mbar_wait(&mbar[b], waited[b] & 1u);
-                ++waited[b];
-                if (__syncthreads_or(!ok)) { failed = true; break; }
+                            for (int q = 0; q < kTcCols / 32; ++q) {
+                                const int mc = lane + 32 * q;
+                                if (mc >= ncols) M.idx[mc] = -1;
+                                else if (to_t) cp_async8(&M.idx[mc], P.map_v + go + mc);
+                                else M.idx[mc] = go + mc;
+                            }
+                            cp_async_arrive(&full[slot]);
+                        }
+                        __syncwarp();   // the lanes' stores are ordered before lane 0's release
+                        if (lane == 0) {
+                            unsigned char *sa = ring + (size_t)slot * kTsSlot;
+                            // the tensor copy always moves the whole 32 x 128 box (zero outside the factor)
+                            mbar_arrive_expect_tx(&full[slot], (uint32_t)(kTsSlotA + nk * kNQW * 4));
+                            tma_load_2d(sa, tm, c_lo, r0 + r, &full[slot]);
+                            bulk_copy_g2s(sa + kTsSlotA, xsrc + (int64_t)r * kNQW, (uint32_t)(nk * kNQW * 4),
+                                          &full[slot]);
+                        }
+                        __syncwarp();
+                        ++s;
+                    }
+                }
+                mine = nextb;
+            }
+        } else {
+            const LeafArgs &A = P.A;
+            const int L = A.L;
+            for (int it = blockIdx.x; it < P.nitems && ok; it += gridDim.x) {
+                const int2 tile = P.tiles[it];
+                const int z0 = tile.x, nl = tile.y;
+                __syncwarp();   // every lane is done with the previous tile's plan
+                const int ld = lane < nl ? A.leaf_ld[z0 + lane] : 0;
+                int off = ld;   // inclusive prefix of the rows over the warp
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, off, d);
+                    if (lane >= d) off += v;
+                }
+                if (lane < nl) {   // this tile's leaves: rows, tile offset, own (level-L) panel
+                    const int z = z0 + lane;
+                    pl_ld[lane] = ld;
+                    pl_off[lane] = off - ld;
+                    pl_lp[lane] = A.leaf_lp[z];
+                    if (L > 0) {
+                        const int Zg = A.leaf_anc[(int64_t)(L - 1) * A.nleaf + z];
+                        pl_RL[lane] = A.R[Zg];
+                        pl_ubL[lane] = A.ubase[Zg] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Zg]]) * A.R[Zg];
+                        pl_tL[lane] = P.tl + A.tbase[Zg] * kNQW;
+                    } else {
+                        pl_RL[lane] = 0;
+                    }
+                }
+                if (lane >= 1 && lane < L) {   // shared ancestors at levels 1 .. L-1
+                    const int Ag = A.leaf_anc[(int64_t)(lane - 1) * A.nleaf + z0];
+                    pl_R[lane] = A.R[Ag];
+                    pl_ub[lane] = A.ubase[Ag];
+                    pl_lplo[lane] = A.leaf_lp[A.leaf_lo[Ag]];
+                    pl_tl[lane] = P.tl + A.tbase[Ag] * kNQW;
+                }
+                __syncwarp();
+                int nst = 0;
+                for (int l = 1; l < L; ++l) nst += (pl_R[l] + kTsK - 1) / kTsK;
+                for (int g = 0; g < nl; ++g) nst += (pl_RL[g] + kTsK - 1) / kTsK;
+                auto stage = [&](int st, int nk, int sel) -> bool {
+                    const int slot = s % kTsSlots;
+                    if (!acquire(slot)) return false;
+                    if (lane == 0) {
+                        TsMeta &M = meta[slot];
+                        M.nk = nk;
+                        M.first = st == 0;
+                        M.last = st == max(nst, 1) - 1;
+                        M.sel = sel;
+                        M.z0 = z0;
+                        M.nl = nl;
+                        for (int g = 0; g < kTileLeaves; ++g) {
+                            M.ld[g] = g < nl ? pl_ld[g] : 0;
+                            M.off[g] = g < nl ? pl_off[g] : 128;
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) {   // its arrive releases the meta it wrote
+                        uint32_t bytes = (uint32_t)(nk * kNQW * 4);
+                        for (int g = 0; g < nl; ++g)
+                            if (sel < 0 || sel == g) bytes += (uint32_t)(nk * pl_ld[g] * 4);
+                        if (nk > 0) mbar_arrive_expect_tx(&full[slot], bytes);
+                        else mbar_arrive(&full[slot]);
+                    }
+                    __syncwarp();
+                    ++s;
+                    return true;
+                };
+                int st = 0;
+                for (int l = 1; l < L && ok; ++l) {
+                    const int R = pl_R[l];
+                    for (int c0 = 0; c0 < R; c0 += kTsK, ++st) {
+                        const int nk = min(kTsK, R - c0);
+                        unsigned char *sa = ring + (size_t)(s % kTsSlots) * kTsSlot;
+                        uint64_t *bar = &full[s % kTsSlots];
+                        if (!(ok = stage(st, nk, -1))) break;
+                        if (lane < nl)
+                            bulk_copy_g2s(sa + 128 * pl_off[lane],
+                                          P.U + pl_ub[l] + (pl_lp[lane] - pl_lplo[l]) * R + (int64_t)c0 * pl_ld[lane],
+                                          (uint32_t)(nk * pl_ld[lane] * 4), bar);
+                        if (lane == 31)
+                            bulk_copy_g2s(sa + kTsSlotA, pl_tl[l] + (int64_t)c0 * kNQW, (uint32_t)(nk * kNQW * 4), bar);
+                    }
+                }
+                for (int g = 0; g < nl && ok; ++g) {
+                    const int R = pl_RL[g];
+                    for (int c0 = 0; c0 < R; c0 += kTsK, ++st) {
+                        const int nk = min(kTsK, R - c0);
+                        unsigned char *sa = ring + (size_t)(s % kTsSlots) * kTsSlot;
+                        uint64_t *bar = &full[s % kTsSlots];
+                        if (!(ok = stage(st, nk, g))) break;
+                        if (lane == 0)
+                            bulk_copy_g2s(sa + 128 * pl_off[g], P.U + pl_ubL[g] + (int64_t)c0 * pl_ld[g],
+                                          (uint32_t)(nk * pl_ld[g] * 4), bar);
+                        if (lane == 31)
+                            bulk_copy_g2s(sa + kTsSlotA, pl_tL[g] + (int64_t)c0 * kNQW, (uint32_t)(nk * kNQW * 4), bar);
+                    }
+                }
+                if (ok && nst == 0) ok = stage(0, 0, -1);   // no far field: the tile still reaches its output
+            }
+        }
+        if (ok) {   // end marker
+            const int slot = s % kTsSlots;
+            if ((ok = acquire(slot))) {
+                if (lane == 0) {
+                    meta[slot].nk = -1;
+                    meta[slot].first = meta[slot].last = 0;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[slot]);
+            }
+        }
+        if (!ok && lane == 0)   // copies still in flight land before the CTA leaves
+            for (int j = max(0, s - kTsSlots); j < s; ++j) mbar_wait(&full[j % kTsSlots], (uint32_t)((j / kTsSlots) & 1));
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t id64 = umma_idesc_tf32(128, 2 * kNQW), id32 = umma_idesc_tf32(128, kNQW);
+            int s = 0;
+            for (;; ++s) {
+                const int b = s & 1;
+                if (!mbar_wait_or_abort(&opfull[b], (uint32_t)((s >> 1) & 1), abort)) break;
                 tc_fence_after();
-            }
-            const int grp = s / kTcGroup;
-            if (s % kTcGroup == 0 && grp >= 2) drain(grp - 2);
-            const int cb = ks << 3;
-            if (tid < ld) {   // A: row tid, 8 columns
-                float hi[8], lo[8];
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    const int c = cb + kk;
-                    split_tf32(c < nc ? sm[c * ld + tid] : 0.f, hi[kk], lo[kk]);
+                const TsOpMeta om = opm[b];
+                if (om.nks < 0) break;
+                const uint32_t bbase = smem_addr(bops + b * kTsBBuf);
+                const uint32_t dmain = tmem + kTmMain + 64u * (uint32_t)b;
+                const uint32_t dcorr = tmem + kTmCorr + 32u * (uint32_t)om.corr;
+                const uint32_t ahi = tmem + kTmA + 64u * (uint32_t)b, alo = ahi + 32u;
+                for (int j = 0; j < om.nks; ++j) {
+                    const uint64_t bd = umma_desc(bbase + 256u * (uint32_t)j, 128, 1024);
+                    umma_tf32_ts(dmain, ahi + 8u * (uint32_t)j, bd, id64, j > 0 ? 1u : 0u);
+                    umma_tf32_ts(dcorr, alo + 8u * (uint32_t)j, bd, id32, (j > 0 || !om.first) ? 1u : 0u);
                 }
-                unsigned char *ah = buf + ((tid >> 3) << 8) + ((tid & 7) << 4);
-                *reinterpret_cast<float4 *>(ah) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<float4 *>(ah + 128) = make_float4(hi[4], hi[5], hi[6], hi[7]);
-                *reinterpret_cast<float4 *>(ah + kTcAOp) = make_float4(lo[0], lo[1], lo[2], lo[3]);
-                *reinterpret_cast<float4 *>(ah + kTcAOp + 128) = make_float4(lo[4], lo[5], lo[6], lo[7]);
+                umma_commit(&opempty[b]);
             }
-            {   // B: 8 columns x 32 right-hand sides of t, two values per thread
-                const int nn = tid & 31, k0 = (tid >> 5) << 1;
+            if (*abort)   // this thread's MMAs finish before TMEM is freed
+                for (int j = max(0, s - 2); j < s; ++j) mbar_wait(&opempty[j & 1], (uint32_t)((j >> 1) & 1));
+        }
+    } else {
+        // ------------------------------------------------------------ converters
+        const int c = warp - 2;                                  // 0..7
+        const int m = ((warp & 3) << 5) | lane;                  // M row = TMEM lane
+        const int hk = (c >> 2) * (kTsK / 2);                    // this warp's half of the K values
+        const int hq = (c >> 2) * (kNQW / 2);                    // and of the right-hand sides
+        const uint32_t tlane = (uint32_t)((warp & 3) << 5) << 16;
+        const int kb = 4 * c;                                    // B: K values kb..kb+3 of right-hand side lane
+        constexpr int QH = kNQW / 2;
+        Acc<float> acc[QH];
+        float cacc[QH];
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const int kq = k0 + kk, c = cb + kq;
-                    const float v = c < nc ? __ldg(tA + (int64_t)c * kNQW + nn) : 0.f;
-                    float h, l;
-                    split_tf32(v, h, l);
-                    const int off = ((nn >> 3) << 8) + ((kq >> 2) << 7) + ((nn & 7) << 4) + ((kq & 3) << 2);
-                    *reinterpret_cast<float *>(buf + 2 * kTcAOp + off) = h;
-                    *reinterpret_cast<float *>(buf + 2 * kTcAOp + kTcBOp + off) = l;
+        for (int q = 0; q < QH; ++q) cacc[q] = 0.f;
+        struct Pend {   // a stage waiting for its drain
+            int nk, last, mma, corr;   // K values, last of its item, item had MMAs, correction set
+            int a, i;                  // gather: output to t; leaf: this row's leaf (-1: none), row in leaf
+            int64_t o;                 // gather: output row of this thread's column (-1: none)
+        };
+        Pend p1{0, 0, 0, 0, 0, 0, -1}, p2 = p1;
+        int item = 0, item_mma = 0;    // items started, current item had MMAs
+        int lg = -1, li = 0, lbase = 0, lstride = 0;   // leaf: this row's leaf, row, slot base, stride
+        // a completed stage: its main accumulator into the compensated sums, its
+        // first correction into the plain ones; the item's output after its last stage
+        auto drain = [&](const Pend &pd, int set) {
+            if (pd.nk > 0) {
+                float v[QH], w[QH];
+                const uint32_t dm = tmem + tlane + kTmMain + 64u * (uint32_t)set + (uint32_t)hq;
+                tmem_ld16x2(dm, dm + 32u, v, w);
+#pragma unroll
+                for (int q = 0; q < QH; ++q) {
+                    acc[q].add(v[q]);
+                    cacc[q] += w[q];
                 }
             }
+            if (!pd.last) return;
+            float cr[QH];
+            if (pd.mma) {
+                tmem_ld16(tmem + tlane + kTmCorr + 32u * (uint32_t)pd.corr + (uint32_t)hq, cr);
+            } else {
+#pragma unroll
+                for (int q = 0; q < QH; ++q) cr[q] = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < QH; ++q) cr[q] += cacc[q];
+            if constexpr (!kLeaf) {
+                if (pd.o >= 0) {
+                    float *o = (pd.a ? P.t : P.partial) + pd.o * kNQW + hq;
+#pragma unroll
+                    for (int q = 0; q < QH; q += 4)
+                        *reinterpret_cast<float4 *>(o + q) =
+                            make_float4(acc[q].get() + cr[q], acc[q + 1].get() + cr[q + 1], acc[q + 2].get() + cr[q + 2],
+                                        acc[q + 3].get() + cr[q + 3]);
+                }
+            } else if (pd.a >= 0) {
+                const int Zg = (int)(P.A.offL + pd.a);
+                const int zs = P.A.box_start[Zg];
+                if (pd.i < P.A.box_end[Zg] - zs) {
+                    const int64_t o = P.A.perm[zs + pd.i];
+                    const float *nb = P.nearbuf + (int64_t)(zs + pd.i) * kNQW + hq;
+#pragma unroll
+                    for (int q = 0; q < QH; ++q)
+                        if (hq + q < P.nq) P.y[(int64_t)(P.q0 + hq + q) * P.n + o] = (acc[q].get() + cr[q]) + nb[q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < QH; ++q) {
+                acc[q] = Acc<float>{};
+                cacc[q] = 0.f;
+            }
+        };
+
+        for (int s = 0;; ++s) {
+            const int slot = s % kTsSlots, b = s & 1;
+            if (!mbar_wait_or_abort(&full[slot], (uint32_t)((s / kTsSlots) & 1), abort)) break;
+            const TsMeta &M = meta[slot];
+            const int nk = M.nk;
+            if (s >= 2) {   // the MMAs of stage s-2 are done: its operands and accumulator are free
+                if (!mbar_wait_or_abort(&opempty[b], (uint32_t)(((s - 2) >> 1) & 1), abort)) break;
+                tc_fence_after();
+                drain(p2, b);
+            }
+            if (nk < 0) {   // end: stop the issuer, drain the last stage
+                if (c == 0 && lane == 0) opm[b].nks = -1;
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&opfull[b]);
+                if (s >= 1) {
+                    if (!mbar_wait_or_abort(&opempty[b ^ 1], (uint32_t)(((s - 1) >> 1) & 1), abort)) break;
+                    tc_fence_after();
+                    drain(p1, b ^ 1);
+                }
+                break;
+            }
+            if (M.first) {
+                ++item;
+                item_mma = 0;
+                if constexpr (kLeaf) {   // this row's leaf in the new tile
+                    lg = -1;
+                    for (int g = 0; g < M.nl; ++g)
+                        if (m >= M.off[g] && m < M.off[g] + M.ld[g]) lg = g;
+                    if (lg >= 0) {
+                        li = m - M.off[lg];
+                        lbase = 32 * M.off[lg] + li;
+                        lstride = M.ld[lg];
+                    }
+                }
+            }
+            if (nk > 0) item_mma = 1;
+            const int corr = item & 1;
+            Pend cur{nk, M.last, item_mma, corr, 0, 0, -1};
+            if (nk > 0) {
+                const float *ta = reinterpret_cast<const float *>(ring + (size_t)slot * kTsSlot);
+                const float *tb = ta + kTsSlotA / 4;
+                bool live;
+                int base, stride;
+                if constexpr (!kLeaf) {   // A(m, k) = V tile row k, column m (rows of 128 floats)
+                    live = m < M.ncols;
+                    base = m;
+                    stride = kTcCols;
+                } else {                  // A(m, k) = the leaf's U chunk column k, row li
+                    live = lg >= 0 && (M.sel < 0 || M.sel == lg);
+                    base = lbase;
+                    stride = lstride;
+                }
+                float h[16], l[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int k = hk + u;
+                    split_tf32_fast((live && k < nk) ? ta[base + k * stride] : 0.f, h[u], l[u]);
+                }
+                const uint32_t acol = tmem + tlane + kTmA + 64u * (uint32_t)b + (uint32_t)hk;
+                tmem_st16(acol, h);
+                tmem_st16(acol + 32u, l);
+                {
+                    float bh[4], bl[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = kb + u;
+                        split_tf32_fast(k < nk ? tb[k * kNQW + lane] : 0.f, bh[u], bl[u]);
+                    }
+                    unsigned char *bbuf = bops + b * kTsBBuf;
+                    const int off = kmajor_off(lane, kb);
+                    *reinterpret_cast<float4 *>(bbuf + off) = make_float4(bh[0], bh[1], bh[2], bh[3]);
+                    *reinterpret_cast<float4 *>(bbuf + kTsBOp + off) = make_float4(bl[0], bl[1], bl[2], bl[3]);
+                }
+                tmem_st_wait();
+            }
+            if (M.last) {
+                if constexpr (!kLeaf) {
+                    cur.a = M.to_t;
+                    cur.o = M.idx[m];
+                } else {
+                    cur.a = lg >= 0 ? M.z0 + lg : -1;
+                    cur.i = li;
+                }
+            }
+            if (c == 0 && lane == 0) opm[b] = TsOpMeta{(nk + 7) >> 3, M.first, corr};
+            // every lane: its B stores visible to the tensor core, its TMEM stores
+            // ordered before the barrier; then one arrival per warp on each barrier
             fence_async_smem();
             tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
-            if (tid == 0) {
-                const uint32_t abase = smem_addr(buf), bbase = abase + 2 * kTcAOp;
-                const uint64_t ahd = umma_desc(abase, 128, 256), ald = umma_desc(abase + kTcAOp, 128, 256);
-                const uint64_t bh = umma_desc(bbase, 128, 256), bl = umma_desc(bbase + kTcBOp, 128, 256);
-                umma_tf32(tmem + 32u * (uint32_t)(grp & 1), ahd, bh, idesc, s % kTcGroup ? 1u : 0u);
-                umma_tf32(tmem + 64u, ahd, bl, idesc, s > 0 ? 1u : 0u);
-                umma_tf32(tmem + 64u, ald, bh, idesc, 1u);
-                umma_commit(&mbar[b]);
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[slot]);   // the warp is done with the slot
+                mbar_arrive(&opfull[b]);
             }
-            ++issued[b];
+            p2 = p1;
+            p1 = cur;
         }
-    }
-    if (!failed) {
-        bool ok = true;
-        for (int bb = 0; bb < 2; ++bb)
-            while (waited[bb] != issued[bb]) {
-                ok = mbar_wait(&mbar[bb], waited[bb] & 1u) && ok;
-                ++waited[bb];
-            }
-        failed = __syncthreads_or(!ok);
-    }
-    if (!failed) {
-        tc_fence_after();
-        if (s > 0) {
-            const int ngroups = (s + kTcGroup - 1) / kTcGroup;
-            if (ngroups >= 2) drain(ngroups - 2);
-            drain(ngroups - 1);
-            float v[32];
-            tmem_ld32(tmem + tlane + 64u, v);
-#pragma unroll
-            for (int q = 0; q < kNQW; ++q) acc[q].add(v[q]);
-        }
-        const int i = tid;
-        if (i < m) {
-            const int64_t o = A.perm[zs + i];
-#pragma unroll
-            for (int q = 0; q < kNQW; ++q)
-                if (q < nq) y[(int64_t)(q0 + q) * n + o] = acc[q].get() + nearbuf[(int64_t)(zs + i) * kNQW + q];
-        }
-    } else if (tid == 0) {
-        *A.err = H3D_ERR_TIMEOUT;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 128);
+    if (*abort && tid == 0) *P.err = H3D_ERR_TIMEOUT;
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 unsigned gridn(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -1748,20 +1743,37 @@ void matvec_wide(Handle &h, const float *x, float *y, int q0, int nq, cudaStream
     H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
     k_near_w<<<std::min(h.nleaf, 2 * kNearCtasPerSm * num_sms()), kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
     H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
+    TsArgs T{};
+    T.gitems = h.tc_items;
+    T.tmaps = (const unsigned char *)h.tc_tmaps;
+    T.tiles = h.tc_tiles;
+    T.V = (const float *)h.V;
+    T.xs = xs;
+    T.t = t;
+    T.partial = (float *)h.partial_w;
+    T.map_v = h.map_v;
+    T.A = A;
+    T.U = (const float *)h.U;
+    T.tl = t;
+    T.nearbuf = nearbuf;
+    T.y = y;
+    T.n = n;
+    T.q0 = q0;
+    T.nq = nq;
+    T.err = h.d_async_err;
     if (h.ntc_items > 0) {
-        GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
-        const int grid = std::min(h.ntc_items, kTcCtasPerSm * num_sms());
-        k_gather_tc<<<grid, kTcThreads, kTcDynSmem, s>>>(G, h.tc_items, h.ntc_items, (const float *)h.V, xs, t,
-                                                         (float *)h.partial_w, h.d_async_err);
+        T.nitems = h.ntc_items;
+        k_tc_stream<false><<<std::min(h.ntc_items, num_sms()), kTsThreads, kTsDynSmem, s>>>(T);
     }
     if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
-    if (h.nsplit > 0) {
-        SplitArgs S{h.split_box, h.split_ntask, h.split_pbase, h.Rv, h.ldv, h.vcol0, h.map_v};
-        k_reduce_partials_w<<<h.nsplit, 256, 0, s>>>(S, (const float *)h.partial_w, t);
+    if (h.nsplit_w > 0) {
+        SplitArgs S{h.split_box_w, h.split_ntask_w, h.split_pbase_w, h.Rv, h.ldv, h.vcol0, h.map_v};
+        k_reduce_partials_w<<<h.nsplit_w, 256, 0, s>>>(S, (const float *)h.partial_w, t);
     }
     H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
     if (ev) H3D_CUDA(cudaEventRecord(ev[3], s));
-    k_leaf_tc<<<h.nleaf, kTcThreads, kLeafTcDynSmem, s>>>(A, (const float *)h.U, t, nearbuf, y, n, q0, nq);
+    T.nitems = h.ntc_tiles;
+    k_tc_stream<true><<<std::min(h.ntc_tiles, num_sms()), kTsThreads, kTsDynSmem, s>>>(T);
     if (ev) H3D_CUDA(cudaEventRecord(ev[4], s));
     H3D_LAUNCH_CHECK();
 }
@@ -1774,7 +1786,7 @@ void ensure_wide_scratch(Handle &h, cudaStream_t s) {
     h.xs_w = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQW * es);
     h.nearbuf_w = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQW * es);
     h.t_w = h.mem.alloc((size_t)std::max<int64_t>(h.sum_rank, 4) * kNQW * es);
-    h.partial_w = h.mem.alloc((size_t)std::max<int64_t>(h.partial_elems, 4) * kNQW * es);
+    h.partial_w = h.mem.alloc((size_t)std::max<int64_t>(h.partial_elems_w, 4) * kNQW * es);
 }
 
 bool use_wide(const Handle &h, int nrhs, bool transpose) {
@@ -1817,9 +1829,10 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     H3D_CUDA(cudaFuncSetAttribute(k_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
     H3D_CUDA(cudaFuncSetAttribute(k_leaf_mr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
     H3D_CUDA(cudaFuncSetAttribute(k_leaf_mr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
-    H3D_CUDA(cudaFuncSetAttribute(k_leaf_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafDynSmem));
-    H3D_CUDA(cudaFuncSetAttribute(k_gather_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcDynSmem));
-    H3D_CUDA(cudaFuncSetAttribute(k_leaf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeafTcDynSmem));
+    H3D_CUDA(cudaFuncSetAttribute(k_tc_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTsDynSmem));
+    H3D_CUDA(cudaFuncSetAttribute(k_tc_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTsDynSmem));
+    H3D_CUDA(cudaFuncSetAttribute(k_tc_stream<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    H3D_CUDA(cudaFuncSetAttribute(k_tc_stream<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     const int64_t nboxes = h.n_boxes;
     const size_t es = h.elem();
     std::vector<int> Rv(nboxes), ldv(nboxes), bs(nboxes), be(nboxes), R(nboxes), llo(nboxes), lhi(nboxes);
@@ -1868,17 +1881,101 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
         H3D_CUDA(cudaMemcpyAsync(h.gtask, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
         H3D_CUDA(cudaMemcpyAsync(h.gtask_pbase, pbase.data(), pbase.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     }
-    // tensor-core gather work items: (task, block of kTcCols columns)
+    // the 32-column path's own row tasks (tall: kTaskRowsW rows) and splits
+    std::vector<int4> wtasks;
+    std::vector<int64_t> wpbase, wspbase;
+    std::vector<int> wsbox, wsntask;
+    int64_t pelw = 0;
+    for (int64_t g = 0; g < nboxes; ++g) {
+        if (Rv[g] == 0) continue;
+        const int n = be[g] - bs[g];
+        const int nt = (n + kTaskRowsW - 1) / kTaskRowsW;
+        if (nt == 1) {
+            wtasks.push_back(make_int4((int)g, 0, n, 1));
+            wpbase.push_back(-1);
+        } else {
+            const int per = (n + nt - 1) / nt;
+            wsbox.push_back((int)g);
+            wsntask.push_back(nt);
+            wspbase.push_back(pelw);
+            for (int k = 0; k < nt; ++k) {
+                wtasks.push_back(make_int4((int)g, k * per, std::min(n, (k + 1) * per), 0));
+                wpbase.push_back(pelw + (int64_t)k * ldv[g]);
+            }
+            pelw += (int64_t)nt * ldv[g];
+        }
+    }
+    h.nsplit_w = (int)wsbox.size();
+    h.split_box_w = h.mem.get<int>(std::max<size_t>(wsbox.size(), 1));
+    h.split_ntask_w = h.mem.get<int>(std::max<size_t>(wsbox.size(), 1));
+    h.split_pbase_w = h.mem.get<int64_t>(std::max<size_t>(wsbox.size(), 1));
+    if (!wsbox.empty()) {
+        H3D_CUDA(cudaMemcpyAsync(h.split_box_w, wsbox.data(), wsbox.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.split_ntask_w, wsntask.data(), wsbox.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.split_pbase_w, wspbase.data(), wsbox.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                 s));
+    }
+    h.partial_elems_w = pelw;
+    // tensor-core gather work items: (wide task, block of kTcCols columns), resolved,
+    // and one 2-D tensor map per source box (FP32 handles whose leaves fit the
+    // 32-column path only)
     {
-        std::vector<int2> items;
-        for (size_t q = 0; q < tasks.size(); ++q) {
-            const int nb = (Rv[tasks[q].x] + kTcCols - 1) / kTcCols;
-            for (int cb = 0; cb < nb; ++cb) items.push_back(make_int2((int)q, cb));
+        std::vector<int64_t> vb(nboxes);
+        H3D_CUDA(cudaMemcpyAsync(vb.data(), h.vbase, nboxes * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        std::vector<int64_t> vc0(nboxes);
+        H3D_CUDA(cudaMemcpyAsync(vc0.data(), h.vcol0, nboxes * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        H3D_CUDA(cudaStreamSynchronize(s));
+        const bool wide = h.prec == H3D_FP32 && h.leaf_size <= kMaxLeafW;
+        std::vector<int> tmap_of(nboxes, -1);
+        std::vector<CUtensorMap> tmaps;
+        if (wide) {
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q{};
+            H3D_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+            if (!fn || q != cudaDriverEntryPointSuccess) throw Error{H3D_ERR_CUDA};   // driver without tensor maps
+            auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+            for (int64_t g = 0; g < nboxes; ++g) {
+                if (Rv[g] == 0) continue;
+                CUtensorMap tm;
+                const cuuint64_t dims[2] = {(cuuint64_t)ldv[g], (cuuint64_t)(be[g] - bs[g])};
+                const cuuint64_t strides[1] = {(cuuint64_t)ldv[g] * sizeof(float)};
+                const cuuint32_t box[2] = {(cuuint32_t)kTcCols, (cuuint32_t)kTsK};
+                const cuuint32_t estr[2] = {1, 1};
+                const CUresult r = encode(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (float *)h.V + vb[g], dims, strides,
+                                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) throw Error{H3D_ERR_CUDA};
+                tmap_of[g] = (int)tmaps.size();
+                tmaps.push_back(tm);
+            }
+        }
+        h.tc_tmaps = h.mem.get<unsigned char>(std::max<size_t>(tmaps.size(), 1) * sizeof(CUtensorMap));
+        if (!tmaps.empty())
+            H3D_CUDA(cudaMemcpyAsync(h.tc_tmaps, tmaps.data(), tmaps.size() * sizeof(CUtensorMap),
+                                     cudaMemcpyHostToDevice, s));
+        std::vector<TcGatherItem> items;
+        for (size_t q = 0; wide && q < wtasks.size(); ++q) {
+            const int Y = wtasks[q].x;
+            const int nb = (Rv[Y] + kTcCols - 1) / kTcCols;
+            for (int cb = 0; cb < nb; ++cb) {
+                const int c_lo = cb * kTcCols;
+                TcGatherItem g{};
+                g.x = (int64_t)bs[Y] + wtasks[q].y;
+                g.to_t = wtasks[q].w;
+                g.o = g.to_t ? vc0[Y] + c_lo : wpbase[q] + c_lo;
+                g.tmap = tmap_of[Y];
+                g.c_lo = c_lo;
+                g.r0 = wtasks[q].y;
+                g.nrows = wtasks[q].z - wtasks[q].y;
+                g.ncols = std::min(kTcCols, Rv[Y] - c_lo);
+                items.push_back(g);
+            }
         }
         h.ntc_items = (int)items.size();
-        h.tc_items = h.mem.get<int2>(std::max<size_t>(items.size(), 1));
+        h.tc_items = h.mem.get<TcGatherItem>(std::max<size_t>(items.size(), 1));
         if (!items.empty())
-            H3D_CUDA(cudaMemcpyAsync(h.tc_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+            H3D_CUDA(cudaMemcpyAsync(h.tc_items, items.data(), items.size() * sizeof(TcGatherItem),
+                                     cudaMemcpyHostToDevice, s));
     }
     h.nsplit = (int)sbox.size();
     h.split_box = h.mem.get<int>(std::max<size_t>(sbox.size(), 1));
@@ -1915,6 +2012,26 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     if (L > 0)
         H3D_CUDA(cudaMemcpyAsync(anc.data(), h.leaf_anc, anc.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
     H3D_CUDA(cudaStreamSynchronize(s));
+    {   // far-field tiles: consecutive sibling leaves whose rows fit in 128
+        std::vector<int> lld(nleaf);
+        H3D_CUDA(cudaMemcpyAsync(lld.data(), h.leaf_ld, nleaf * sizeof(int), cudaMemcpyDeviceToHost, s));
+        H3D_CUDA(cudaStreamSynchronize(s));
+        std::vector<int2> tiles;
+        for (int z = 0; z < nleaf;) {
+            const int parent = L >= 2 ? anc[(size_t)(L - 2) * nleaf + z] : 0;
+            int nl = 1, rows = lld[z];
+            while (z + nl < nleaf && nl < kTileLeaves && rows + lld[z + nl] <= 128 &&
+                   (L >= 2 ? anc[(size_t)(L - 2) * nleaf + z + nl] : 0) == parent) {
+                rows += lld[z + nl];
+                ++nl;
+            }
+            tiles.push_back(make_int2(z, nl));
+            z += nl;
+        }
+        h.ntc_tiles = (int)tiles.size();
+        h.tc_tiles = h.mem.get<int2>(std::max<size_t>(tiles.size(), 1));
+        H3D_CUDA(cudaMemcpyAsync(h.tc_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    }
     std::vector<int64_t> tpb((size_t)std::max(1, L) * nleaf, 0);
     int64_t tel = 0;
     std::vector<int> tsb, tsl;

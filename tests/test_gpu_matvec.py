@@ -241,3 +241,21 @@ def test_wide_blocks_of_32_columns():
     assert rel(Y[:, :3], ref) <= 1e-6
     for c in (0, 17, 31, 32, 39):
         assert rel(Y[:, c], gpu_apply(A, np.ascontiguousarray(x[:, c]))) <= 1e-6
+
+
+@pytest.mark.parametrize("case,pts,leaf,mode", [
+    ("one_leaf", I.uniform(100, 101), 128, "hodlr3d"),          # L = 0: no far field, no gather work
+    ("no_far_field", I.uniform(600, 102), 128, "strong"),       # L = 1 strong: every leaf without far field
+    ("sphere_ragged", I.sphere(20000, 103) * 0.99, 128, "hodlr3d"),
+    ("hodlr_long_rows", I.uniform(12000, 104), 100, "weak"),    # level-1 blocks: many stages per item
+])
+def test_wide_edge_cases(case, pts, leaf, mode):
+    n = pts.shape[0]
+    A = H(pts, leaf_size=leaf, tol=1e-7, precision="fp32", admissibility=mode)
+    x = I.rhs_normal(n, 33, 105).astype(np.float32)
+    Y = gpu_apply(A, x)
+    cols = [0, 13, 31, 32]
+    ref = O.direct(pts, x[:, cols].astype(np.float64))
+    assert rel(Y[:, cols], ref) <= 1e-6, case
+    for c in (0, 31):
+        assert rel(Y[:, c], gpu_apply(A, np.ascontiguousarray(x[:, c]))) <= 1e-6, case
