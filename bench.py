@@ -32,9 +32,12 @@ from paper_2307_16303_gb300 import inputs as I  # noqa: E402
 METRIC = "HODLR3D matvec ms @N=1M rel.err<=1e-6 (FP32 factors; plain FP64 beside it), %HBM peak"
 FALLBACK_HBM_GBS = 6800.0
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
-# of the unchanged kernel on this workload (None when not captured).
-NCU_TRAFFIC_BYTES: dict = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch divided by the launch's
+# algorithmic bytes, from one ncu capture of the unchanged kernels on the
+# N = 125,000 uniform case (same per-leaf shape as N = 1M; FP32, one right-hand
+# side): traffic grows with the factor entries, so a launch's traffic is this
+# ratio times its algorithmic bytes.  Kernels without a capture report None.
+NCU_TRAFFIC_RATIO: dict = {"k_leaf": 1.052, "k_gather": 1.055}
 
 
 def parse():
@@ -247,7 +250,9 @@ def main():
     total_bytes = passes * s * (st["u_entries"] + st["v_entries"]) + (4 * s * nrhs + 20) * N
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-            "traffic": NCU_TRAFFIC_BYTES.get(dom), "alg_bytes_per_launch": int(alg_bytes[dom]),
+            "traffic": (int(NCU_TRAFFIC_RATIO[dom] * alg_bytes[dom]) if nrhs == 1 and dom in NCU_TRAFFIC_RATIO
+                        else None),
+            "alg_bytes_per_launch": int(alg_bytes[dom]),
             "launch_ms": round(dom_ms, 4)}
     phase_ms = {n: round(v / passes, 4) for n, v in zip(names, phases)}
 
