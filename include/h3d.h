@@ -123,6 +123,18 @@ h3d_status h3d_matvec(h3d_handle h, const void *x, void *y, int nrhs, void *stre
  * compressed on its own, as Alg. 1 does).  Arguments as h3d_matvec.          */
 h3d_status h3d_matvec_T(h3d_handle h, const void *x, void *y, int nrhs, void *stream);
 
+/* Energy of charges q and its gradient (differentiation of the product):
+ *   E = 1/2 q^T A~ q,   grad = dE/dq = 1/2 (A~ + A~^T) q
+ * with A~ the operator of h3d_matvec (Alg. 2); both products are taken because
+ * A~ is not exactly symmetric (Alg. 1 compresses every ordered pair on its own).
+ *   q     device, N values in the caller's order (read only).
+ *   E     device, one double: the energy, reduced in FP64 in a fixed order.
+ *   grad  device, N values (element type of the handle), overwritten; NULL skips
+ *         the transpose product and the gradient.  Must not alias q.
+ * Enqueues on `stream`; the first call allocates (and keeps) 2N values of
+ * scratch after synchronising `stream`.                                       */
+h3d_status h3d_energy(h3d_handle h, const void *q, double *E, void *grad, void *stream);
+
 /* h3d_matvec with HOST x and y: copies x to the device, runs the product and
  * copies y back, all on `stream`, then synchronises the stream.  Device staging
  * buffers are allocated on the first call (and grown if nrhs grows) and kept by

@@ -146,6 +146,15 @@ h3d_status h3d_matvec_T(h3d_handle h, const void *x, void *y, int nrhs, void *st
     return matvec_common(h, x, y, nrhs, stream, true);
 }
 
+h3d_status h3d_energy(h3d_handle hh, const void *q, double *E, void *grad, void *stream) {
+    if (!hh) return H3D_ERR_ARG;
+    Handle &h = hh->h;
+    if (!h.ok) return H3D_ERR_STATE;
+    if (h3d_status e = async_error(h)) return e;
+    if (!q || !E || q == grad) return H3D_ERR_ARG;
+    return guard([&] { h3d::energy(h, q, E, grad, as_stream(stream)); });
+}
+
 h3d_status h3d_matvec_host(h3d_handle hh, const void *x_host, void *y_host, int nrhs, void *stream) {
     if (!hh) return H3D_ERR_ARG;
     Handle &h = hh->h;

@@ -225,6 +225,8 @@ struct Handle {
     int *tsplit_box = nullptr, *tsplit_level = nullptr;
 
     // host staging for h3d_matvec_host
+    void *ey = nullptr, *eyT = nullptr;           // energy scratch: A~ q, A~^T q (N each)
+    double *epart = nullptr;                      // energy partial sums
     void *hx = nullptr, *hy = nullptr;
     int64_t host_cols = 0;
 
@@ -321,6 +323,7 @@ void build_lists(Handle &h, cudaStream_t s, Arena &tmp);                        
 void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget);      // h3d_aca.cu
 void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp);                   // h3d_matvec.cu
 int matvec_passes(const Handle &h, int nrhs, bool transpose);  // kernel sequences one product launches
+void energy(Handle &h, const void *q, double *E, void *grad, cudaStream_t s);
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s,
                 cudaEvent_t *ev = nullptr);  // h3d_matvec.cu; ev: 5 events per rhs
 
