@@ -847,3 +847,153 @@ int h3do_apply(const h3do_t *h, const double *x, int nrhs, double *y, int transp
     free(xs_); free(ys_);
     return st;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Forces: the gradient with respect to the point positions of the energy
+ *   E = 1/2 q^T K~ q,
+ * where K~ holds the exact near blocks and, for every admissible block
+ * (X, Y) with its pivots frozen, the cross (skeleton) form of Eq. prank,
+ *   K(X,Y) ~ K(X,tau) M^{-1} K(sigma,Y),   M = K(sigma,tau).
+ * With s = K(sigma,Y) q_Y, c = M^{-1} s, u = K(X,tau)^T q_X, a = M^{-T} u, the
+ * block's energy 1/2 q_X^T K(X,tau) c has the differential
+ *   1/2 [ q_X^T dK(X,tau) c + a^T dK(sigma,Y) q_Y - a^T dM c ]
+ * (d(M^{-1}) = -M^{-1} dM M^{-1}).  Every kernel entry K(p_i, p_j) = f(|p_i - p_j|)
+ * differentiates to  g = f'(rho) (p_i - p_j) / rho  for p_i and -g for p_j; the
+ * near blocks contribute 1/2 q_i q_j K(p_i, p_j) for every ordered pair.  The
+ * sums run serially in a fixed order.                                        */
+static void kernel_grad(int kind, double kappa, const double *a, const double *b, double *g)
+{
+    double d[3] = {a[0] - b[0], a[1] - b[1], a[2] - b[2]};
+    double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double r, fp;
+    g[0] = g[1] = g[2] = 0.0;
+    if (d2 == 0.0) return;
+    r = sqrt(d2);
+    switch (kind) {
+    case KER_LAPLACE: fp = -ORC_ONE_OVER_FOUR_PI / d2; break;                                  /* f = 1/(4 pi r)       */
+    case KER_YUKAWA:  fp = -ORC_ONE_OVER_FOUR_PI * exp(-kappa * r) * (1.0 + kappa * r) / d2; break;
+    case KER_INV_R4:  fp = -4.0 / (d2 * d2 * r); break;                                        /* f = r^-4             */
+    case KER_COS_R:   fp = -(r * sin(r) + cos(r)) / d2; break;                                 /* f = cos r / r        */
+    default:          fp = NAN;
+    }
+    for (int k = 0; k < 3; ++k) g[k] = fp * d[k] / r;
+}
+
+/* Solve A z = rhs for an n x n row-major A by Gaussian elimination with
+ * partial pivoting (A and rhs are overwritten).  Returns 0 on success.       */
+static int dense_solve(int n, double *A, double *rhs)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (fabs(A[(size_t)i * n + k]) > fabs(A[(size_t)p * n + k])) p = i;
+        if (A[(size_t)p * n + k] == 0.0) return 1;
+        if (p != k) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[(size_t)k * n + j]; A[(size_t)k * n + j] = A[(size_t)p * n + j]; A[(size_t)p * n + j] = t;
+            }
+            { double t = rhs[k]; rhs[k] = rhs[p]; rhs[p] = t; }
+        }
+        for (int i = k + 1; i < n; ++i) {
+            double f = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+            for (int j = k; j < n; ++j) A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+            rhs[i] -= f * rhs[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        double s = rhs[k];
+        for (int j = k + 1; j < n; ++j) s -= A[(size_t)k * n + j] * rhs[j];
+        rhs[k] = s / A[(size_t)k * n + k];
+    }
+    return 0;
+}
+
+/* E (scalar) and dE/dp (N x 3, row-major, the caller's point order) for charges
+ * q (N, the caller's order); pivots must be present (compress or set_pivots). */
+int h3do_energy_forces(const h3do_t *h, const double *q, double *E_out, double *grad)
+{
+    const int64_t N = h->N;
+    const int kind = h->kind;
+    const double kap = h->kappa;
+    double *qs, *G, E = 0.0;
+    if (!h->have_pivots) return ST_ARG;
+    qs = (double *)malloc((size_t)N * sizeof(double));
+    G = (double *)calloc((size_t)N * 3, sizeof(double));
+    if (!qs || !G) { free(qs); free(G); return ST_OOM; }
+    for (int64_t s = 0; s < N; ++s) qs[s] = q[h->perm[s]];
+
+    /* near blocks: every ordered pair (i, j), i != j, of each near pair of leaves */
+    {
+        const int64_t o = h->box_off[h->L];
+        for (int64_t p = 0; p < h->lists.n_near; ++p) {
+            int64_t t = o + h->lists.near_tgt[p], sb = o + h->lists.near_src[p];
+            for (int64_t i = h->box_start[t]; i < h->box_end[t]; ++i)
+                for (int64_t j = h->box_start[sb]; j < h->box_end[sb]; ++j) {
+                    double g[3], w;
+                    if (i == j) continue;
+                    w = 0.5 * qs[i] * qs[j];
+                    E += w * kernel_f(kind, kap, h->pts + 3 * i, h->pts + 3 * j);
+                    kernel_grad(kind, kap, h->pts + 3 * i, h->pts + 3 * j, g);
+                    for (int k = 0; k < 3; ++k) { G[3 * i + k] += w * g[k]; G[3 * j + k] -= w * g[k]; }
+                }
+        }
+    }
+    /* admissible blocks in the cross form */
+    for (int64_t b = 0; b < h->lists.n_blocks; ++b) {
+        int64_t x0, y0;
+        int m, n, r = h->rank[b];
+        const int *sg = h->sigma + h->piv_off[b], *ta = h->tau + h->piv_off[b];
+        double *M, *Mt, *c, *a, g[3];
+        if (r == 0) continue;
+        block_ranges(h, b, &x0, &m, &y0, &n);
+        M = (double *)malloc((size_t)r * r * sizeof(double));
+        Mt = (double *)malloc((size_t)r * r * sizeof(double));
+        c = (double *)malloc((size_t)r * sizeof(double));
+        a = (double *)malloc((size_t)r * sizeof(double));
+        for (int k = 0; k < r; ++k) {
+            double sk = 0.0, uk = 0.0;
+            for (int j = 0; j < n; ++j) sk += kernel_f(kind, kap, h->pts + 3 * (x0 + sg[k]), h->pts + 3 * (y0 + j)) * qs[y0 + j];
+            for (int i = 0; i < m; ++i) uk += qs[x0 + i] * kernel_f(kind, kap, h->pts + 3 * (x0 + i), h->pts + 3 * (y0 + ta[k]));
+            c[k] = sk;
+            a[k] = uk;
+            for (int l = 0; l < r; ++l) {
+                double v = kernel_f(kind, kap, h->pts + 3 * (x0 + sg[k]), h->pts + 3 * (y0 + ta[l]));
+                M[(size_t)k * r + l] = v;
+                Mt[(size_t)l * r + k] = v;
+            }
+        }
+        if (dense_solve(r, M, c) || dense_solve(r, Mt, a)) {
+            free(M); free(Mt); free(c); free(a); free(qs); free(G);
+            return ST_RANK;
+        }
+        for (int i = 0; i < m; ++i) {        /* q_X^T K(X,tau) c: energy and first term */
+            for (int k = 0; k < r; ++k) {
+                const double *pi = h->pts + 3 * (x0 + i), *pk = h->pts + 3 * (y0 + ta[k]);
+                double w = 0.5 * qs[x0 + i] * c[k];
+                E += w * kernel_f(kind, kap, pi, pk);
+                kernel_grad(kind, kap, pi, pk, g);
+                for (int d = 0; d < 3; ++d) { G[3 * (x0 + i) + d] += w * g[d]; G[3 * (y0 + ta[k]) + d] -= w * g[d]; }
+            }
+        }
+        for (int k = 0; k < r; ++k)          /* a^T dK(sigma,Y) q_Y */
+            for (int j = 0; j < n; ++j) {
+                const double *pk = h->pts + 3 * (x0 + sg[k]), *pj = h->pts + 3 * (y0 + j);
+                double w = 0.5 * a[k] * qs[y0 + j];
+                kernel_grad(kind, kap, pk, pj, g);
+                for (int d = 0; d < 3; ++d) { G[3 * (x0 + sg[k]) + d] += w * g[d]; G[3 * (y0 + j) + d] -= w * g[d]; }
+            }
+        for (int k = 0; k < r; ++k)          /* - a^T dM c */
+            for (int l = 0; l < r; ++l) {
+                const double *pk = h->pts + 3 * (x0 + sg[k]), *pl = h->pts + 3 * (y0 + ta[l]);
+                double w = -0.5 * a[k] * c[l];
+                kernel_grad(kind, kap, pk, pl, g);
+                for (int d = 0; d < 3; ++d) { G[3 * (x0 + sg[k]) + d] += w * g[d]; G[3 * (y0 + ta[l]) + d] -= w * g[d]; }
+            }
+        free(M); free(Mt); free(c); free(a);
+    }
+    for (int64_t s = 0; s < N; ++s)
+        for (int d = 0; d < 3; ++d) grad[3 * h->perm[s] + d] = G[3 * s + d];
+    *E_out = E;
+    free(qs); free(G);
+    return ST_OK;
+}

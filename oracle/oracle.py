@@ -11,7 +11,9 @@ Functions and the passage of arXiv 2307.16303 each one follows:
   y_i = sum_{j != i} f(|r_i - r_j|) x_j.
 * :func:`morton` -- Sec. 2.1 recursive subdivision of B = [-1, 1]^3.
 * :class:`Oracle` -- Alg. 1 (tree, interaction lists, ACA pivots, Sec. 4.1
-  Eq. prank) and Alg. 2 (matrix-vector product and its transpose); with
+  Eq. prank) and Alg. 2 (matrix-vector product and its transpose); the energy
+  q^T K~ q / 2 and its gradient in the point positions with the pivots frozen
+  (the cross form of Eq. prank differentiated entry by entry); with
   ``admissibility="strong"`` / ``"weak"`` the paper's comparison formats on the
   same octree (H-matrix with eta = sqrt(3), Eq. adm; HODLR, Sec. 2.3).
 
@@ -96,6 +98,7 @@ def _load():
             "h3do_block_geometry": (i32, [P, i64, C.POINTER(i64), C.POINTER(C.c_int),
                                           C.POINTER(i64), C.POINTER(C.c_int)]),
             "h3do_apply": (i32, [P, P, i32, P, i32]),
+            "h3do_energy_forces": (i32, [P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -267,6 +270,17 @@ class Oracle:
         y = np.zeros((self.N, nrhs), np.float64, order="F")
         _check(_load().h3do_apply(self._h, _ptr(xf), nrhs, _ptr(y), 1 if transpose else 0))
         return y[:, 0] if vec else y
+
+    # --- forces: gradient of E = q^T K~ q / 2 in the point positions -------
+    def energy_forces(self, q) -> tuple[float, np.ndarray]:
+        """E and dE/dp (N x 3, the caller's order) with the pivots frozen: near
+        blocks exact, admissible blocks in the cross form K(X,tau) K(sigma,tau)^{-1}
+        K(sigma,Y) of Eq. prank, every kernel entry differentiated."""
+        qf = np.ascontiguousarray(q, np.float64).reshape(self.N)
+        E = np.zeros(1, np.float64)
+        G = np.zeros((self.N, 3), np.float64)
+        _check(_load().h3do_energy_forces(self._h, _ptr(qf), _ptr(E), _ptr(G)))
+        return float(E[0]), G
 
     def sorted_points(self) -> np.ndarray:
         return self.points[self.tree()["perm"]]
