@@ -135,6 +135,21 @@ h3d_status h3d_matvec_T(h3d_handle h, const void *x, void *y, int nrhs, void *st
  * scratch after synchronising `stream`.                                       */
 h3d_status h3d_energy(h3d_handle h, const void *q, double *E, void *grad, void *stream);
 
+/* Forces on the points for the same energy, F = -dE/dp, with the ACA pivots of
+ * the build frozen: the near blocks are exact kernel entries and each
+ * admissible block (X, Y) is the cross form K(X,tau) K(sigma,tau)^{-1} K(sigma,Y)
+ * of its pivots (Sec. 4.1, Eq. prank), so E is the energy of the paper's
+ * representation (it equals that of h3d_energy up to rounding times the
+ * condition of K(sigma,tau)).  Kernel entries and their gradients are
+ * recomputed in FP64 (nothing is stored); K(sigma,tau) is factored in FP64 with
+ * partial pivoting.  Supported for every kernel of h3d_kernel.
+ *   q  device, N charges in the caller's order (element type of the handle).
+ *   E  device, one double: the energy.
+ *   F  device, N x 3 doubles, row-major, the caller's order; overwritten.
+ * Enqueues on `stream`; the first call allocates (and keeps) O(N) doubles and a
+ * scratch of max_rank^2 doubles per CTA after synchronising `stream`.          */
+h3d_status h3d_forces(h3d_handle h, const void *q, double *E, double *F, void *stream);
+
 /* h3d_matvec with HOST x and y: copies x to the device, runs the product and
  * copies y back, all on `stream`, then synchronises the stream.  Device staging
  * buffers are allocated on the first call (and grown if nrhs grows) and kept by

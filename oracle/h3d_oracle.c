@@ -997,3 +997,23 @@ int h3do_energy_forces(const h3do_t *h, const double *q, double *E_out, double *
     free(qs); free(G);
     return ST_OK;
 }
+
+/* Exact forces of the dense energy E = 1/2 q^T K q on selected points:
+ * F_i = -dE/dp_i = -sum_{j != i} q_i q_j f'(|p_i - p_j|) (p_i - p_j) / |p_i - p_j|,
+ * points and charges in the caller's order, out: nrows x 3.                  */
+int h3do_direct_forces_rows(int kind, double kappa, const double *pts, int64_t N, const double *q,
+                            const int64_t *rows, int64_t nrows, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t i = rows[r];
+        double acc[3] = {0.0, 0.0, 0.0}, g[3];
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            kernel_grad(kind, kappa, pts + 3 * i, pts + 3 * j, g);
+            for (int d = 0; d < 3; ++d) acc[d] += q[j] * g[d];
+        }
+        for (int d = 0; d < 3; ++d) out[3 * r + d] = -q[i] * acc[d];
+    }
+    return ST_OK;
+}

@@ -9,6 +9,8 @@ Functions and the passage of arXiv 2307.16303 each one follows:
 
 * :func:`direct`, :func:`direct_rows` -- O1, the dense sum of Eq. (Laplace3D):
   y_i = sum_{j != i} f(|r_i - r_j|) x_j.
+* :func:`direct_forces_rows` -- the gradient of O1's energy q^T K q / 2 in the
+  point positions (exact forces on selected points).
 * :func:`morton` -- Sec. 2.1 recursive subdivision of B = [-1, 1]^3.
 * :class:`Oracle` -- Alg. 1 (tree, interaction lists, ACA pivots, Sec. 4.1
   Eq. prank) and Alg. 2 (matrix-vector product and its transpose); the energy
@@ -44,6 +46,17 @@ ADMISSIBILITY = {"hodlr3d": 0, "strong": 1, "weak": 2}
 STATUS = {0: "ok", 1: "bad argument", 2: "point outside the domain", 3: "out of memory",
           5: "ACA rank cap reached", 8: "tree deeper than 21 levels"}
 CLS_NAMES = {0: "self", 1: "face", 2: "edge", 3: "vertex", 4: "far"}
+
+
+def direct_forces_rows(points, q, rows, kernel: str = "laplace", kappa: float = 1.0) -> np.ndarray:
+    """Exact forces -dE/dp_i of the dense energy q^T K q / 2 on the given points (O1's gradient)."""
+    p = np.ascontiguousarray(points, np.float64)
+    qf = np.ascontiguousarray(q, np.float64).reshape(p.shape[0])
+    r = np.ascontiguousarray(rows, np.int64)
+    out = np.zeros((r.shape[0], 3), np.float64)
+    _check(_load().h3do_direct_forces_rows(KERNELS[kernel], kappa, _ptr(p), p.shape[0], _ptr(qf), _ptr(r),
+                                           r.shape[0], _ptr(out)))
+    return out
 
 
 class OracleError(RuntimeError):
@@ -99,6 +112,7 @@ def _load():
                                           C.POINTER(i64), C.POINTER(C.c_int)]),
             "h3do_apply": (i32, [P, P, i32, P, i32]),
             "h3do_energy_forces": (i32, [P, P, P, P]),
+            "h3do_direct_forces_rows": (i32, [i32, f64, P, i64, P, P, i64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

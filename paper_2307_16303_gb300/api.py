@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_
 # every entry point declared in include/h3d.h
 EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3d_matvec_host", "h3d_free",
            "h3d_status_string", "h3d_get_stats", "h3d_matvec_profile", "h3d_export_tree", "h3d_export_lists",
-           "h3d_export_pivots", "h3d_morton_order_noalloc", "h3d_energy")
+           "h3d_export_pivots", "h3d_morton_order_noalloc", "h3d_energy", "h3d_forces")
 
 
 class H3DError(RuntimeError):
@@ -78,6 +78,7 @@ def lib():
             "h3d_export_pivots": (i32, [P, P, P, P]),
             "h3d_morton_order_noalloc": (i32, [P, i64, P, f64, P, P, P]),
             "h3d_energy": (i32, [P, P, P, P, P]),
+            "h3d_forces": (i32, [P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -180,6 +181,21 @@ class H3DMatrix:
         if st != 0:
             raise H3DError(st, "h3d_energy")
         return (E, g) if grad else E
+
+    def forces(self, q, stream=None):
+        """E (0-d FP64 CUDA tensor) and the forces F = -dE/dp (N x 3 FP64) for charges q,
+        with the ACA pivots frozen (cross form of the admissible blocks)."""
+        import torch
+        self._check_x(q)
+        if q.dim() != 1:
+            raise ValueError("q must be one column")
+        qc = q.contiguous()
+        E = torch.empty((), dtype=torch.float64, device=q.device)
+        F = torch.empty((self.N, 3), dtype=torch.float64, device=q.device)
+        st = lib().h3d_forces(self._h, qc.data_ptr(), E.data_ptr(), F.data_ptr(), _stream_ptr(stream))
+        if st != 0:
+            raise H3DError(st, "h3d_forces")
+        return E, F
 
     def matvec_raw(self, x_ptr: int, y_ptr: int, nrhs: int, stream=None, transpose: bool = False):
         """Call the C ABI directly on device pointers (column-major N x nrhs)."""

@@ -155,6 +155,15 @@ h3d_status h3d_energy(h3d_handle hh, const void *q, double *E, void *grad, void 
     return guard([&] { h3d::energy(h, q, E, grad, as_stream(stream)); });
 }
 
+h3d_status h3d_forces(h3d_handle hh, const void *q, double *E, double *F, void *stream) {
+    if (!hh) return H3D_ERR_ARG;
+    Handle &h = hh->h;
+    if (!h.ok) return H3D_ERR_STATE;
+    if (h3d_status e = async_error(h)) return e;
+    if (!q || !E || !F) return H3D_ERR_ARG;
+    return guard([&] { h3d::forces(h, q, E, F, as_stream(stream)); });
+}
+
 h3d_status h3d_matvec_host(h3d_handle hh, const void *x_host, void *y_host, int nrhs, void *stream) {
     if (!hh) return H3D_ERR_ARG;
     Handle &h = hh->h;

@@ -227,6 +227,8 @@ struct Handle {
     // host staging for h3d_matvec_host
     void *ey = nullptr, *eyT = nullptr;           // energy scratch: A~ q, A~^T q (N each)
     double *epart = nullptr;                      // energy partial sums
+    double *fqs = nullptr, *fG = nullptr;         // forces: charges and dE/dp in Morton order
+    double *fE = nullptr, *fM = nullptr;          // forces: energy partials, K(sigma,tau) scratch
     void *hx = nullptr, *hy = nullptr;
     int64_t host_cols = 0;
 
@@ -324,6 +326,7 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget);      
 void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp);                   // h3d_matvec.cu
 int matvec_passes(const Handle &h, int nrhs, bool transpose);  // kernel sequences one product launches
 void energy(Handle &h, const void *q, double *E, void *grad, cudaStream_t s);
+void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s);
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s,
                 cudaEvent_t *ev = nullptr);  // h3d_matvec.cu; ev: 5 events per rhs
 

@@ -98,3 +98,29 @@ def test_compressed_gradient_by_central_differences():
             assert abs(fd - G[i, d]) <= 1e-5 * np.abs(G[i]).max() + 1e-9
             checked += 1
     assert checked >= 30
+
+
+@pytest.mark.parametrize("kern", ["laplace", "yukawa", "inv_r4", "cos_r"])
+def test_direct_forces_by_central_differences(kern):
+    p = I.uniform(300, 239)
+    q = I.rhs_uniform(300, 1, 240)[:, 0]
+    rows = np.array([0, 7, 123, 299])
+    F = O.direct_forces_rows(p, q, rows, kernel=kern, kappa=0.9)
+    h = 1e-6
+    for r, i in enumerate(rows):
+        for d in range(3):
+            pp, pm = p.copy(), p.copy()
+            pp[i, d] += h
+            pm[i, d] -= h
+            ep = 0.5 * q @ O.direct(pp, q, kernel=kern, kappa=0.9)
+            em = 0.5 * q @ O.direct(pm, q, kernel=kern, kappa=0.9)
+            assert abs(-(ep - em) / (2 * h) - F[r, d]) <= 1e-6 * np.abs(F[r]).max() + 1e-9
+
+
+def test_full_rank_forces_equal_direct_forces():
+    p = I.uniform(500, 241)
+    q = I.rhs_uniform(500, 1, 242)[:, 0]
+    o = O.Oracle(p, leaf_size=9, tol=0.0).compress()
+    _, G = o.energy_forces(q)
+    F = O.direct_forces_rows(p, q, np.arange(500))
+    assert np.abs(-G - F).max() <= 1e-9 * np.abs(F).max()
