@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     p.add_argument("--rows", type=int, default=10_000, help="sampled rows for the error / CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the baseline leg")
+    p.add_argument("--forces", action="store_true",
+                   help="also time the energy and forces (charges ~ U(-1,1) FP32, pivots frozen) and check them "
+                        "against the exact dense forces on 4,096 sampled points")
     return p.parse_args()
 
 
@@ -271,6 +274,25 @@ def main():
     y_host = y.cpu().numpy().T          # N x nrhs
     if nrhs == 1:
         y_host = y_host.reshape(-1)
+    forces = None
+    if a.forces:
+        qh = I.rhs_uniform(a.N, 1, 6 + 1000 * rank)[:, 0].astype(np.float32)
+        qd = torch.from_numpy(qh).cuda()
+        Fo = {}
+        def force_step():
+            Fo["E"], Fo["F"] = A.forces(qd)
+        f_ms = time_steps(force_step, max(1, a.steps // 4), 1, torch, None)
+        e_ms = time_steps(lambda: A.energy(qd), a.steps, a.warmup, torch, None)
+        forces = {"forces_ms": round(f_ms, 3), "energy_grad_q_ms": round(e_ms, 3),
+                  "energy": Fo["E"].item()}
+        if rank == 0:
+            from oracle import oracle as O
+            frows = I.sample_rows(a.N, 4096, 7)
+            Fx = O.direct_forces_rows(pts, qh.astype(np.float64), frows)
+            Fg = Fo["F"].cpu().numpy()[frows]
+            forces["rel_err_4096_points"] = float(np.linalg.norm(Fg - Fx) / np.linalg.norm(Fx))
+            forces["sum_of_forces_rel"] = float(np.abs(Fo["F"].sum(dim=0).cpu().numpy()).max()
+                                                / Fo["F"].abs().sum().item())
     A.free()
     del A
     torch.cuda.empty_cache()
@@ -311,7 +333,7 @@ def main():
         "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload(a),
-        "rel_err_sampled_rows": err, "fp64": fp64,
+        "rel_err_sampled_rows": err, "fp64": fp64, "forces": forces,
         "speedup_vs_fp64": (round(fp64["ms"] / ms, 3) if fp64 and fp64.get("ms") else None),
         "interactions_per_s": N * N * nrhs / (ms * 1e-3),
         "matvec_alg_GBps": round(total_bytes / (ms * 1e-3) / 1e9, 1),

@@ -141,8 +141,10 @@ h3d_status h3d_energy(h3d_handle h, const void *q, double *E, void *grad, void *
  * of its pivots (Sec. 4.1, Eq. prank), so E is the energy of the paper's
  * representation (it equals that of h3d_energy up to rounding times the
  * condition of K(sigma,tau)).  Kernel entries and their gradients are
- * recomputed in FP64 (nothing is stored); K(sigma,tau) is factored in FP64 with
- * partial pivoting.  Supported for every kernel of h3d_kernel.
+ * recomputed (nothing is stored): the admissible blocks in FP64 for every
+ * handle (their weights carry the condition of K(sigma,tau)), the near field in
+ * the handle's precision; K(sigma,tau) is factored in FP64 with partial
+ * pivoting.  Supported for every kernel of h3d_kernel.
  *   q  device, N charges in the caller's order (element type of the handle).
  *   E  device, one double: the energy.
  *   F  device, N x 3 doubles, row-major, the caller's order; overwritten.

@@ -9,9 +9,14 @@
 //   1/2 [ q_X^T dK(X,tau) c + a^T dK(sigma,Y) q_Y - a^T dM c ],
 // and each kernel entry K(p_i, p_j) = f(|p_i - p_j|) differentiates to
 // g = f'(rho) (p_i - p_j) / rho for p_i and -g for p_j.  Kernel entries are
-// recomputed (nothing is stored), in FP64; M is factored by Gaussian elimination
-// with partial pivoting in FP64.  Far-field contributions reach the points
-// through FP64 atomic additions; the energy is reduced in a fixed order.
+// recomputed (nothing is stored).  The admissible blocks are evaluated in FP64
+// for every handle: c and a carry the condition of M (up to ~1e7), and the
+// terms at the pivot points cancel to the interpolation error, so an FP32 entry
+// error of 1e-7 would be amplified past the result.  M is factored by Gaussian
+// elimination with partial pivoting.  The near field of FP32 handles evaluates
+// in FP32 (coordinate differences from a hi + lo split, compensated sums).
+// Far-field contributions reach the points through FP64 atomic additions; the
+// energy is reduced in a fixed order.
 #include "h3d_internal.cuh"
 
 namespace h3d {
@@ -20,7 +25,15 @@ namespace {
 constexpr int kFThreads = 128;
 constexpr int kFWarps = kFThreads / 32;
 
-// K(a, b) and dK/da for a - b = (dx, dy, dz)
+// 1/sqrt(d2) to FP64 accuracy: an FP32 seed and two Newton steps (avoids the
+// FP64 square root and division)
+__device__ __forceinline__ double rsqrt64(double d2) {
+    double y = (double)rsqrtf((float)d2);
+    y = y * (1.5 - 0.5 * d2 * y * y);
+    return y * (1.5 - 0.5 * d2 * y * y);
+}
+
+// K(a, b) and dK/da = (f'(rho) / rho) (a - b) for a - b = (dx, dy, dz)
 __device__ __forceinline__ double kval_grad(int kind, double kappa, double dx, double dy, double dz, double &gx,
                                             double &gy, double &gz) {
     const double d2 = dx * dx + dy * dy + dz * dz;
@@ -28,40 +41,73 @@ __device__ __forceinline__ double kval_grad(int kind, double kappa, double dx, d
         gx = gy = gz = 0.0;
         return 0.0;
     }
-    const double r = sqrt(d2), ir = 1.0 / r;
-    double f, fp;
+    const double ir = rsqrt64(d2), r = d2 * ir;
+    double f, fr;   // f and f'(rho) / rho
     switch (kind) {
-    case H3D_LAPLACE: f = H3D_INV4PI * ir; fp = -f * ir; break;
-    case H3D_YUKAWA: {
-        const double e = exp(-kappa * r);
-        f = H3D_INV4PI * e * ir;
-        fp = -f * (1.0 + kappa * r) * ir;
-        break;
-    }
-    case H3D_INV_R4: f = 1.0 / (d2 * d2); fp = -4.0 * f * ir; break;
+    case H3D_LAPLACE: f = H3D_INV4PI * ir; fr = -f * ir * ir; break;
+    case H3D_YUKAWA: f = H3D_INV4PI * exp(-kappa * r) * ir; fr = -f * (1.0 + kappa * r) * ir * ir; break;
+    case H3D_INV_R4: f = (ir * ir) * (ir * ir); fr = -4.0 * f * ir * ir; break;
     default: {
         double sn, cs;
         sincos(r, &sn, &cs);
         f = cs * ir;
-        fp = -(r * sn + cs) * ir * ir;
+        fr = -(r * sn + cs) * ir * ir * ir;
     }
     }
-    const double s = fp * ir;
-    gx = s * dx;
-    gy = s * dy;
-    gz = s * dz;
+    gx = fr * dx;
+    gy = fr * dy;
+    gz = fr * dz;
     return f;
 }
 
-__device__ __forceinline__ double kval(int kind, double kappa, double dx, double dy, double dz) {
-    double gx, gy, gz;
-    return kval_grad(kind, kappa, dx, dy, dz, gx, gy, gz);
+__device__ __forceinline__ float kval_grad(int kind, float kappa, float dx, float dy, float dz, float &gx, float &gy,
+                                           float &gz) {
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 == 0.0f) {
+        gx = gy = gz = 0.0f;
+        return 0.0f;
+    }
+    const float ir = rsqrtf(d2), r = d2 * ir;
+    float f, fr;
+    switch (kind) {
+    case H3D_LAPLACE: f = (float)H3D_INV4PI * ir; fr = -f * ir * ir; break;
+    case H3D_YUKAWA: f = (float)H3D_INV4PI * expf(-kappa * r) * ir; fr = -f * (1.0f + kappa * r) * ir * ir; break;
+    case H3D_INV_R4: f = (ir * ir) * (ir * ir); fr = -4.0f * f * ir * ir; break;
+    default: {
+        float sn, cs;
+        sincosf(r, &sn, &cs);
+        f = cs * ir;
+        fr = -(r * sn + cs) * ir * ir * ir;
+    }
+    }
+    gx = fr * dx;
+    gy = fr * dy;
+    gz = fr * dz;
+    return f;
 }
+
+// sums of evaluations: plain in FP64, compensated (Kahan) in FP32
+template <class T> struct KSum;
+template <> struct KSum<double> {
+    double s = 0.0;
+    __device__ void add(double v) { s += v; }
+    __device__ double get() const { return s; }
+};
+template <> struct KSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ void add(float v) {
+        const float y = v - c, t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ double get() const { return (double)s - (double)c; }
+};
 
 struct ForceArgs {
     int kind;
     double kappa;
     const double *px, *py, *pz;
+    const float4 *ph, *pl;     // FP32 evaluation: coordinates split hi + lo, charge in ph.w
     const double *qs;          // charges, Morton order
     double *G;                 // dE/dp, Morton order, N x 3
     // near
@@ -77,11 +123,50 @@ struct ForceArgs {
     double *Epart;             // per leaf (near), then per block (far)
 };
 
+// p_i - p_j in the evaluation type: FP64 directly; FP32 from the hi + lo split
+// (each FP32 subtraction is correctly rounded, so the difference keeps ~1e-7 of
+// its own size, not of the coordinates)
+__device__ __forceinline__ void pdiff(const ForceArgs &A, int i, int j, double &dx, double &dy, double &dz) {
+    dx = A.px[i] - A.px[j];
+    dy = A.py[i] - A.py[j];
+    dz = A.pz[i] - A.pz[j];
+}
+__device__ __forceinline__ void pdiff(const ForceArgs &A, int i, int j, float &dx, float &dy, float &dz) {
+    const float4 hi = A.ph[i], hj = A.ph[j], li = A.pl[i], lj = A.pl[j];
+    dx = (hi.x - hj.x) + (li.x - lj.x);
+    dy = (hi.y - hj.y) + (li.y - lj.y);
+    dz = (hi.z - hj.z) + (li.z - lj.z);
+}
+template <class T> __device__ __forceinline__ T charge(const ForceArgs &A, int i);
+template <> __device__ __forceinline__ double charge<double>(const ForceArgs &A, int i) { return A.qs[i]; }
+template <> __device__ __forceinline__ float charge<float>(const ForceArgs &A, int i) { return A.ph[i].w; }
+
 template <class T>
-__global__ void k_charges_sorted(const T *__restrict__ q, const int *__restrict__ perm, int64_t n,
-                                 double *__restrict__ qs) {
+__device__ __forceinline__ T kv(const ForceArgs &A, int i, int j) {
+    T dx, dy, dz, gx, gy, gz;
+    pdiff(A, i, j, dx, dy, dz);
+    return kval_grad(A.kind, (T)A.kappa, dx, dy, dz, gx, gy, gz);
+}
+template <class T>
+__device__ __forceinline__ void kg(const ForceArgs &A, int i, int j, T &gx, T &gy, T &gz) {
+    T dx, dy, dz;
+    pdiff(A, i, j, dx, dy, dz);
+    kval_grad(A.kind, (T)A.kappa, dx, dy, dz, gx, gy, gz);
+}
+
+template <class T>
+__global__ void k_charges_sorted(const T *__restrict__ q, const int *__restrict__ perm, const double *__restrict__ px,
+                                 const double *__restrict__ py, const double *__restrict__ pz, int64_t n,
+                                 double *__restrict__ qs, float4 *__restrict__ ph, float4 *__restrict__ pl) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n) qs[s] = (double)q[perm[s]];
+    if (s >= n) return;
+    const double q64 = (double)q[perm[s]];
+    qs[s] = q64;
+    if (ph) {
+        const float xh = (float)px[s], yh = (float)py[s], zh = (float)pz[s];
+        ph[s] = make_float4(xh, yh, zh, (float)q64);
+        pl[s] = make_float4((float)(px[s] - xh), (float)(py[s] - yh), (float)(pz[s] - zh), 0.f);
+    }
 }
 
 __device__ double block_sum(double v, double *red) {
@@ -94,7 +179,13 @@ __device__ double block_sum(double v, double *red) {
     return t;
 }
 
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // near field: every point of a leaf against every point of its near leaves
+template <class T>
 __global__ void __launch_bounds__(kFThreads) k_force_near(ForceArgs A) {
     __shared__ double red[kFWarps];
     const int z = blockIdx.x;
@@ -102,25 +193,26 @@ __global__ void __launch_bounds__(kFThreads) k_force_near(ForceArgs A) {
     const int x0 = A.box_start[Zg], x1 = A.box_end[Zg];
     double e = 0.0;
     for (int i = x0 + threadIdx.x; i < x1; i += kFThreads) {
-        const double xi = A.px[i], yi = A.py[i], zi = A.pz[i], qi = A.qs[i];
-        double ei = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+        KSum<T> ei, gx, gy, gz;
         for (int p = A.near_ptr[z]; p < A.near_ptr[z + 1]; ++p) {
             const int Sg = (int)(A.offL + A.near_src[p]);
             for (int j = A.box_start[Sg]; j < A.box_end[Sg]; ++j) {
                 if (j == i) continue;
-                double hx, hy, hz;
-                const double k = kval_grad(A.kind, A.kappa, xi - A.px[j], yi - A.py[j], zi - A.pz[j], hx, hy, hz);
-                const double w = qi * A.qs[j];
-                ei += A.qs[j] * k;
-                gx += w * hx;
-                gy += w * hy;
-                gz += w * hz;
+                T dx, dy, dz, hx, hy, hz;
+                pdiff(A, i, j, dx, dy, dz);
+                const T k = kval_grad(A.kind, (T)A.kappa, dx, dy, dz, hx, hy, hz);
+                const T qj = charge<T>(A, j);
+                ei.add(qj * k);
+                gx.add(qj * hx);
+                gy.add(qj * hy);
+                gz.add(qj * hz);
             }
         }
-        e += 0.5 * qi * ei;
-        A.G[3 * (int64_t)i] = gx;
-        A.G[3 * (int64_t)i + 1] = gy;
-        A.G[3 * (int64_t)i + 2] = gz;
+        const double qi = A.qs[i];
+        e += 0.5 * qi * ei.get();
+        A.G[3 * (int64_t)i] = qi * gx.get();
+        A.G[3 * (int64_t)i + 1] = qi * gy.get();
+        A.G[3 * (int64_t)i + 2] = qi * gz.get();
     }
     const double t = block_sum(e, red);
     if (threadIdx.x == 0) A.Epart[z] = t;
@@ -132,10 +224,13 @@ __device__ __forceinline__ void gadd(double *G, int p, double s, double gx, doub
     atomicAdd(G + 3 * (int64_t)p + 2, s * gz);
 }
 
-// far field: one block at a time per CTA (grid-stride), M in this CTA's scratch
+// far field: one block at a time per CTA (grid-stride), M in this CTA's scratch,
+// everything in FP64
 __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
+    using T = double;
     __shared__ int sp[kMaxRank], tp[kMaxRank], piv[kMaxRank];
     __shared__ double c[kMaxRank], a[kMaxRank], u0[kMaxRank];
+    __shared__ double gs[kMaxRank][3], gt[kMaxRank][3];   // sum_j q_j dK(sigma_k, p_j), sum_i q_i dK(p_i, tau_k)
     __shared__ double red[kFWarps];
     __shared__ int pmax;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -155,32 +250,51 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
             tp[k] = y0 + ta[k];
         }
         __syncthreads();
-        // s = K(sigma, Y) q_Y -> c,  u = K(X, tau)^T q_X -> a (one warp per pivot)
+        // one warp per pivot, each entry evaluated once for its value and gradient:
+        //   s = K(sigma, Y) q_Y -> c,  u = K(X, tau)^T q_X -> a, u0,
+        //   gs_k = sum_j q_j dK(sigma_k, p_j),  gt_k = sum_i q_i dK(p_i, tau_k)
         for (int k = warp; k < r; k += kFWarps) {
             const int ps = sp[k], pt = tp[k];
-            double sv = 0.0, uv = 0.0;
-            for (int j = y0 + lane; j < y0 + n; j += 32)
-                sv += kval(A.kind, A.kappa, A.px[ps] - A.px[j], A.py[ps] - A.py[j], A.pz[ps] - A.pz[j]) * A.qs[j];
-            for (int i = x0 + lane; i < x0 + m; i += 32)
-                uv += A.qs[i] * kval(A.kind, A.kappa, A.px[i] - A.px[pt], A.py[i] - A.py[pt], A.pz[i] - A.pz[pt]);
-            for (int o = 16; o > 0; o >>= 1) {
-                sv += __shfl_xor_sync(0xffffffffu, sv, o);
-                uv += __shfl_xor_sync(0xffffffffu, uv, o);
+            double sv = 0.0, uv = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0;
+            for (int j = y0 + lane; j < y0 + n; j += 32) {
+                double dx, dy, dz, hx, hy, hz;
+                pdiff(A, ps, j, dx, dy, dz);
+                const double f = kval_grad(A.kind, A.kappa, dx, dy, dz, hx, hy, hz), qj = A.qs[j];
+                sv += f * qj;
+                s0 += qj * hx;
+                s1 += qj * hy;
+                s2 += qj * hz;
             }
+            for (int i = x0 + lane; i < x0 + m; i += 32) {
+                double dx, dy, dz, hx, hy, hz;
+                pdiff(A, i, pt, dx, dy, dz);
+                const double f = kval_grad(A.kind, A.kappa, dx, dy, dz, hx, hy, hz), qi = A.qs[i];
+                uv += qi * f;
+                t0 += qi * hx;
+                t1 += qi * hy;
+                t2 += qi * hz;
+            }
+            sv = warp_sum(sv); uv = warp_sum(uv);
+            s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2);
+            t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2);
             if (lane == 0) {
                 c[k] = sv;
                 a[k] = uv;
                 u0[k] = uv;
+                gs[k][0] = s0; gs[k][1] = s1; gs[k][2] = s2;
+                gt[k][0] = t0; gt[k][1] = t1; gt[k][2] = t2;
             }
         }
-        // M = K(sigma, tau), row-major r x r
+        // M = K(sigma, tau), row-major r x r, FP64
         for (int e = tid; e < r * r; e += kFThreads) {
             const int k = e / r, l = e - k * r;
-            const int ps = sp[k], pt = tp[l];
-            M[e] = kval(A.kind, A.kappa, A.px[ps] - A.px[pt], A.py[ps] - A.py[pt], A.pz[ps] - A.pz[pt]);
+            double dx, dy, dz, gx, gy, gz;
+            pdiff(A, sp[k], tp[l], dx, dy, dz);
+            M[e] = kval_grad(A.kind, A.kappa, dx, dy, dz, gx, gy, gz);
         }
         for (int k = tid; k < r; k += kFThreads) piv[k] = k;
         __syncthreads();
+        // energy of the block: 1/2 u^T c with c = M^{-1} s (after the solves)
         // P M = L U (partial pivoting), the row swaps applied to c as well
         for (int k = 0; k < r; ++k) {
             if (warp == 0) {
@@ -231,6 +345,12 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
             if (tid == 0) c[k] = (c[k] - t) / M[(size_t)k * r + k];
             __syncthreads();
         }
+        {   // energy 1/2 u^T c, u still intact in u0
+            double e = 0.0;
+            for (int k = tid; k < r; k += kFThreads) e += 0.5 * u0[k] * c[k];
+            e = block_sum(e, red);
+            if (tid == 0) A.Epart[A.nleaf + b] = e;
+        }
         for (int k = 0; k < r; ++k) {   // U^T z = u (z in a)
             double t = 0.0;
             for (int l = tid; l < k; l += kFThreads) t += M[(size_t)l * r + k] * a[l];
@@ -250,107 +370,57 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
         __syncthreads();
         for (int k = tid; k < r; k += kFThreads) a[piv[k]] = u0[k];
         __syncthreads();
-        // energy 1/2 u^T c (u recomputed: u0 was reused)
-        {
-            double e = 0.0;
-            for (int k = warp; k < r; k += kFWarps) {
-                const int pt = tp[k];
-                double uv = 0.0;
-                for (int i = x0 + lane; i < x0 + m; i += 32)
-                    uv += A.qs[i] * kval(A.kind, A.kappa, A.px[i] - A.px[pt], A.py[i] - A.py[pt], A.pz[i] - A.pz[pt]);
-                for (int o = 16; o > 0; o >>= 1) uv += __shfl_xor_sync(0xffffffffu, uv, o);
-                if (lane == 0) e += 0.5 * uv * c[k];
-            }
-            e = block_sum(e, red);
-            if (tid == 0) A.Epart[A.nleaf + b] = e;
-        }
         // first term: q_X^T dK(X,tau) c
         for (int i = x0 + tid; i < x0 + m; i += kFThreads) {
-            double gx = 0.0, gy = 0.0, gz = 0.0;
+            KSum<T> gx, gy, gz;
             for (int k = 0; k < r; ++k) {
-                const int pt = tp[k];
-                double hx, hy, hz;
-                kval_grad(A.kind, A.kappa, A.px[i] - A.px[pt], A.py[i] - A.py[pt], A.pz[i] - A.pz[pt], hx, hy, hz);
-                gx += c[k] * hx;
-                gy += c[k] * hy;
-                gz += c[k] * hz;
+                T hx, hy, hz;
+                kg<T>(A, i, tp[k], hx, hy, hz);
+                const T ck = (T)c[k];
+                gx.add(ck * hx);
+                gy.add(ck * hy);
+                gz.add(ck * hz);
             }
-            gadd(A.G, i, 0.5 * A.qs[i], gx, gy, gz);
+            gadd(A.G, i, 0.5 * A.qs[i], gx.get(), gy.get(), gz.get());
         }
-        for (int k = warp; k < r; k += kFWarps) {
-            const int pt = tp[k];
-            double gx = 0.0, gy = 0.0, gz = 0.0;
-            for (int i = x0 + lane; i < x0 + m; i += 32) {
-                double hx, hy, hz;
-                kval_grad(A.kind, A.kappa, A.px[i] - A.px[pt], A.py[i] - A.py[pt], A.pz[i] - A.pz[pt], hx, hy, hz);
-                gx += A.qs[i] * hx;
-                gy += A.qs[i] * hy;
-                gz += A.qs[i] * hz;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                gx += __shfl_xor_sync(0xffffffffu, gx, o);
-                gy += __shfl_xor_sync(0xffffffffu, gy, o);
-                gz += __shfl_xor_sync(0xffffffffu, gz, o);
-            }
-            if (lane == 0) gadd(A.G, pt, -0.5 * c[k], gx, gy, gz);
-        }
+        for (int k = tid; k < r; k += kFThreads) gadd(A.G, tp[k], -0.5 * c[k], gt[k][0], gt[k][1], gt[k][2]);
         // second term: a^T dK(sigma,Y) q_Y
-        for (int k = warp; k < r; k += kFWarps) {
-            const int ps = sp[k];
-            double gx = 0.0, gy = 0.0, gz = 0.0;
-            for (int j = y0 + lane; j < y0 + n; j += 32) {
-                double hx, hy, hz;
-                kval_grad(A.kind, A.kappa, A.px[ps] - A.px[j], A.py[ps] - A.py[j], A.pz[ps] - A.pz[j], hx, hy, hz);
-                gx += A.qs[j] * hx;
-                gy += A.qs[j] * hy;
-                gz += A.qs[j] * hz;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                gx += __shfl_xor_sync(0xffffffffu, gx, o);
-                gy += __shfl_xor_sync(0xffffffffu, gy, o);
-                gz += __shfl_xor_sync(0xffffffffu, gz, o);
-            }
-            if (lane == 0) gadd(A.G, ps, 0.5 * a[k], gx, gy, gz);
-        }
+        for (int k = tid; k < r; k += kFThreads) gadd(A.G, sp[k], 0.5 * a[k], gs[k][0], gs[k][1], gs[k][2]);
         for (int j = y0 + tid; j < y0 + n; j += kFThreads) {
-            double gx = 0.0, gy = 0.0, gz = 0.0;
+            KSum<T> gx, gy, gz;
             for (int k = 0; k < r; ++k) {
-                const int ps = sp[k];
-                double hx, hy, hz;
-                kval_grad(A.kind, A.kappa, A.px[ps] - A.px[j], A.py[ps] - A.py[j], A.pz[ps] - A.pz[j], hx, hy, hz);
-                gx += a[k] * hx;
-                gy += a[k] * hy;
-                gz += a[k] * hz;
+                T hx, hy, hz;
+                kg<T>(A, sp[k], j, hx, hy, hz);
+                const T ak = (T)a[k];
+                gx.add(ak * hx);
+                gy.add(ak * hy);
+                gz.add(ak * hz);
             }
-            gadd(A.G, j, -0.5 * A.qs[j], gx, gy, gz);
+            gadd(A.G, j, -0.5 * A.qs[j], gx.get(), gy.get(), gz.get());
         }
-        // third term: - a^T dM c
+        // third term: - a^T dM c (FP64: these entries are those of M)
         for (int k = tid; k < r; k += kFThreads) {
-            const int ps = sp[k];
             double gx = 0.0, gy = 0.0, gz = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
             for (int l = 0; l < r; ++l) {
-                const int pt = tp[l];
-                double hx, hy, hz;
-                kval_grad(A.kind, A.kappa, A.px[ps] - A.px[pt], A.py[ps] - A.py[pt], A.pz[ps] - A.pz[pt], hx, hy, hz);
+                double dx, dy, dz, hx, hy, hz;
+                pdiff(A, sp[k], tp[l], dx, dy, dz);
+                kval_grad(A.kind, A.kappa, dx, dy, dz, hx, hy, hz);
                 gx += c[l] * hx;
                 gy += c[l] * hy;
                 gz += c[l] * hz;
-                // entry (l, k) of the same sums for the column-pivot side
-                const int ps2 = sp[l], pt2 = tp[k];
-                kval_grad(A.kind, A.kappa, A.px[ps2] - A.px[pt2], A.py[ps2] - A.py[pt2], A.pz[ps2] - A.pz[pt2], hx, hy,
-                          hz);
+                pdiff(A, sp[l], tp[k], dx, dy, dz);
+                kval_grad(A.kind, A.kappa, dx, dy, dz, hx, hy, hz);
                 fx += a[l] * hx;
                 fy += a[l] * hy;
                 fz += a[l] * hz;
             }
-            gadd(A.G, ps, -0.5 * a[k], gx, gy, gz);
+            gadd(A.G, sp[k], -0.5 * a[k], gx, gy, gz);
             gadd(A.G, tp[k], 0.5 * c[k], fx, fy, fz);
         }
         __syncthreads();
     }
 }
 
-template <class T>
 __global__ void k_forces_out(const double *__restrict__ G, const int *__restrict__ perm, int64_t n,
                              double *__restrict__ F) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -362,7 +432,7 @@ __global__ void k_forces_out(const double *__restrict__ G, const int *__restrict
 }
 
 __global__ void k_sum_parts(const double *__restrict__ part, int64_t np, double *__restrict__ out, int nout) {
-    // out[b] = sum of part[b*per ... ]: fixed blocked order
+    // out[b] = sum of one contiguous share of part (fixed order)
     __shared__ double red[256];
     const int64_t per = (np + nout - 1) / nout;
     const int64_t lo = (int64_t)blockIdx.x * per, hi = min(np, lo + per);
@@ -388,22 +458,30 @@ void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s) {
     H3D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h.nblk, (int64_t)kFarCtas * sms));
     const int64_t nparts = h.nleaf + h.nblk;
+    const bool fp32 = h.prec != H3D_FP64;
     if (!h.fG) {   // scratch kept by the handle
         H3D_CUDA(cudaStreamSynchronize(s));
         h.fqs = h.mem.get<double>((size_t)std::max<int64_t>(h.N, 1));
         h.fG = h.mem.get<double>((size_t)std::max<int64_t>(h.N, 1) * 3);
         h.fE = h.mem.get<double>((size_t)std::max<int64_t>(nparts, 1) + 1024);
         h.fM = h.mem.get<double>((size_t)grid * std::max(1, h.max_rank) * std::max(1, h.max_rank));
+        if (fp32) {
+            h.fph = h.mem.get<float4>((size_t)std::max<int64_t>(h.N, 1));
+            h.fpl = h.mem.get<float4>((size_t)std::max<int64_t>(h.N, 1));
+        }
     }
     const int64_t N = h.N;
-    if (h.prec == H3D_FP64)
-        k_charges_sorted<double><<<gn(N, 256), 256, 0, s>>>((const double *)q, h.perm, N, h.fqs);
+    if (fp32)
+        k_charges_sorted<float><<<gn(N, 256), 256, 0, s>>>((const float *)q, h.perm, h.px, h.py, h.pz, N, h.fqs,
+                                                            h.fph, h.fpl);
     else
-        k_charges_sorted<float><<<gn(N, 256), 256, 0, s>>>((const float *)q, h.perm, N, h.fqs);
+        k_charges_sorted<double><<<gn(N, 256), 256, 0, s>>>((const double *)q, h.perm, h.px, h.py, h.pz, N, h.fqs,
+                                                             nullptr, nullptr);
     ForceArgs A{};
     A.kind = h.kernel;
     A.kappa = h.kappa;
     A.px = h.px; A.py = h.py; A.pz = h.pz;
+    A.ph = h.fph; A.pl = h.fpl;
     A.qs = h.fqs;
     A.G = h.fG;
     A.offL = h.box_off[h.L];
@@ -416,9 +494,14 @@ void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s) {
     A.Mscr = h.fM;
     A.mr = std::max(1, h.max_rank);
     A.Epart = h.fE + 1024;
-    k_force_near<<<h.nleaf, kFThreads, 0, s>>>(A);   // writes G (every point lies in one leaf)
+    // the near kernel writes every point's gradient (each point lies in one leaf),
+    // the far kernel then adds to it
+    if (fp32)
+        k_force_near<float><<<h.nleaf, kFThreads, 0, s>>>(A);
+    else
+        k_force_near<double><<<h.nleaf, kFThreads, 0, s>>>(A);
     if (h.nblk > 0) k_force_far<<<grid, kFThreads, 0, s>>>(A);
-    k_forces_out<double><<<gn(N, 256), 256, 0, s>>>(h.fG, h.perm, N, F);
+    k_forces_out<<<gn(N, 256), 256, 0, s>>>(h.fG, h.perm, N, F);
     const int nout = (int)std::min<int64_t>(1024, std::max<int64_t>(1, nparts));
     k_sum_parts<<<nout, 256, 0, s>>>(h.fE + 1024, nparts, h.fE, nout);
     k_sum_parts<<<1, 256, 0, s>>>(h.fE, nout, E, 1);

@@ -1,10 +1,12 @@
 """GPU forces (h3d_forces) against the oracle and the exact dense forces.
 
-* FP64 and FP32 handles, pivots frozen (the oracle takes the GPU's): the energy
-  equals the oracle's to 1e-10 and the forces its cross-form gradient to 1e-8.
-  Both are FP64 throughout; they differ in summation order and in the
-  elimination of K(sigma, tau), whose condition (up to ~1e7 at tol 1e-6) scales
-  the rounding of the solves: u * cond ~ 1e-9.
+* FP64 handles, pivots frozen (the oracle takes the GPU's): the energy equals
+  the oracle's to 1e-10 and the forces its cross-form gradient to 1e-8.  Both
+  are FP64 throughout; they differ in summation order and in the elimination of
+  K(sigma, tau), whose condition (up to ~1e7 at tol 1e-6) scales the rounding of
+  the solves: u * cond ~ 1e-9.
+* FP32 handles evaluate only the near field in FP32 (entries to ~2e-7; the
+  admissible blocks stay FP64): energy and forces within 1e-6 of the oracle's.
 * Other kernels (Yukawa, 1/r^4, cos r / r): the same parity.
 * The forces sum to zero (translation invariance with frozen pivots).
 * Against the exact forces of the dense energy on sampled points (O1's
@@ -30,7 +32,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("prec,kern", [("fp64", "laplace"), ("fp32", "laplace"), ("fp64", "yukawa"),
-                                       ("fp64", "inv_r4"), ("fp64", "cos_r")])
+                                       ("fp32", "yukawa"), ("fp64", "inv_r4"), ("fp64", "cos_r")])
 def test_forces_match_oracle_frozen(prec, kern):
     import torch
     n = 6000
@@ -42,8 +44,11 @@ def test_forces_match_oracle_frozen(prec, kern):
     E, F = A.forces(qt)
     o = O.Oracle(pts, **kw).set_pivots(*A.export_pivots())
     Eo, Go = o.energy_forces(qt.double().cpu().numpy())
-    assert abs(E.item() - Eo) <= 1e-10 * abs(Eo)
-    assert rel(F.cpu().numpy(), -Go) <= 1e-8
+    tE, tF = (1e-10, 1e-8) if prec == "fp64" else (1e-6, 1e-6)
+    eF = rel(F.cpu().numpy(), -Go)
+    print(f"{prec} {kern}: energy {abs(E.item() - Eo) / abs(Eo):.3e} forces {eF:.3e}")
+    assert abs(E.item() - Eo) <= tE * abs(Eo)
+    assert eF <= tF
 
 
 def test_forces_sum_to_zero_and_match_exact():
@@ -54,7 +59,9 @@ def test_forces_sum_to_zero_and_match_exact():
     q = I.rhs_uniform(n, 1, 254)[:, 0].astype(np.float32)
     E, F = A.forces(torch.from_numpy(q).cuda())
     F = F.cpu().numpy()
-    assert np.abs(F.sum(axis=0)).max() <= 1e-10 * np.abs(F).sum()
+    # zero up to rounding: this FP32 handle evaluates the two sides of each near
+    # pair separately in FP32 (~1e-7 each)
+    assert np.abs(F.sum(axis=0)).max() <= 1e-8 * np.abs(F).sum()
     rows = np.random.default_rng(255).choice(n, 512, replace=False)
     Fx = O.direct_forces_rows(pts, q.astype(np.float64), rows)
     err = rel(F[rows], Fx)
