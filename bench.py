@@ -54,6 +54,10 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     p.add_argument("--rows", type=int, default=10_000, help="sampled rows for the error / CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the baseline leg")
+    p.add_argument("--batched", action="store_true",
+                   help="time 64 independent clouds (N log-uniform in [8192, --batch-nmax], half cube / half "
+                        "sphere, Laplace / Yukawa alternating, FP32) as one graph against separate products")
+    p.add_argument("--batch-nmax", type=int, default=131072)
     p.add_argument("--forces", action="store_true",
                    help="also time the energy and forces (charges ~ U(-1,1) FP32, pivots frozen) and check them "
                         "against the exact dense forces on 4,096 sampled points")
@@ -190,10 +194,56 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(a):
+    import torch
+    from paper_2307_16303_gb300.api import H3DMatrix, H3DBatch
+    from oracle import oracle as O
+    rng = np.random.default_rng(5)
+    sizes = np.round(np.exp(rng.uniform(np.log(8192), np.log(a.batch_nmax), 64))).astype(int)
+    mats, pts, kerns, xs = [], [], [], []
+    t0 = time.perf_counter()
+    for c, n in enumerate(sizes):
+        p = I.uniform(int(n), 500 + c) if c % 2 == 0 else I.sphere(int(n), 500 + c)
+        kern = "laplace" if (c // 2) % 2 == 0 else "yukawa"
+        mats.append(H3DMatrix(torch.from_numpy(p).cuda(), leaf_size=a.leaf, tol=a.tol, precision="fp32", kernel=kern))
+        pts.append(p)
+        kerns.append(kern)
+        xs.append(torch.from_numpy(I.rhs_normal(int(n), 1, 600 + c)[:, 0].astype(np.float32)).cuda())
+    build_s = time.perf_counter() - t0
+    ys = [torch.empty_like(x) for x in xs]
+    # separate products, one after another on one stream
+    seq = sum(time_steps(lambda m=m, x=x, y=y: m.matvec(x, out=y), a.steps, a.warmup, torch) for m, x, y in
+              zip(mats, xs, ys))
+    B = H3DBatch(mats)
+    branches = B.tune(xs, ys)
+    with Clocks(torch.cuda.current_device()) as clk:
+        ms = time_steps(lambda: B.matvec(xs, ys), a.steps, a.warmup, torch)
+    errs = []
+    for c in (0, 1, 2, 3):
+        rows = I.sample_rows(int(sizes[c]), 256, 8 + c)
+        ref = O.direct_rows(pts[c], xs[c].double().cpu().numpy(), rows, kernel=kerns[c])
+        got = ys[c].double().cpu().numpy()[rows]
+        errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+    out = {"metric": "HODLR3D batched matvec ms, 64 clouds (one graph launch)", "value": round(ms, 4), "unit": "ms",
+           "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"64 clouds, N log-uniform in [8192, {a.batch_nmax}] seed 5, even: uniform cube, "
+                                  f"odd: unit sphere; Laplace / Yukawa by pairs; leaf {a.leaf}, tol {a.tol}",
+                      "total_points": int(sizes.sum()), "n_min": int(sizes.min()), "n_max": int(sizes.max())},
+           "separate_products_ms": round(seq, 4), "speedup_vs_separate": round(seq / ms, 3),
+           "graph_branches": branches, "build_s": round(build_s, 1),
+           "rel_err_sampled_rows": errs, "clocks": clk.summary(),
+           "gpu_launches": 5 * 64 * a.steps}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.batched:
+        run_batched(a)
         return
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))

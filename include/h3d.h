@@ -152,6 +152,27 @@ h3d_status h3d_energy(h3d_handle h, const void *q, double *E, void *grad, void *
  * scratch of max_rank^2 doubles per CTA after synchronising `stream`.          */
 h3d_status h3d_forces(h3d_handle h, const void *q, double *E, double *F, void *stream);
 
+/* ---- Batches of independent operators (many point clouds) ------------------
+ * A batch runs the products of several handles (one right-hand side each) as
+ * one CUDA graph: the first call captures every handle's product (the same
+ * kernels as h3d_matvec) on `branches` concurrent streams, clouds assigned
+ * longest first to the least loaded stream; later calls with the same vectors
+ * replay it with a single graph launch on `stream` (new vectors re-capture).
+ * The handles must outlive the batch and must not be used elsewhere while a
+ * batch product is in flight.
+ *   handles  host array of `count` built handles.
+ *   x, y     host arrays of `count` device pointers: x[i], y[i] are N_i values
+ *            of handle i's element type (caller's order); y overwritten.
+ * h3d_batch_tune times the graph for 1, 2, 4, ... branches (up to 32 and the
+ * number of handles; three replays each, CUDA events on `stream`), keeps the
+ * fastest and reports it in *branches_out (may be NULL); it synchronises
+ * `stream`.  The default is min(count, 8) branches.                          */
+typedef struct h3d_batch_s *h3d_batch;
+h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out);
+h3d_status h3d_batch_matvec(h3d_batch b, const void *const *x, void *const *y, void *stream);
+h3d_status h3d_batch_tune(h3d_batch b, const void *const *x, void *const *y, void *stream, int *branches_out);
+h3d_status h3d_batch_free(h3d_batch b);
+
 /* h3d_matvec with HOST x and y: copies x to the device, runs the product and
  * copies y back, all on `stream`, then synchronises the stream.  Device staging
  * buffers are allocated on the first call (and grown if nrhs grows) and kept by

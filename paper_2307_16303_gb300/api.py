@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_
 # every entry point declared in include/h3d.h
 EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3d_matvec_host", "h3d_free",
            "h3d_status_string", "h3d_get_stats", "h3d_matvec_profile", "h3d_export_tree", "h3d_export_lists",
-           "h3d_export_pivots", "h3d_morton_order_noalloc", "h3d_energy", "h3d_forces")
+           "h3d_export_pivots", "h3d_morton_order_noalloc", "h3d_energy", "h3d_forces",
+           "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_free")
 
 
 class H3DError(RuntimeError):
@@ -79,6 +80,10 @@ def lib():
             "h3d_morton_order_noalloc": (i32, [P, i64, P, f64, P, P, P]),
             "h3d_energy": (i32, [P, P, P, P, P]),
             "h3d_forces": (i32, [P, P, P, P, P]),
+            "h3d_batch_create": (i32, [P, i32, C.POINTER(P)]),
+            "h3d_batch_matvec": (i32, [P, P, P, P]),
+            "h3d_batch_tune": (i32, [P, P, P, P, C.POINTER(i32)]),
+            "h3d_batch_free": (i32, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -275,3 +280,49 @@ class H3DMatrix:
         if st != 0:
             raise H3DError(st, "h3d_export_pivots")
         return rank[:s["n_blocks"]], sig[:s["sum_rank"]], tau[:s["sum_rank"]]
+
+
+class H3DBatch:
+    """Products of several H3DMatrix operators (independent point clouds) as one
+    CUDA graph (h3d_batch_*).  The matrices must outlive the batch."""
+
+    def __init__(self, mats):
+        self.mats = list(mats)
+        arr = (C.c_void_p * len(self.mats))(*[m._h for m in self.mats])
+        h = C.c_void_p()
+        st = lib().h3d_batch_create(arr, len(self.mats), C.byref(h))
+        if st != 0:
+            raise H3DError(st, "h3d_batch_create")
+        self._b = h
+
+    def _ptrs(self, xs, ys):
+        for m, x, y in zip(self.mats, xs, ys):
+            m._check_x(x)
+            m._check_x(y)
+            if x.dim() != 1 or y.dim() != 1 or not x.is_contiguous() or not y.is_contiguous():
+                raise ValueError("one contiguous column per cloud")
+        n = len(self.mats)
+        return (C.c_void_p * n)(*[x.data_ptr() for x in xs]), (C.c_void_p * n)(*[y.data_ptr() for y in ys])
+
+    def matvec(self, xs, ys, stream=None):
+        """ys[i] = A_i xs[i] for every cloud (device tensors, kept by the caller)."""
+        xp, yp = self._ptrs(xs, ys)
+        st = lib().h3d_batch_matvec(self._b, xp, yp, _stream_ptr(stream))
+        if st != 0:
+            raise H3DError(st, "h3d_batch_matvec")
+
+    def tune(self, xs, ys, stream=None) -> int:
+        xp, yp = self._ptrs(xs, ys)
+        nb = C.c_int()
+        st = lib().h3d_batch_tune(self._b, xp, yp, _stream_ptr(stream), C.byref(nb))
+        if st != 0:
+            raise H3DError(st, "h3d_batch_tune")
+        return nb.value
+
+    def free(self):
+        if getattr(self, "_b", None) is not None and _lib is not None:
+            _lib.h3d_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        self.free()

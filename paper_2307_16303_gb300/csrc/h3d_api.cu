@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "h3d_internal.cuh"
 
@@ -318,6 +319,181 @@ h3d_status h3d_export_pivots(h3d_handle hh, int *rank, int *sigma, int *tau) {
             H3D_CUDA(cudaMemcpy(tau, h.tau, (size_t)h.sum_rank * sizeof(int), cudaMemcpyDeviceToHost));
         }
     });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent operators (many point clouds): the products of every
+// handle, one right-hand side each, are captured once into a CUDA graph whose
+// branches (one stream each) run the clouds side by side; later calls with the
+// same vectors replay the graph with one launch.
+struct h3d_batch_s {
+    std::vector<h3d_handle> hs;
+    std::vector<int64_t> cost;                    // per handle: factor entries + near interactions
+    int branches = 0;                             // streams in the graph
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> st;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec = nullptr;
+    int exec_branches = 0;
+    std::vector<const void *> xs;
+    std::vector<void *> ys;
+    ~h3d_batch_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (cudaEvent_t e : join) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        for (cudaStream_t s : st) cudaStreamDestroy(s);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+// longest job first onto the least loaded branch
+std::vector<int> assign_branches(const std::vector<int64_t> &cost, int nb) {
+    std::vector<int> order(cost.size()), owner(cost.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b] || (cost[a] == cost[b] && a < b); });
+    std::vector<int64_t> load(nb, 0);
+    for (int i : order) {
+        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        owner[i] = b;
+        load[b] += cost[i];
+    }
+    return owner;
+}
+
+void batch_capture(h3d_batch_s &B, const void *const *x, void *const *y, int nb) {
+    if (B.exec) {
+        H3D_CUDA(cudaGraphExecDestroy(B.exec));
+        B.exec = nullptr;
+    }
+    while ((int)B.st.size() < nb) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        H3D_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        H3D_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        B.st.push_back(s);
+        B.join.push_back(e);
+    }
+    const std::vector<int> owner = assign_branches(B.cost, nb);
+    cudaGraph_t g = nullptr;
+    H3D_CUDA(cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeThreadLocal));
+    try {
+        H3D_CUDA(cudaEventRecord(B.fork, B.cap));
+        for (int b = 0; b < nb; ++b) H3D_CUDA(cudaStreamWaitEvent(B.st[b], B.fork, 0));
+        for (size_t i = 0; i < B.hs.size(); ++i) h3d::run_matvec(B.hs[i]->h, x[i], y[i], 1, false, B.st[owner[i]]);
+        for (int b = 0; b < nb; ++b) {
+            H3D_CUDA(cudaEventRecord(B.join[b], B.st[b]));
+            H3D_CUDA(cudaStreamWaitEvent(B.cap, B.join[b], 0));
+        }
+    } catch (...) {
+        cudaStreamEndCapture(B.cap, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    H3D_CUDA(cudaStreamEndCapture(B.cap, &g));
+    const cudaError_t e = cudaGraphInstantiate(&B.exec, g, 0);
+    cudaGraphDestroy(g);
+    H3D_CUDA(e);
+    B.exec_branches = nb;
+    B.xs.assign(x, x + B.hs.size());
+    B.ys.assign(y, y + B.hs.size());
+}
+
+h3d_status batch_check(h3d_batch B, const void *const *x, void *const *y) {
+    if (!B || !x || !y) return H3D_ERR_ARG;
+    for (size_t i = 0; i < B->hs.size(); ++i) {
+        const Handle &h = B->hs[i]->h;
+        if (!h.ok) return H3D_ERR_STATE;
+        if (h3d_status e = async_error(h)) return e;
+        if (!x[i] || !y[i] || x[i] == y[i]) return H3D_ERR_ARG;
+    }
+    return H3D_OK;
+}
+
+bool same_vectors(const h3d_batch_s &B, const void *const *x, void *const *y) {
+    for (size_t i = 0; i < B.hs.size(); ++i)
+        if (B.xs[i] != x[i] || B.ys[i] != y[i]) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out) {
+    if (!handles || count < 1 || !out) return H3D_ERR_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!handles[i] || !handles[i]->h.ok) return H3D_ERR_ARG;
+    h3d_batch_s *B = new (std::nothrow) h3d_batch_s;
+    if (!B) return H3D_ERR_OOM;
+    const h3d_status st = guard([&] {
+        B->hs.assign(handles, handles + count);
+        for (int i = 0; i < count; ++i) {   // work estimate: factor entries plus the near field
+            const Handle &h = handles[i]->h;
+            B->cost.push_back(h.factor_entries + h.N * 32);
+        }
+        B->branches = std::min(count, 8);
+        H3D_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+        H3D_CUDA(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+    });
+    if (st != H3D_OK) {
+        delete B;
+        return st;
+    }
+    *out = B;
+    return H3D_OK;
+}
+
+h3d_status h3d_batch_matvec(h3d_batch B, const void *const *x, void *const *y, void *stream) {
+    if (h3d_status e = batch_check(B, x, y)) return e;
+    return guard([&] {
+        if (!B->exec || B->exec_branches != B->branches || !same_vectors(*B, x, y))
+            batch_capture(*B, x, y, B->branches);
+        H3D_CUDA(cudaGraphLaunch(B->exec, as_stream(stream)));
+    });
+}
+
+h3d_status h3d_batch_tune(h3d_batch B, const void *const *x, void *const *y, void *stream, int *branches_out) {
+    if (h3d_status e = batch_check(B, x, y)) return e;
+    return guard([&] {
+        cudaStream_t s = as_stream(stream);
+        cudaEvent_t e0, e1;
+        H3D_CUDA(cudaEventCreate(&e0));
+        H3D_CUDA(cudaEventCreate(&e1));
+        float best = 0.f;
+        int best_nb = 1;
+        const int n = (int)B->hs.size();
+        for (int nb = 1; nb <= std::min(n, 32); nb *= 2) {
+            batch_capture(*B, x, y, nb);
+            H3D_CUDA(cudaGraphLaunch(B->exec, s));   // warm-up
+            H3D_CUDA(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) H3D_CUDA(cudaGraphLaunch(B->exec, s));
+            H3D_CUDA(cudaEventRecord(e1, s));
+            H3D_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            H3D_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (nb == 1 || ms < best) {
+                best = ms;
+                best_nb = nb;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        B->branches = best_nb;
+        batch_capture(*B, x, y, best_nb);
+        if (branches_out) *branches_out = best_nb;
+    });
+}
+
+h3d_status h3d_batch_free(h3d_batch B) {
+    if (!B) return H3D_OK;
+    cudaDeviceSynchronize();
+    delete B;
+    return H3D_OK;
 }
 
 }  // extern "C"
