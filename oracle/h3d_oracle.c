@@ -1017,3 +1017,55 @@ int h3do_direct_forces_rows(int kind, double kappa, const double *pts, int64_t N
     }
     return ST_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* The skeleton form of the product (the paper's own storage, Sec. 4.1: only
+ * the pivots and K(sigma,tau) are kept): y = near + sum over admissible blocks
+ * of K(X,tau) K(sigma,tau)^{-1} K(sigma,Y) x_Y, each block evaluated from
+ * kernel entries with a dense solve.  x, y: N values, the caller's order.     */
+int h3do_apply_skeleton(const h3do_t *h, const double *x, double *y)
+{
+    const int64_t N = h->N;
+    double *xs_, *ys_;
+    if (!h->have_pivots) return ST_ARG;
+    xs_ = (double *)malloc((size_t)N * sizeof(double));
+    ys_ = (double *)calloc((size_t)N, sizeof(double));
+    if (!xs_ || !ys_) { free(xs_); free(ys_); return ST_OOM; }
+    for (int64_t s = 0; s < N; ++s) xs_[s] = x[h->perm[s]];
+    {   /* near blocks */
+        const int64_t o = h->box_off[h->L];
+        for (int64_t p = 0; p < h->lists.n_near; ++p) {
+            int64_t t = o + h->lists.near_tgt[p], sb = o + h->lists.near_src[p];
+            for (int64_t i = h->box_start[t]; i < h->box_end[t]; ++i)
+                for (int64_t j = h->box_start[sb]; j < h->box_end[sb]; ++j)
+                    if (i != j) ys_[i] += kernel_f(h->kind, h->kappa, h->pts + 3 * i, h->pts + 3 * j) * xs_[j];
+        }
+    }
+    for (int64_t b = 0; b < h->lists.n_blocks; ++b) {
+        int64_t x0, y0;
+        int m, n, r = h->rank[b];
+        const int *sg = h->sigma + h->piv_off[b], *ta = h->tau + h->piv_off[b];
+        double *M, *c;
+        if (r == 0) continue;
+        block_ranges(h, b, &x0, &m, &y0, &n);
+        M = (double *)malloc((size_t)r * r * sizeof(double));
+        c = (double *)malloc((size_t)r * sizeof(double));
+        for (int k = 0; k < r; ++k) {
+            double sk = 0.0;
+            for (int j = 0; j < n; ++j) sk += kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + sg[k]), h->pts + 3 * (y0 + j)) * xs_[y0 + j];
+            c[k] = sk;
+            for (int l = 0; l < r; ++l)
+                M[(size_t)k * r + l] = kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + sg[k]), h->pts + 3 * (y0 + ta[l]));
+        }
+        if (dense_solve(r, M, c)) { free(M); free(c); free(xs_); free(ys_); return ST_RANK; }
+        for (int i = 0; i < m; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < r; ++k) acc += kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + i), h->pts + 3 * (y0 + ta[k])) * c[k];
+            ys_[x0 + i] += acc;
+        }
+        free(M); free(c);
+    }
+    for (int64_t s = 0; s < N; ++s) y[h->perm[s]] = ys_[s];
+    free(xs_); free(ys_);
+    return ST_OK;
+}
