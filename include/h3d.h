@@ -76,6 +76,21 @@ typedef enum {
     H3D_ADM_WEAK = 2       /* every off-diagonal pair (HODLR)                    */
 } h3d_admissibility;
 
+/* What a handle keeps of each admissible block (Sec. 4.1).
+ *   FACTORS   the ACA factors U, V (FP32 or FP64): products stream them.
+ *   SKELETON  the paper's own storage: the pivots sigma, tau and an LU factorisation
+ *             of K(sigma,tau) (FP64, partial pivoting).  Products recompute every
+ *             entry of K(sigma,Y) and K(X,tau) in FP64 (their weights carry the
+ *             condition of K(sigma,tau), so FP32 entries would not do) and solve
+ *             with the LU; memory is O(sum of r^2) instead of O(sum of r (m+n)).
+ *             Supports h3d_matvec (any nrhs, one column at a time), the batch
+ *             calls and h3d_forces; h3d_matvec_T, h3d_energy and
+ *             h3d_matvec_profile return H3D_ERR_ARG.                           */
+typedef enum {
+    H3D_STORE_FACTORS = 0,
+    H3D_STORE_SKELETON = 1
+} h3d_storage;
+
 typedef struct {
     int precision;          /* h3d_precision, default H3D_FP32                          */
     double kappa;           /* Yukawa decay, default 1.0                                 */
@@ -84,6 +99,7 @@ typedef struct {
     double side;            /* edge length of the domain cube, default 2.0               */
     int64_t workspace_bytes;/* device scratch budget for the build; 0 = automatic        */
     int admissibility;      /* h3d_admissibility, default H3D_ADM_HODLR3D                */
+    int storage;            /* h3d_storage, default H3D_STORE_FACTORS                    */
 } h3d_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libh3d.so")
 KERNELS = {"laplace": 0, "yukawa": 1, "inv_r4": 2, "cos_r": 3}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 ADMISSIBILITY = {"hodlr3d": 0, "strong": 1, "weak": 2}
+STORAGE = {"factors": 0, "skeleton": 1}
 STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_OOM", 4: "H3D_ERR_CUDA",
                 5: "H3D_ERR_ACA_RANK", 6: "H3D_ERR_TIMEOUT", 7: "H3D_ERR_STATE", 8: "H3D_ERR_DEPTH"}
 
@@ -37,7 +38,7 @@ class H3DError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("kappa", C.c_double), ("rank_cap", C.c_int),
                 ("lo", C.c_double * 3), ("side", C.c_double), ("workspace_bytes", C.c_int64),
-                ("admissibility", C.c_int)]
+                ("admissibility", C.c_int), ("storage", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -109,7 +110,8 @@ class H3DMatrix:
 
     def __init__(self, points, kernel: str = "laplace", leaf_size: int = 128, tol: float = 1e-7,
                  precision: str = "fp32", rank_cap: int = 512, kappa: float = 1.0, lo=(-1.0, -1.0, -1.0),
-                 side: float = 2.0, workspace_bytes: int = 0, admissibility: str = "hodlr3d", stream=None):
+                 side: float = 2.0, workspace_bytes: int = 0, admissibility: str = "hodlr3d",
+                 storage: str = "factors", stream=None):
         import torch
         if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float64
                 and points.dim() == 2 and points.shape[1] == 3):
@@ -125,6 +127,7 @@ class H3DMatrix:
         opt.side = side
         opt.workspace_bytes = workspace_bytes
         opt.admissibility = ADMISSIBILITY[admissibility]
+        opt.storage = STORAGE[storage]
         h = C.c_void_p()
         st = lib().h3d_build(pts.data_ptr(), pts.shape[0], KERNELS[kernel], leaf_size, tol, C.byref(opt),
                              _stream_ptr(stream), C.byref(h))

@@ -551,6 +551,10 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget) {
     tmp.free_one(scratch);
     tmp.free_one(flags);
 
+    if (h.storage == H3D_STORE_SKELETON) {   // pivots and K(sigma,tau) only: no U, V
+        build_skeleton(h, s, tmp);
+        return;
+    }
     const size_t es = h.elem();
     h.U = h.mem.alloc((size_t)std::max<int64_t>(h.u_elems, 4) * es);
     h.V = h.mem.alloc((size_t)std::max<int64_t>(h.v_elems, 4) * es);

@@ -52,6 +52,7 @@ void h3d_default_options(h3d_options *opt) {
     opt->side = 2.0;
     opt->workspace_bytes = 0;
     opt->admissibility = H3D_ADM_HODLR3D;
+    opt->storage = H3D_STORE_FACTORS;
 }
 
 const char *h3d_status_string(h3d_status s) {
@@ -84,6 +85,7 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
         if (!std::isfinite(o.lo[d])) return H3D_ERR_ARG;
     if (!(o.kappa >= 0.0) || !std::isfinite(o.kappa)) return H3D_ERR_ARG;
     if (o.admissibility < H3D_ADM_HODLR3D || o.admissibility > H3D_ADM_WEAK) return H3D_ERR_ARG;
+    if (o.storage != H3D_STORE_FACTORS && o.storage != H3D_STORE_SKELETON) return H3D_ERR_ARG;
     if (!is_device_ptr(points)) return H3D_ERR_ARG;
 
     h3d_handle_s *hs = new (std::nothrow) h3d_handle_s;
@@ -95,6 +97,7 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
     h.leaf_size = leaf_size;
     h.rank_cap = o.rank_cap;
     h.adm = o.admissibility;
+    h.storage = o.storage;
     h.tol = tol;
     h.kappa = o.kappa;
     h.side = o.side;
@@ -136,6 +139,7 @@ static h3d_status matvec_common(h3d_handle hh, const void *x, void *y, int nrhs,
     if (!h.ok) return H3D_ERR_STATE;
     if (h3d_status e = async_error(h)) return e;
     if (!x || !y || nrhs < 1 || x == y) return H3D_ERR_ARG;
+    if (transpose && h.storage == H3D_STORE_SKELETON) return H3D_ERR_ARG;
     return guard([&] { h3d::run_matvec(h, x, y, nrhs, transpose, as_stream(stream)); });
 }
 
@@ -153,6 +157,7 @@ h3d_status h3d_energy(h3d_handle hh, const void *q, double *E, void *grad, void 
     if (!h.ok) return H3D_ERR_STATE;
     if (h3d_status e = async_error(h)) return e;
     if (!q || !E || q == grad) return H3D_ERR_ARG;
+    if (h.storage == H3D_STORE_SKELETON) return H3D_ERR_ARG;   // needs the transpose product
     return guard([&] { h3d::energy(h, q, E, grad, as_stream(stream)); });
 }
 
@@ -195,6 +200,7 @@ h3d_status h3d_matvec_profile(h3d_handle hh, const void *x, void *y, int nrhs, v
     if (!hh || !phase_ms || nphase < 1) return H3D_ERR_ARG;
     Handle &h = hh->h;
     if (!h.ok) return H3D_ERR_STATE;
+    if (h.storage == H3D_STORE_SKELETON) return H3D_ERR_ARG;   // phases of the factor-streaming product only
     if (!x || !y || nrhs < 1 || x == y) return H3D_ERR_ARG;
     cudaStream_t s = as_stream(stream);
     std::vector<cudaEvent_t> ev((size_t)5 * nrhs, nullptr);
@@ -244,7 +250,9 @@ h3d_status h3d_get_stats(h3d_handle hh, h3d_stats *st) {
     st->factor_entries = h.factor_entries;
     st->u_entries = h.u_entries;
     st->v_entries = h.v_entries;
-    st->factor_bytes = (h.u_elems + h.v_elems) * (int64_t)h.elem();
+    st->factor_bytes = h.storage == H3D_STORE_SKELETON
+                           ? h.lu_off_total * (int64_t)sizeof(double) + h.sum_rank * (int64_t)sizeof(int)
+                           : (h.u_elems + h.v_elems) * (int64_t)h.elem();
     st->near_interactions = h.near_interactions;
     st->device_bytes = (int64_t)h.mem.total();
     st->build_ms = h.build_ms;

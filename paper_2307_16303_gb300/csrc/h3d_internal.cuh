@@ -117,6 +117,14 @@ struct Handle {
     // parameters
     int64_t N = 0;
     int kernel = H3D_LAPLACE, prec = H3D_FP32, leaf_size = 0, rank_cap = kMaxRank, adm = H3D_ADM_HODLR3D;
+    int storage = H3D_STORE_FACTORS;
+    // skeleton storage: per block the LU of K(sigma,tau) (row-major, L unit lower,
+    // at lu_off[b]) and its row order (at piv_off[b]); product scratch per block
+    double *lu = nullptr;
+    int64_t *lu_off = nullptr;                    // nblk + 1
+    int64_t lu_off_total = 0;                     // sum of r^2
+    int *lu_piv = nullptr;
+    double *skel_s = nullptr, *skel_c = nullptr;  // K(sigma,Y) x and K(sigma,tau)^{-1} of it
     double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
     int L = 0;
 
@@ -328,6 +336,8 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp);                  
 int matvec_passes(const Handle &h, int nrhs, bool transpose);  // kernel sequences one product launches
 void energy(Handle &h, const void *q, double *E, void *grad, cudaStream_t s);
 void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s);
+void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp);
+void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, cudaStream_t s);
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s,
                 cudaEvent_t *ev = nullptr);  // h3d_matvec.cu; ev: 5 events per rhs
 

@@ -1790,7 +1790,8 @@ void ensure_wide_scratch(Handle &h, cudaStream_t s) {
 }
 
 bool use_wide(const Handle &h, int nrhs, bool transpose) {
-    return nrhs > kNQ && !transpose && h.prec == H3D_FP32 && h.leaf_size <= kMaxLeafW;
+    return nrhs > kNQ && !transpose && h.prec == H3D_FP32 && h.leaf_size <= kMaxLeafW &&
+           h.storage == H3D_STORE_FACTORS;
 }
 
 template <class T>
@@ -1818,6 +1819,213 @@ void matvec_mr(Handle &h, const T *x, T *y, int q0, int nq, cudaStream_t s, cuda
     if (ev) H3D_CUDA(cudaEventRecord(ev[3], s));
     k_leaf_mr<T><<<h.nleaf, kLeafThreads, kLeafDynSmem, s>>>(A, (const T *)h.U, t, nearbuf, y, n, q0, nq);
     if (ev) H3D_CUDA(cudaEventRecord(ev[4], s));
+    H3D_LAUNCH_CHECK();
+}
+
+// ===========================================================================
+// Skeleton storage (the paper's own, Sec. 4.1): per admissible block only the
+// pivots and an LU factorisation of M = K(sigma,tau); a product recomputes
+// K(sigma,Y) x_Y, solves with M and applies K(X,tau).  Entries are FP64: the
+// solve's output carries the condition of M (up to ~1e7), which FP32 entries of
+// K(X,tau) would turn into O(1) errors.
+
+// 1/sqrt(d2) to FP64 accuracy from an FP32 seed and two Newton steps
+__device__ __forceinline__ double skel_rsqrt(double d2) {
+    double y = (double)rsqrtf((float)d2);
+    y = y * (1.5 - 0.5 * d2 * y * y);
+    return y * (1.5 - 0.5 * d2 * y * y);
+}
+
+__device__ __forceinline__ double skel_k(int kind, double kappa, const double *px, const double *py,
+                                         const double *pz, int i, int j) {
+    const double dx = px[i] - px[j], dy = py[i] - py[j], dz = pz[i] - pz[j];
+    const double d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 == 0.0) return 0.0;
+    const double ir = skel_rsqrt(d2);
+    switch (kind) {
+    case H3D_LAPLACE: return H3D_INV4PI * ir;
+    case H3D_YUKAWA: return H3D_INV4PI * exp(-kappa * d2 * ir) * ir;
+    case H3D_INV_R4: return (ir * ir) * (ir * ir);
+    default: return cos(d2 * ir) * ir;
+    }
+}
+
+struct SkelArgs {
+    int kind;
+    double kappa;
+    const double *px, *py, *pz;
+    int64_t nblk;
+    const int *blk_tgt, *blk_src, *box_start, *box_end, *rank, *sigma, *tau;
+    const int64_t *piv_off, *lu_off;
+    double *lu;
+    int *lu_piv;
+    double *sbuf, *cbuf;
+};
+
+constexpr int kSkThreads = 128;
+
+// M = K(sigma,tau) of every block, factored P M = L U in place (partial pivoting)
+__global__ void __launch_bounds__(kSkThreads) k_skel_factor(SkelArgs S) {
+    __shared__ int piv[kMaxRank];
+    __shared__ int pmax;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int64_t b = blockIdx.x; b < S.nblk; b += gridDim.x) {
+        const int r = S.rank[b];
+        if (r == 0) continue;
+        const int x0 = S.box_start[S.blk_tgt[b]], y0 = S.box_start[S.blk_src[b]];
+        const int *sg = S.sigma + S.piv_off[b], *ta = S.tau + S.piv_off[b];
+        double *M = S.lu + S.lu_off[b];
+        for (int e = tid; e < r * r; e += kSkThreads) {
+            const int k = e / r, l = e - k * r;
+            M[e] = skel_k(S.kind, S.kappa, S.px, S.py, S.pz, x0 + sg[k], y0 + ta[l]);
+        }
+        for (int k = tid; k < r; k += kSkThreads) piv[k] = k;
+        __syncthreads();
+        for (int k = 0; k < r; ++k) {
+            if (warp == 0) {
+                double best = -1.0;
+                int bi = k;
+                for (int i = k + lane; i < r; i += 32) {
+                    const double v = fabs(M[(size_t)i * r + k]);
+                    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+                }
+                if (lane == 0) pmax = bi;
+            }
+            __syncthreads();
+            const int p = pmax;
+            if (p != k) {
+                for (int j = tid; j < r; j += kSkThreads) {
+                    const double t = M[(size_t)k * r + j];
+                    M[(size_t)k * r + j] = M[(size_t)p * r + j];
+                    M[(size_t)p * r + j] = t;
+                }
+                if (tid == 0) {
+                    const int ti = piv[k];
+                    piv[k] = piv[p];
+                    piv[p] = ti;
+                }
+            }
+            __syncthreads();
+            const double d = M[(size_t)k * r + k];
+            for (int i = k + 1 + tid; i < r; i += kSkThreads) M[(size_t)i * r + k] /= d;
+            __syncthreads();
+            const int rem = r - k - 1;
+            for (int e = tid; e < rem * rem; e += kSkThreads) {
+                const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+                M[(size_t)i * r + j] -= M[(size_t)i * r + k] * M[(size_t)k * r + j];
+            }
+            __syncthreads();
+        }
+        for (int k = tid; k < r; k += kSkThreads) S.lu_piv[S.piv_off[b] + k] = piv[k];
+        __syncthreads();
+    }
+}
+
+// per block (one warp): s = K(sigma,Y) x_Y, then c = U^{-1} L^{-1} P s
+template <class T>
+__global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__restrict__ xs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * kSkThreads + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kSkThreads) >> 5;
+    for (int64_t b = w0; b < S.nblk; b += nw) {
+        const int r = S.rank[b];
+        if (r == 0) continue;
+        const int X = S.blk_tgt[b], Y = S.blk_src[b];
+        const int x0 = S.box_start[X], y0 = S.box_start[Y], y1 = S.box_end[Y];
+        const int64_t po = S.piv_off[b];
+        const int *sg = S.sigma + po;
+        double *sv = S.sbuf + po, *cv = S.cbuf + po;
+        const double *M = S.lu + S.lu_off[b];
+        const int *pv = S.lu_piv + po;
+        for (int k = 0; k < r; ++k) {
+            const int ps = x0 + sg[k];
+            double acc = 0.0;
+            for (int j = y0 + lane; j < y1; j += 32)
+                acc += skel_k(S.kind, S.kappa, S.px, S.py, S.pz, ps, j) * (double)xs[j];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) sv[k] = acc;
+        }
+        __syncwarp();
+        for (int k = 0; k < r; ++k) {   // L z = P s (unit lower)
+            double acc = 0.0;
+            for (int l = lane; l < k; l += 32) acc += M[(size_t)k * r + l] * cv[l];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) cv[k] = sv[pv[k]] - acc;
+            __syncwarp();
+        }
+        for (int k = r - 1; k >= 0; --k) {   // U c = z
+            double acc = 0.0;
+            for (int l = k + 1 + lane; l < r; l += 32) acc += M[(size_t)k * r + l] * cv[l];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) cv[k] = (cv[k] - acc) / M[(size_t)k * r + k];
+            __syncwarp();
+        }
+    }
+}
+
+// per leaf: y = near + sum over its ancestors' blocks of K(rows, tau) c
+template <class T>
+__global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A, const int64_t *__restrict__ tgt_ptr,
+                                                          const T *__restrict__ nearbuf, T *__restrict__ y) {
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], ze = A.box_end[Zg];
+    for (int i = zs + threadIdx.x; i < ze; i += kSkThreads) {
+        double acc = 0.0;
+        for (int l = 1; l <= A.L; ++l) {
+            const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
+            for (int64_t b = tgt_ptr[Ag]; b < tgt_ptr[Ag + 1]; ++b) {
+                const int r = S.rank[b];
+                const int y0 = S.box_start[S.blk_src[b]];
+                const int64_t po = S.piv_off[b];
+                for (int k = 0; k < r; ++k)
+                    acc += skel_k(S.kind, S.kappa, S.px, S.py, S.pz, i, y0 + S.tau[po + k]) * S.cbuf[po + k];
+            }
+        }
+        y[A.perm[i]] = (T)(acc + (double)nearbuf[i]);
+    }
+}
+
+SkelArgs skel_args(Handle &h) {
+    SkelArgs S{};
+    S.kind = h.kernel;
+    S.kappa = h.kappa;
+    S.px = h.px; S.py = h.py; S.pz = h.pz;
+    S.nblk = h.nblk;
+    S.blk_tgt = h.blk_tgt; S.blk_src = h.blk_src; S.box_start = h.box_start; S.box_end = h.box_end;
+    S.rank = h.rank; S.sigma = h.sigma; S.tau = h.tau;
+    S.piv_off = h.piv_off; S.lu_off = h.lu_off;
+    S.lu = h.lu; S.lu_piv = h.lu_piv;
+    S.sbuf = h.skel_s; S.cbuf = h.skel_c;
+    return S;
+}
+
+template <class T>
+void matvec_skel_one(Handle &h, const T *x, T *y, cudaStream_t s) {
+    const int64_t n = h.N;
+    T *xs = (T *)h.xs;
+    k_permute_in<T><<<gridn(n, 256), 256, 0, s>>>(x, h.perm, n, xs);
+    LeafArgs A = leaf_args(h);
+    T *nearbuf = (T *)h.nearbuf;
+    H3D_CUDA(cudaEventRecord(h.ev_fork, s));
+    H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
+    const int near_grid = sizeof(T) == 4 ? std::min(h.nleaf, kNearCtasPerSm * num_sms()) : h.nleaf;
+    k_near<T><<<near_grid, kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
+    H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
+    SkelArgs S = skel_args(h);
+    if (h.nblk > 0) {
+        const int64_t warps = h.nblk;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps * 32 + kSkThreads - 1) / kSkThreads,
+                                                                      16LL * num_sms()));
+        k_skel_src<T><<<grid, kSkThreads, 0, s>>>(S, xs);
+    }
+    H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
+    k_skel_leaf<T><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, y);
     H3D_LAUNCH_CHECK();
 }
 
@@ -1925,7 +2133,7 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
         std::vector<int64_t> vc0(nboxes);
         H3D_CUDA(cudaMemcpyAsync(vc0.data(), h.vcol0, nboxes * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         H3D_CUDA(cudaStreamSynchronize(s));
-        const bool wide = h.prec == H3D_FP32 && h.leaf_size <= kMaxLeafW;
+        const bool wide = h.prec == H3D_FP32 && h.leaf_size <= kMaxLeafW && h.storage == H3D_STORE_FACTORS;
         std::vector<int> tmap_of(nboxes, -1);
         std::vector<CUtensorMap> tmaps;
         if (wide) {
@@ -2063,8 +2271,46 @@ int matvec_passes(const Handle &h, int nrhs, bool transpose) {
     return nrhs;
 }
 
+void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
+    const int64_t nblk = h.nblk;
+    std::vector<int> rk(nblk);
+    if (nblk > 0) H3D_CUDA(cudaMemcpyAsync(rk.data(), h.rank, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> off(nblk + 1, 0);
+    for (int64_t b = 0; b < nblk; ++b) off[b + 1] = off[b] + (int64_t)rk[b] * rk[b];
+    h.lu_off_total = off[nblk];
+    h.lu_off = h.mem.get<int64_t>((size_t)nblk + 1);
+    H3D_CUDA(cudaMemcpyAsync(h.lu_off, off.data(), (nblk + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    h.lu = h.mem.get<double>((size_t)std::max<int64_t>(h.lu_off_total, 1));
+    h.lu_piv = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
+    h.skel_s = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1));
+    h.skel_c = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1));
+    if (nblk > 0) {
+        SkelArgs S = skel_args(h);
+        const int grid = (int)std::min<int64_t>(nblk, 4LL * num_sms());
+        k_skel_factor<<<grid, kSkThreads, 0, s>>>(S);
+        H3D_LAUNCH_CHECK();
+    }
+    H3D_CUDA(cudaStreamSynchronize(s));
+    (void)tmp;
+}
+
+void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, cudaStream_t s) {
+    const int64_t n = h.N;
+    for (int c = 0; c < nrhs; ++c) {
+        if (h.prec == H3D_FP64)
+            matvec_skel_one<double>(h, (const double *)x + (size_t)c * n, (double *)y + (size_t)c * n, s);
+        else
+            matvec_skel_one<float>(h, (const float *)x + (size_t)c * n, (float *)y + (size_t)c * n, s);
+    }
+}
+
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s, cudaEvent_t *ev) {
     const int64_t n = h.N;
+    if (h.storage == H3D_STORE_SKELETON) {   // transposes are refused by the entry points
+        matvec_skeleton(h, x, y, nrhs, s);
+        return;
+    }
     if (use_wide(h, nrhs, transpose)) {
         ensure_wide_scratch(h, s);
         for (int q0 = 0, b = 0; q0 < nrhs; q0 += kNQW, ++b)

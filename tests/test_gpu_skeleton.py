@@ -1,0 +1,62 @@
+"""Skeleton storage (pivots + LU of K(sigma,tau), entries recomputed in FP64).
+
+* FP64 handle: the product equals the oracle's skeleton-form product with the
+  GPU's pivots to 1e-10 (cond K(sigma,tau) times rounding), and the factor-
+  storage product of a handle built the same way to 1e-9.
+* FP32 handle: within 1e-6 of the direct sum at tol 1e-7; several right-hand
+  sides; forces work unchanged; the stored bytes are far below the factors'.
+* The transpose product and the energy are refused (H3D_ERR_ARG).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2307_16303_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def H(pts, **kw):
+    import torch
+    from paper_2307_16303_gb300.api import H3DMatrix
+    return H3DMatrix(torch.from_numpy(np.ascontiguousarray(pts)).cuda(), **kw)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_skeleton_fp64_matches_oracle_and_factor_storage():
+    import torch
+    pts = I.uniform(8000, 271)
+    kw = dict(leaf_size=32, tol=1e-6, precision="fp64")
+    S = H(pts, storage="skeleton", **kw)
+    F = H(pts, **kw)
+    x = I.rhs_normal(8000, 1, 272)[:, 0]
+    xt = torch.from_numpy(x).cuda()
+    ys = S.matvec(xt).cpu().numpy()
+    o = O.Oracle(pts, leaf_size=32, tol=1e-6).set_pivots(*S.export_pivots())
+    assert rel(ys, o.matvec_skeleton(x)) <= 1e-10
+    assert rel(ys, F.matvec(xt).cpu().numpy()) <= 1e-9
+    assert S.stats()["factor_bytes"] < 0.5 * F.stats()["factor_bytes"]
+
+
+def test_skeleton_fp32_vs_direct_multi_rhs_and_forces():
+    import torch
+    from paper_2307_16303_gb300.api import H3DError
+    n = 20000
+    pts = I.uniform(n, 273)
+    S = H(pts, leaf_size=64, tol=1e-7, precision="fp32", storage="skeleton")
+    X = I.rhs_normal(n, 3, 274).astype(np.float32)
+    Y = S.matvec(torch.from_numpy(X).cuda()).double().cpu().numpy()
+    ref = O.direct(pts, X.astype(np.float64))
+    assert rel(Y, ref) <= 1e-6
+    q = torch.from_numpy(I.rhs_uniform(n, 1, 275)[:, 0].astype(np.float32)).cuda()
+    E, Fo = S.forces(q)
+    rows = np.arange(0, n, 97)
+    Fx = O.direct_forces_rows(pts, q.double().cpu().numpy(), rows)
+    assert rel(Fo.cpu().numpy()[rows], Fx) <= 1e-5
+    with pytest.raises(H3DError):
+        S.matvec_T(q)
+    with pytest.raises(H3DError):
+        S.energy(q)
