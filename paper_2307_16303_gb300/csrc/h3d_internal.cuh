@@ -124,7 +124,8 @@ struct Handle {
     int64_t *lu_off = nullptr;                    // nblk + 1
     int64_t lu_off_total = 0;                     // sum of r^2
     int *lu_piv = nullptr;
-    double *skel_s = nullptr, *skel_c = nullptr;  // K(sigma,Y) x and K(sigma,tau)^{-1} of it
+    double *skel_s = nullptr, *skel_c = nullptr;  // K(sigma,Y) X and K(sigma,tau)^{-1} of it, 16 per pivot
+    void *skel_xs = nullptr, *skel_near = nullptr; // pass columns: permuted x point-major, near field
     double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
     int L = 0;
 

@@ -1860,6 +1860,7 @@ struct SkelArgs {
     double *lu;
     int *lu_piv;
     double *sbuf, *cbuf;
+    int mr;                   // largest rank (per-warp scratch stride)
 };
 
 constexpr int kSkThreads = 128;
@@ -1926,9 +1927,25 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_factor(SkelArgs S) {
     }
 }
 
-// per block (one warp): s = K(sigma,Y) x_Y, then c = U^{-1} L^{-1} P s
+// up to kSkNQ right-hand sides per pass: each entry is evaluated once for all
+constexpr int kSkNQ = 16;
+
+// xs[i * nq + q] = x[(q0 + q) n + perm[i]]: the pass's columns, point-major
 template <class T>
-__global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__restrict__ xs) {
+__global__ void k_skel_permute(const T *__restrict__ x, int64_t n, int q0, int nq, const int *__restrict__ perm,
+                               T *__restrict__ xs) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * nq) return;
+    const int64_t i = e / nq;
+    const int q = (int)(e - i * nq);
+    xs[e] = x[(int64_t)(q0 + q) * n + perm[i]];
+}
+
+// per block (one warp): s = K(sigma,Y) X_Y for the pass's nq <= NQ columns (each
+// entry evaluated once), then C = U^{-1} L^{-1} P s with lane q solving column q.
+// cbuf: kSkNQ values per pivot; sbuf: a scratch of max_rank x kSkNQ per warp.
+template <class T, int NQ>
+__global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__restrict__ xs, int nq) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * kSkThreads + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kSkThreads) >> 5;
@@ -1939,55 +1956,108 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
         const int x0 = S.box_start[X], y0 = S.box_start[Y], y1 = S.box_end[Y];
         const int64_t po = S.piv_off[b];
         const int *sg = S.sigma + po;
-        double *sv = S.sbuf + po, *cv = S.cbuf + po;
+        double *sv = S.sbuf + w0 * (int64_t)S.mr * kSkNQ, *cv = S.cbuf + po * kSkNQ;
         const double *M = S.lu + S.lu_off[b];
         const int *pv = S.lu_piv + po;
         for (int k = 0; k < r; ++k) {
             const int ps = x0 + sg[k];
-            double acc = 0.0;
-            for (int j = y0 + lane; j < y1; j += 32)
-                acc += skel_k(S.kind, S.kappa, S.px, S.py, S.pz, ps, j) * (double)xs[j];
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) sv[k] = acc;
+            double acc[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+            for (int j = y0 + lane; j < y1; j += 32) {
+                const double kv = skel_k(S.kind, S.kappa, S.px, S.py, S.pz, ps, j);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    if (q < nq) acc[q] += kv * (double)xs[(int64_t)j * nq + q];
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                if (q < nq) {
+                    double v = acc[q];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) sv[(int64_t)k * kSkNQ + q] = v;
+                }
+            }
         }
         __syncwarp();
-        for (int k = 0; k < r; ++k) {   // L z = P s (unit lower)
-            double acc = 0.0;
-            for (int l = lane; l < k; l += 32) acc += M[(size_t)k * r + l] * cv[l];
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) cv[k] = sv[pv[k]] - acc;
-            __syncwarp();
+        if constexpr (NQ == 1) {   // one column: the warp shares each dot product
+            for (int k = 0; k < r; ++k) {   // L z = P s (unit lower)
+                double acc = 0.0;
+                for (int l = lane; l < k; l += 32) acc += M[(size_t)k * r + l] * cv[(int64_t)l * kSkNQ];
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) cv[(int64_t)k * kSkNQ] = sv[(int64_t)pv[k] * kSkNQ] - acc;
+                __syncwarp();
+            }
+            for (int k = r - 1; k >= 0; --k) {   // U c = z
+                double acc = 0.0;
+                for (int l = k + 1 + lane; l < r; l += 32) acc += M[(size_t)k * r + l] * cv[(int64_t)l * kSkNQ];
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) cv[(int64_t)k * kSkNQ] = (cv[(int64_t)k * kSkNQ] - acc) / M[(size_t)k * r + k];
+                __syncwarp();
+            }
+        } else if (lane < nq) {   // lane q solves column q
+            const int q = lane;
+            for (int k = 0; k < r; ++k) {   // L z = P s (unit lower)
+                double acc = 0.0;
+                for (int l = 0; l < k; ++l) acc += M[(size_t)k * r + l] * cv[(int64_t)l * kSkNQ + q];
+                cv[(int64_t)k * kSkNQ + q] = sv[(int64_t)pv[k] * kSkNQ + q] - acc;
+            }
+            for (int k = r - 1; k >= 0; --k) {   // U c = z
+                double acc = 0.0;
+                for (int l = k + 1; l < r; ++l) acc += M[(size_t)k * r + l] * cv[(int64_t)l * kSkNQ + q];
+                cv[(int64_t)k * kSkNQ + q] = (cv[(int64_t)k * kSkNQ + q] - acc) / M[(size_t)k * r + k];
+            }
         }
-        for (int k = r - 1; k >= 0; --k) {   // U c = z
-            double acc = 0.0;
-            for (int l = k + 1 + lane; l < r; l += 32) acc += M[(size_t)k * r + l] * cv[l];
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) cv[k] = (cv[k] - acc) / M[(size_t)k * r + k];
-            __syncwarp();
-        }
+        __syncwarp();
     }
 }
 
-// per leaf: y = near + sum over its ancestors' blocks of K(rows, tau) c
-template <class T>
+// per leaf: Y = near + sum over its ancestors' blocks of K(rows, tau) C.  The
+// four warps split the blocks, lanes take rows (32 at a time); the partial sums
+// are added in shared memory in warp order.  nearbuf is column-major (N x nq).
+template <class T, int NQ>
 __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A, const int64_t *__restrict__ tgt_ptr,
-                                                          const T *__restrict__ nearbuf, T *__restrict__ y) {
+                                                          const T *__restrict__ nearbuf, T *__restrict__ y, int64_t n,
+                                                          int nq) {
+    __shared__ double red[kSkThreads / 32][32][NQ];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int z = blockIdx.x;
     const int Zg = (int)(A.offL + z);
     const int zs = A.box_start[Zg], ze = A.box_end[Zg];
-    for (int i = zs + threadIdx.x; i < ze; i += kSkThreads) {
-        double acc = 0.0;
+    for (int r0 = zs; r0 < ze; r0 += 32) {
+        const int i = r0 + lane;
+        const bool row = i < ze;
+        double acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+        int cnt = 0;
         for (int l = 1; l <= A.L; ++l) {
             const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
-            for (int64_t b = tgt_ptr[Ag]; b < tgt_ptr[Ag + 1]; ++b) {
+            for (int64_t b = tgt_ptr[Ag]; b < tgt_ptr[Ag + 1]; ++b, ++cnt) {
+                if ((cnt & 3) != warp) continue;
                 const int r = S.rank[b];
                 const int y0 = S.box_start[S.blk_src[b]];
                 const int64_t po = S.piv_off[b];
-                for (int k = 0; k < r; ++k)
-                    acc += skel_k(S.kind, S.kappa, S.px, S.py, S.pz, i, y0 + S.tau[po + k]) * S.cbuf[po + k];
+                for (int k = 0; k < r; ++k) {
+                    const double kv = row ? skel_k(S.kind, S.kappa, S.px, S.py, S.pz, i, y0 + S.tau[po + k]) : 0.0;
+                    const double *cv = S.cbuf + (po + k) * kSkNQ;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+                        if (q < nq) acc[q] += kv * cv[q];
+                }
             }
         }
-        y[A.perm[i]] = (T)(acc + (double)nearbuf[i]);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) red[warp][lane][q] = acc[q];
+        __syncthreads();
+        if (warp == 0 && row) {
+            const int64_t o = A.perm[i];
+            for (int q = 0; q < nq; ++q) {
+                const double v = ((red[0][lane][q] + red[1][lane][q]) + red[2][lane][q]) + red[3][lane][q];
+                y[(int64_t)q * n + o] = (T)(v + (double)nearbuf[(int64_t)q * n + i]);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -2002,30 +2072,39 @@ SkelArgs skel_args(Handle &h) {
     S.piv_off = h.piv_off; S.lu_off = h.lu_off;
     S.lu = h.lu; S.lu_piv = h.lu_piv;
     S.sbuf = h.skel_s; S.cbuf = h.skel_c;
+    S.mr = std::max(1, h.max_rank);
     return S;
 }
 
+int skel_src_grid(const Handle &h) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((h.nblk * 32 + kSkThreads - 1) / kSkThreads, 16LL * num_sms()));
+}
+
+// one pass of up to kSkNQ columns: x, y column-major (N x nrhs), from column q0
 template <class T>
-void matvec_skel_one(Handle &h, const T *x, T *y, cudaStream_t s) {
+void matvec_skel_pass(Handle &h, const T *x, T *y, int q0, int nq, cudaStream_t s) {
     const int64_t n = h.N;
-    T *xs = (T *)h.xs;
-    k_permute_in<T><<<gridn(n, 256), 256, 0, s>>>(x, h.perm, n, xs);
+    T *xs = (T *)h.skel_xs, *nearbuf = (T *)h.skel_near, *x1 = (T *)h.xs;
     LeafArgs A = leaf_args(h);
-    T *nearbuf = (T *)h.nearbuf;
-    H3D_CUDA(cudaEventRecord(h.ev_fork, s));
-    H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
+    k_skel_permute<T><<<gridn(n * nq, 256), 256, 0, s>>>(x, n, q0, nq, h.perm, xs);
+    // near field one column at a time on the side stream (the single-column kernel)
     const int near_grid = sizeof(T) == 4 ? std::min(h.nleaf, kNearCtasPerSm * num_sms()) : h.nleaf;
-    k_near<T><<<near_grid, kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
-    H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
+    for (int q = 0; q < nq; ++q) {
+        k_permute_in<T><<<gridn(n, 256), 256, 0, s>>>(x + (size_t)(q0 + q) * n, h.perm, n, x1);
+        H3D_CUDA(cudaEventRecord(h.ev_fork, s));
+        H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
+        k_near<T><<<near_grid, kLeafThreads, 0, h.side_stream>>>(A, x1, nearbuf + (size_t)q * n);
+        H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
+        H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));   // x1 is reused by the next column
+    }
     SkelArgs S = skel_args(h);
     if (h.nblk > 0) {
-        const int64_t warps = h.nblk;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((warps * 32 + kSkThreads - 1) / kSkThreads,
-                                                                      16LL * num_sms()));
-        k_skel_src<T><<<grid, kSkThreads, 0, s>>>(S, xs);
+        const int grid = skel_src_grid(h);
+        if (nq == 1) k_skel_src<T, 1><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+        else k_skel_src<T, kSkNQ><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
     }
-    H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
-    k_skel_leaf<T><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, y);
+    if (nq == 1) k_skel_leaf<T, 1><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, y + (size_t)q0 * n, n, nq);
+    else k_skel_leaf<T, kSkNQ><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, y + (size_t)q0 * n, n, nq);
     H3D_LAUNCH_CHECK();
 }
 
@@ -2283,8 +2362,10 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
     H3D_CUDA(cudaMemcpyAsync(h.lu_off, off.data(), (nblk + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     h.lu = h.mem.get<double>((size_t)std::max<int64_t>(h.lu_off_total, 1));
     h.lu_piv = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
-    h.skel_s = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1));
-    h.skel_c = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1));
+    h.skel_s = h.mem.get<double>((size_t)skel_src_grid(h) * (kSkThreads / 32) * std::max(1, h.max_rank) * kSkNQ);
+    h.skel_c = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1) * kSkNQ);
+    h.skel_xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
+    h.skel_near = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
     if (nblk > 0) {
         SkelArgs S = skel_args(h);
         const int grid = (int)std::min<int64_t>(nblk, 4LL * num_sms());
@@ -2296,12 +2377,10 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
 }
 
 void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, cudaStream_t s) {
-    const int64_t n = h.N;
-    for (int c = 0; c < nrhs; ++c) {
-        if (h.prec == H3D_FP64)
-            matvec_skel_one<double>(h, (const double *)x + (size_t)c * n, (double *)y + (size_t)c * n, s);
-        else
-            matvec_skel_one<float>(h, (const float *)x + (size_t)c * n, (float *)y + (size_t)c * n, s);
+    for (int q0 = 0; q0 < nrhs; q0 += kSkNQ) {
+        const int nq = std::min(kSkNQ, nrhs - q0);
+        if (h.prec == H3D_FP64) matvec_skel_pass<double>(h, (const double *)x, (double *)y, q0, nq, s);
+        else matvec_skel_pass<float>(h, (const float *)x, (float *)y, q0, nq, s);
     }
 }
 
