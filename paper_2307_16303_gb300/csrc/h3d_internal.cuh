@@ -126,6 +126,7 @@ struct Handle {
     int *lu_piv = nullptr;
     double *skel_s = nullptr, *skel_c = nullptr;  // K(sigma,Y) X and K(sigma,tau)^{-1} of it, 16 per pivot
     void *skel_xs = nullptr, *skel_near = nullptr; // pass columns: permuted x point-major, near field
+    int skel_nq = 16;                             // columns per skeleton pass (memory-bound choice)
     double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
     int L = 0;
 

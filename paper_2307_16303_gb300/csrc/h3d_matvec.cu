@@ -1861,6 +1861,7 @@ struct SkelArgs {
     int *lu_piv;
     double *sbuf, *cbuf;
     int mr;                   // largest rank (per-warp scratch stride)
+    int cst;                  // columns per pass (cbuf stride per pivot)
 };
 
 constexpr int kSkThreads = 128;
@@ -1956,7 +1957,7 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
         const int x0 = S.box_start[X], y0 = S.box_start[Y], y1 = S.box_end[Y];
         const int64_t po = S.piv_off[b];
         const int *sg = S.sigma + po;
-        double *sv = S.sbuf + w0 * (int64_t)S.mr * kSkNQ, *cv = S.cbuf + po * kSkNQ;
+        double *sv = S.sbuf + w0 * (int64_t)S.mr * kSkNQ, *cv = S.cbuf + po * S.cst;
         const double *M = S.lu + S.lu_off[b];
         const int *pv = S.lu_piv + po;
         for (int k = 0; k < r; ++k) {
@@ -1983,29 +1984,29 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
         if constexpr (NQ == 1) {   // one column: the warp shares each dot product
             for (int k = 0; k < r; ++k) {   // L z = P s (unit lower)
                 double acc = 0.0;
-                for (int l = lane; l < k; l += 32) acc += M[(size_t)k * r + l] * cv[(int64_t)l * kSkNQ];
+                for (int l = lane; l < k; l += 32) acc += M[(size_t)k * r + l] * cv[(int64_t)l * S.cst];
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) cv[(int64_t)k * kSkNQ] = sv[(int64_t)pv[k] * kSkNQ] - acc;
+                if (lane == 0) cv[(int64_t)k * S.cst] = sv[(int64_t)pv[k] * kSkNQ] - acc;
                 __syncwarp();
             }
             for (int k = r - 1; k >= 0; --k) {   // U c = z
                 double acc = 0.0;
-                for (int l = k + 1 + lane; l < r; l += 32) acc += M[(size_t)k * r + l] * cv[(int64_t)l * kSkNQ];
+                for (int l = k + 1 + lane; l < r; l += 32) acc += M[(size_t)k * r + l] * cv[(int64_t)l * S.cst];
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) cv[(int64_t)k * kSkNQ] = (cv[(int64_t)k * kSkNQ] - acc) / M[(size_t)k * r + k];
+                if (lane == 0) cv[(int64_t)k * S.cst] = (cv[(int64_t)k * S.cst] - acc) / M[(size_t)k * r + k];
                 __syncwarp();
             }
         } else if (lane < nq) {   // lane q solves column q
             const int q = lane;
             for (int k = 0; k < r; ++k) {   // L z = P s (unit lower)
                 double acc = 0.0;
-                for (int l = 0; l < k; ++l) acc += M[(size_t)k * r + l] * cv[(int64_t)l * kSkNQ + q];
-                cv[(int64_t)k * kSkNQ + q] = sv[(int64_t)pv[k] * kSkNQ + q] - acc;
+                for (int l = 0; l < k; ++l) acc += M[(size_t)k * r + l] * cv[(int64_t)l * S.cst + q];
+                cv[(int64_t)k * S.cst + q] = sv[(int64_t)pv[k] * kSkNQ + q] - acc;
             }
             for (int k = r - 1; k >= 0; --k) {   // U c = z
                 double acc = 0.0;
-                for (int l = k + 1; l < r; ++l) acc += M[(size_t)k * r + l] * cv[(int64_t)l * kSkNQ + q];
-                cv[(int64_t)k * kSkNQ + q] = (cv[(int64_t)k * kSkNQ + q] - acc) / M[(size_t)k * r + k];
+                for (int l = k + 1; l < r; ++l) acc += M[(size_t)k * r + l] * cv[(int64_t)l * S.cst + q];
+                cv[(int64_t)k * S.cst + q] = (cv[(int64_t)k * S.cst + q] - acc) / M[(size_t)k * r + k];
             }
         }
         __syncwarp();
@@ -2040,7 +2041,7 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A
                 const int64_t po = S.piv_off[b];
                 for (int k = 0; k < r; ++k) {
                     const double kv = row ? skel_k(S.kind, S.kappa, S.px, S.py, S.pz, i, y0 + S.tau[po + k]) : 0.0;
-                    const double *cv = S.cbuf + (po + k) * kSkNQ;
+                    const double *cv = S.cbuf + (po + k) * S.cst;
 #pragma unroll
                     for (int q = 0; q < NQ; ++q)
                         if (q < nq) acc[q] += kv * cv[q];
@@ -2073,6 +2074,7 @@ SkelArgs skel_args(Handle &h) {
     S.lu = h.lu; S.lu_piv = h.lu_piv;
     S.sbuf = h.skel_s; S.cbuf = h.skel_c;
     S.mr = std::max(1, h.max_rank);
+    S.cst = std::max(1, h.skel_nq);
     return S;
 }
 
@@ -2276,11 +2278,13 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
         H3D_CUDA(cudaMemcpyAsync(h.split_pbase, spbase.data(), sbox.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     }
     h.partial_elems = pel;
-    h.partial = h.mem.alloc((size_t)std::max<int64_t>(pel, 4) * es);
-    h.t = h.mem.alloc((size_t)std::max<int64_t>(h.sum_rank, 4) * es);
+    // the skeleton storage's products use none of the factor-streaming scratch
+    const bool stream = h.storage == H3D_STORE_FACTORS;
+    h.partial = h.mem.alloc((size_t)std::max<int64_t>(stream ? pel : 0, 4) * es);
+    h.t = h.mem.alloc((size_t)std::max<int64_t>(stream ? h.sum_rank : 0, 4) * es);
     h.xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * es);
     h.nearbuf = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * es);
-    if (h.leaf_size <= kMaxLeafMR) {   // scratch of the multi-RHS product (kNQ columns per pass)
+    if (stream && h.leaf_size <= kMaxLeafMR) {   // scratch of the multi-RHS product (kNQ columns per pass)
         h.xs_mr = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQ * es);
         h.nearbuf_mr = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQ * es);
         h.t_mr = h.mem.alloc((size_t)std::max<int64_t>(h.sum_rank, 4) * kNQ * es);
@@ -2333,7 +2337,7 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     h.tp_base = h.mem.get<int64_t>(tpb.size());
     H3D_CUDA(cudaMemcpyAsync(h.tp_base, tpb.data(), tpb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     h.tpartial_elems = tel;
-    h.tpartial = h.mem.alloc((size_t)std::max<int64_t>(tel, 4) * es);
+    h.tpartial = h.mem.alloc((size_t)std::max<int64_t>(stream ? tel : 0, 4) * es);
     h.nsplit_T = (int)tsb.size();
     h.tsplit_box = h.mem.get<int>(std::max<size_t>(tsb.size(), 1));
     h.tsplit_level = h.mem.get<int>(std::max<size_t>(tsb.size(), 1));
@@ -2362,8 +2366,17 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
     H3D_CUDA(cudaMemcpyAsync(h.lu_off, off.data(), (nblk + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     h.lu = h.mem.get<double>((size_t)std::max<int64_t>(h.lu_off_total, 1));
     h.lu_piv = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
+    // columns per pass: 16 unless the per-pivot solutions (FP64, sum_rank x columns)
+    // would take more than a third of the memory left after the LU factors
+    {
+        size_t free_b = 0, total_b = 0;
+        H3D_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        const double avail = (double)free_b - (double)h.lu_off_total * 8.0;
+        h.skel_nq = kSkNQ;
+        while (h.skel_nq > 1 && (double)h.sum_rank * h.skel_nq * 8.0 > avail / 3.0) h.skel_nq /= 2;
+    }
     h.skel_s = h.mem.get<double>((size_t)skel_src_grid(h) * (kSkThreads / 32) * std::max(1, h.max_rank) * kSkNQ);
-    h.skel_c = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1) * kSkNQ);
+    h.skel_c = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1) * h.skel_nq);
     h.skel_xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
     h.skel_near = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
     if (nblk > 0) {
@@ -2377,8 +2390,9 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
 }
 
 void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, cudaStream_t s) {
-    for (int q0 = 0; q0 < nrhs; q0 += kSkNQ) {
-        const int nq = std::min(kSkNQ, nrhs - q0);
+    const int width = std::max(1, std::min(kSkNQ, h.skel_nq));
+    for (int q0 = 0; q0 < nrhs; q0 += width) {
+        const int nq = std::min(width, nrhs - q0);
         if (h.prec == H3D_FP64) matvec_skel_pass<double>(h, (const double *)x, (double *)y, q0, nq, s);
         else matvec_skel_pass<float>(h, (const float *)x, (float *)y, q0, nq, s);
     }
