@@ -128,6 +128,21 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def replica_seeds(rank: int, seed: int) -> tuple[int, int]:
+    """Seeds of one rank's independent replica (points, right-hand sides): the
+    product has no exchange step, so ranks run replicas and share nothing."""
+    return seed + 1000 * rank, 2 + 1000 * rank
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The job's time is the slowest rank's (all_reduce MAX; identity on one rank)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_steps(fn, steps, warmup, torch, dist=None):
     for _ in range(warmup):
         fn()
@@ -302,8 +317,9 @@ def main():
     from paper_2307_16303_gb300.api import H3DMatrix, H3DError
 
     # independent replica per rank (the product does not need a collective)
-    pts = I.uniform(a.N, a.seed + 1000 * rank)
-    xh = I.rhs_normal(a.N, a.nrhs, 2 + 1000 * rank).astype(np.float32)
+    pseed, xseed = replica_seeds(rank, a.seed)
+    pts = I.uniform(a.N, pseed)
+    xh = I.rhs_normal(a.N, a.nrhs, xseed).astype(np.float32)
     dev_pts = torch.from_numpy(pts).cuda()
     A = H3DMatrix(dev_pts, leaf_size=a.leaf, tol=a.tol, precision="fp32")
     st = A.stats()
@@ -316,10 +332,7 @@ def main():
 
     with Clocks(local) as clk:
         ms = time_steps(step, a.steps, a.warmup, torch, dist)
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
 
     # per-kernel durations (CUDA events on the launching stream) over K more products
     phases = np.zeros(4)
