@@ -1022,8 +1022,10 @@ int h3do_direct_forces_rows(int kind, double kappa, const double *pts, int64_t N
 /* The skeleton form of the product (the paper's own storage, Sec. 4.1: only
  * the pivots and K(sigma,tau) are kept): y = near + sum over admissible blocks
  * of K(X,tau) K(sigma,tau)^{-1} K(sigma,Y) x_Y, each block evaluated from
- * kernel entries with a dense solve.  x, y: N values, the caller's order.     */
-int h3do_apply_skeleton(const h3do_t *h, const double *x, double *y)
+ * kernel entries with a dense solve; with transpose = 1 the transposed operator,
+ * y_Y += K(sigma,Y)^T K(sigma,tau)^{-T} K(X,tau)^T x_X (the near blocks are
+ * symmetric).  x, y: N values, the caller's order.                           */
+int h3do_apply_skeleton(const h3do_t *h, const double *x, double *y, int transpose)
 {
     const int64_t N = h->N;
     double *xs_, *ys_;
@@ -1050,18 +1052,36 @@ int h3do_apply_skeleton(const h3do_t *h, const double *x, double *y)
         block_ranges(h, b, &x0, &m, &y0, &n);
         M = (double *)malloc((size_t)r * r * sizeof(double));
         c = (double *)malloc((size_t)r * sizeof(double));
-        for (int k = 0; k < r; ++k) {
-            double sk = 0.0;
-            for (int j = 0; j < n; ++j) sk += kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + sg[k]), h->pts + 3 * (y0 + j)) * xs_[y0 + j];
-            c[k] = sk;
-            for (int l = 0; l < r; ++l)
-                M[(size_t)k * r + l] = kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + sg[k]), h->pts + 3 * (y0 + ta[l]));
+        if (!transpose) {
+            for (int k = 0; k < r; ++k) {
+                double sk = 0.0;
+                for (int j = 0; j < n; ++j) sk += kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + sg[k]), h->pts + 3 * (y0 + j)) * xs_[y0 + j];
+                c[k] = sk;
+                for (int l = 0; l < r; ++l)
+                    M[(size_t)k * r + l] = kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + sg[k]), h->pts + 3 * (y0 + ta[l]));
+            }
+        } else {   /* M^T a = K(X,tau)^T x_X */
+            for (int k = 0; k < r; ++k) {
+                double uk = 0.0;
+                for (int i = 0; i < m; ++i) uk += kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + i), h->pts + 3 * (y0 + ta[k])) * xs_[x0 + i];
+                c[k] = uk;
+                for (int l = 0; l < r; ++l)
+                    M[(size_t)k * r + l] = kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + sg[l]), h->pts + 3 * (y0 + ta[k]));
+            }
         }
         if (dense_solve(r, M, c)) { free(M); free(c); free(xs_); free(ys_); return ST_RANK; }
-        for (int i = 0; i < m; ++i) {
-            double acc = 0.0;
-            for (int k = 0; k < r; ++k) acc += kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + i), h->pts + 3 * (y0 + ta[k])) * c[k];
-            ys_[x0 + i] += acc;
+        if (!transpose) {
+            for (int i = 0; i < m; ++i) {
+                double acc = 0.0;
+                for (int k = 0; k < r; ++k) acc += kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + i), h->pts + 3 * (y0 + ta[k])) * c[k];
+                ys_[x0 + i] += acc;
+            }
+        } else {
+            for (int j = 0; j < n; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < r; ++k) acc += kernel_f(h->kind, h->kappa, h->pts + 3 * (x0 + sg[k]), h->pts + 3 * (y0 + j)) * c[k];
+                ys_[y0 + j] += acc;
+            }
         }
         free(M); free(c);
     }

@@ -112,7 +112,7 @@ def _load():
                                           C.POINTER(i64), C.POINTER(C.c_int)]),
             "h3do_apply": (i32, [P, P, i32, P, i32]),
             "h3do_energy_forces": (i32, [P, P, P, P]),
-            "h3do_apply_skeleton": (i32, [P, P, P]),
+            "h3do_apply_skeleton": (i32, [P, P, P, i32]),
             "h3do_direct_forces_rows": (i32, [i32, f64, P, i64, P, P, i64, P]),
         }
         for name, (res, args) in sig.items():
@@ -286,12 +286,13 @@ class Oracle:
         _check(_load().h3do_apply(self._h, _ptr(xf), nrhs, _ptr(y), 1 if transpose else 0))
         return y[:, 0] if vec else y
 
-    def matvec_skeleton(self, x) -> np.ndarray:
+    def matvec_skeleton(self, x, transpose: bool = False) -> np.ndarray:
         """The product in the skeleton form the paper stores (Sec. 4.1): near blocks
-        plus K(X,tau) K(sigma,tau)^{-1} K(sigma,Y) x_Y per admissible block."""
+        plus K(X,tau) K(sigma,tau)^{-1} K(sigma,Y) x_Y per admissible block (or the
+        transposed operator)."""
         xf = np.ascontiguousarray(x, np.float64).reshape(self.N)
         y = np.zeros(self.N, np.float64)
-        _check(_load().h3do_apply_skeleton(self._h, _ptr(xf), _ptr(y)))
+        _check(_load().h3do_apply_skeleton(self._h, _ptr(xf), _ptr(y), 1 if transpose else 0))
         return y
 
     # --- forces: gradient of E = q^T K~ q / 2 in the point positions -------

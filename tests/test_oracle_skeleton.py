@@ -35,3 +35,13 @@ def test_skeleton_error_tracks_tolerance():
     y = O.direct(p, x)
     e = [rel(O.Oracle(p, leaf_size=40, tol=t).compress().matvec_skeleton(x), y) for t in (1e-4, 1e-6, 1e-8)]
     assert e[0] > e[1] > e[2] and e[2] < 1e-6
+
+
+def test_skeleton_transpose_is_exact_transpose():
+    p = I.uniform(500, 267)
+    o = O.Oracle(p, leaf_size=10, tol=1e-5).compress()
+    E = np.eye(500)
+    A = np.stack([o.matvec_skeleton(E[:, j]) for j in range(500)], axis=1)
+    AT = np.stack([o.matvec_skeleton(E[:, j], transpose=True) for j in range(500)], axis=1)
+    assert np.abs(AT - A.T).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.norm(A - A.T) > 0
