@@ -83,9 +83,9 @@ typedef enum {
  *             entry of K(sigma,Y) and K(X,tau) in FP64 (their weights carry the
  *             condition of K(sigma,tau), so FP32 entries would not do) and solve
  *             with the LU; memory is O(sum of r^2) instead of O(sum of r (m+n)).
- *             Supports h3d_matvec (any nrhs, one column at a time), the batch
- *             calls and h3d_forces; h3d_matvec_T, h3d_energy and
- *             h3d_matvec_profile return H3D_ERR_ARG.                           */
+ *             Supports every product call (passes of up to 16 columns, each
+ *             entry evaluated once per pass), h3d_energy and h3d_forces;
+ *             h3d_matvec_profile returns H3D_ERR_ARG.                           */
 typedef enum {
     H3D_STORE_FACTORS = 0,
     H3D_STORE_SKELETON = 1

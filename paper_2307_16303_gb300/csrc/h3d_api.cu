@@ -139,7 +139,6 @@ static h3d_status matvec_common(h3d_handle hh, const void *x, void *y, int nrhs,
     if (!h.ok) return H3D_ERR_STATE;
     if (h3d_status e = async_error(h)) return e;
     if (!x || !y || nrhs < 1 || x == y) return H3D_ERR_ARG;
-    if (transpose && h.storage == H3D_STORE_SKELETON) return H3D_ERR_ARG;
     return guard([&] { h3d::run_matvec(h, x, y, nrhs, transpose, as_stream(stream)); });
 }
 
@@ -157,7 +156,6 @@ h3d_status h3d_energy(h3d_handle hh, const void *q, double *E, void *grad, void 
     if (!h.ok) return H3D_ERR_STATE;
     if (h3d_status e = async_error(h)) return e;
     if (!q || !E || q == grad) return H3D_ERR_ARG;
-    if (h.storage == H3D_STORE_SKELETON) return H3D_ERR_ARG;   // needs the transpose product
     return guard([&] { h3d::energy(h, q, E, grad, as_stream(stream)); });
 }
 

@@ -127,6 +127,7 @@ struct Handle {
     double *skel_s = nullptr, *skel_c = nullptr;  // K(sigma,Y) X and K(sigma,tau)^{-1} of it, 16 per pivot
     void *skel_xs = nullptr, *skel_near = nullptr; // pass columns: permuted x point-major, near field
     int skel_nq = 16;                             // columns per skeleton pass (memory-bound choice)
+    int64_t *skel_src_ptr = nullptr, *skel_src_order = nullptr;   // blocks by source box (transpose)
     double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
     int L = 0;
 
@@ -339,7 +340,7 @@ int matvec_passes(const Handle &h, int nrhs, bool transpose);  // kernel sequenc
 void energy(Handle &h, const void *q, double *E, void *grad, cudaStream_t s);
 void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s);
 void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp);
-void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, cudaStream_t s);
+void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s);
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s,
                 cudaEvent_t *ev = nullptr);  // h3d_matvec.cu; ev: 5 events per rhs
 

@@ -2062,6 +2062,129 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A
     }
 }
 
+// transpose, per block (one warp): u = K(X,tau)^T X_X for the pass's columns,
+// then a = M^{-T} u from P M = L U: U^T z = u, L^T w = z, a = P^T w.
+template <class T, int NQ>
+__global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *__restrict__ xs, int nq) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * kSkThreads + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kSkThreads) >> 5;
+    for (int64_t b = w0; b < S.nblk; b += nw) {
+        const int r = S.rank[b];
+        if (r == 0) continue;
+        const int X = S.blk_tgt[b], Y = S.blk_src[b];
+        const int x0 = S.box_start[X], x1 = S.box_end[X], y0 = S.box_start[Y];
+        const int64_t po = S.piv_off[b];
+        const int *ta = S.tau + po;
+        double *sv = S.sbuf + w0 * (int64_t)S.mr * kSkNQ, *cv = S.cbuf + po * S.cst;
+        const double *M = S.lu + S.lu_off[b];
+        const int *pv = S.lu_piv + po;
+        for (int k = 0; k < r; ++k) {
+            const int pt = y0 + ta[k];
+            double acc[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+            for (int i = x0 + lane; i < x1; i += 32) {
+                const double kv = skel_k(S.kind, S.kappa, S.px, S.py, S.pz, i, pt);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    if (q < nq) acc[q] += kv * (double)xs[(int64_t)i * nq + q];
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                if (q < nq) {
+                    double v = acc[q];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) sv[(int64_t)k * kSkNQ + q] = v;
+                }
+            }
+        }
+        __syncwarp();
+        // z and w overwrite u in sv; a is scattered into cv by the row order
+        if constexpr (NQ == 1) {
+            for (int k = 0; k < r; ++k) {   // U^T z = u
+                double acc = 0.0;
+                for (int l = lane; l < k; l += 32) acc += M[(size_t)l * r + k] * sv[(int64_t)l * kSkNQ];
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) sv[(int64_t)k * kSkNQ] = (sv[(int64_t)k * kSkNQ] - acc) / M[(size_t)k * r + k];
+                __syncwarp();
+            }
+            for (int k = r - 1; k >= 0; --k) {   // L^T w = z (unit diagonal)
+                double acc = 0.0;
+                for (int l = k + 1 + lane; l < r; l += 32) acc += M[(size_t)l * r + k] * sv[(int64_t)l * kSkNQ];
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) sv[(int64_t)k * kSkNQ] -= acc;
+                __syncwarp();
+            }
+            for (int k = lane; k < r; k += 32) cv[(int64_t)pv[k] * S.cst] = sv[(int64_t)k * kSkNQ];
+        } else if (lane < nq) {
+            const int q = lane;
+            for (int k = 0; k < r; ++k) {
+                double acc = 0.0;
+                for (int l = 0; l < k; ++l) acc += M[(size_t)l * r + k] * sv[(int64_t)l * kSkNQ + q];
+                sv[(int64_t)k * kSkNQ + q] = (sv[(int64_t)k * kSkNQ + q] - acc) / M[(size_t)k * r + k];
+            }
+            for (int k = r - 1; k >= 0; --k) {
+                double acc = 0.0;
+                for (int l = k + 1; l < r; ++l) acc += M[(size_t)l * r + k] * sv[(int64_t)l * kSkNQ + q];
+                sv[(int64_t)k * kSkNQ + q] -= acc;
+            }
+            for (int k = 0; k < r; ++k) cv[(int64_t)pv[k] * S.cst + q] = sv[(int64_t)k * kSkNQ + q];
+        }
+        __syncwarp();
+    }
+}
+
+// transpose, per leaf: Y = near + sum over blocks whose source is an ancestor of
+// the leaf of K(sigma, rows)^T a, blocks taken from the source-major index
+template <class T, int NQ>
+__global__ void __launch_bounds__(kSkThreads) k_skelT_leaf(SkelArgs S, LeafArgs A, const int64_t *__restrict__ src_ptr,
+                                                           const int64_t *__restrict__ src_order,
+                                                           const T *__restrict__ nearbuf, T *__restrict__ y,
+                                                           int64_t n, int nq) {
+    __shared__ double red[kSkThreads / 32][32][NQ];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int z = blockIdx.x;
+    const int Zg = (int)(A.offL + z);
+    const int zs = A.box_start[Zg], ze = A.box_end[Zg];
+    for (int r0 = zs; r0 < ze; r0 += 32) {
+        const int i = r0 + lane;
+        const bool row = i < ze;
+        double acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+        int cnt = 0;
+        for (int l = 1; l <= A.L; ++l) {
+            const int Bg = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
+            for (int64_t e = src_ptr[Bg]; e < src_ptr[Bg + 1]; ++e, ++cnt) {
+                if ((cnt & 3) != warp) continue;
+                const int64_t b = src_order[e];
+                const int r = S.rank[b];
+                const int x0 = S.box_start[S.blk_tgt[b]];
+                const int64_t po = S.piv_off[b];
+                for (int k = 0; k < r; ++k) {
+                    const double kv = row ? skel_k(S.kind, S.kappa, S.px, S.py, S.pz, x0 + S.sigma[po + k], i) : 0.0;
+                    const double *cv = S.cbuf + (po + k) * S.cst;
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+                        if (q < nq) acc[q] += kv * cv[q];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) red[warp][lane][q] = acc[q];
+        __syncthreads();
+        if (warp == 0 && row) {
+            const int64_t o = A.perm[i];
+            for (int q = 0; q < nq; ++q) {
+                const double v = ((red[0][lane][q] + red[1][lane][q]) + red[2][lane][q]) + red[3][lane][q];
+                y[(int64_t)q * n + o] = (T)(v + (double)nearbuf[(int64_t)q * n + i]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 SkelArgs skel_args(Handle &h) {
     SkelArgs S{};
     S.kind = h.kernel;
@@ -2084,7 +2207,7 @@ int skel_src_grid(const Handle &h) {
 
 // one pass of up to kSkNQ columns: x, y column-major (N x nrhs), from column q0
 template <class T>
-void matvec_skel_pass(Handle &h, const T *x, T *y, int q0, int nq, cudaStream_t s) {
+void matvec_skel_pass(Handle &h, const T *x, T *y, int q0, int nq, bool transpose, cudaStream_t s) {
     const int64_t n = h.N;
     T *xs = (T *)h.skel_xs, *nearbuf = (T *)h.skel_near, *x1 = (T *)h.xs;
     LeafArgs A = leaf_args(h);
@@ -2102,11 +2225,25 @@ void matvec_skel_pass(Handle &h, const T *x, T *y, int q0, int nq, cudaStream_t 
     SkelArgs S = skel_args(h);
     if (h.nblk > 0) {
         const int grid = skel_src_grid(h);
-        if (nq == 1) k_skel_src<T, 1><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
-        else k_skel_src<T, kSkNQ><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+        if (transpose) {
+            if (nq == 1) k_skelT_src<T, 1><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+            else k_skelT_src<T, kSkNQ><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+        } else {
+            if (nq == 1) k_skel_src<T, 1><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+            else k_skel_src<T, kSkNQ><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+        }
     }
-    if (nq == 1) k_skel_leaf<T, 1><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, y + (size_t)q0 * n, n, nq);
-    else k_skel_leaf<T, kSkNQ><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, y + (size_t)q0 * n, n, nq);
+    T *yq = y + (size_t)q0 * n;
+    if (transpose) {
+        if (nq == 1)
+            k_skelT_leaf<T, 1><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.skel_src_ptr, h.skel_src_order, nearbuf, yq, n, nq);
+        else
+            k_skelT_leaf<T, kSkNQ><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.skel_src_ptr, h.skel_src_order, nearbuf, yq, n,
+                                                                 nq);
+    } else {
+        if (nq == 1) k_skel_leaf<T, 1><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, yq, n, nq);
+        else k_skel_leaf<T, kSkNQ><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, yq, n, nq);
+    }
     H3D_LAUNCH_CHECK();
 }
 
@@ -2379,6 +2516,22 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
     h.skel_c = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1) * h.skel_nq);
     h.skel_xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
     h.skel_near = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
+    {   // blocks grouped by source box (stable), for the transpose product
+        const int64_t nboxes = h.n_boxes;
+        std::vector<int> src(nblk);
+        if (nblk > 0) H3D_CUDA(cudaMemcpyAsync(src.data(), h.blk_src, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+        H3D_CUDA(cudaStreamSynchronize(s));
+        std::vector<int64_t> ptr(nboxes + 1, 0), order(std::max<int64_t>(nblk, 1), 0);
+        for (int64_t b = 0; b < nblk; ++b) ptr[src[b] + 1]++;
+        for (int64_t g = 0; g < nboxes; ++g) ptr[g + 1] += ptr[g];
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t b = 0; b < nblk; ++b) order[fill[src[b]]++] = b;
+        h.skel_src_ptr = h.mem.get<int64_t>((size_t)nboxes + 1);
+        h.skel_src_order = h.mem.get<int64_t>(order.size());
+        H3D_CUDA(cudaMemcpyAsync(h.skel_src_ptr, ptr.data(), ptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.skel_src_order, order.data(), order.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                 s));
+    }
     if (nblk > 0) {
         SkelArgs S = skel_args(h);
         const int grid = (int)std::min<int64_t>(nblk, 4LL * num_sms());
@@ -2389,19 +2542,19 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
     (void)tmp;
 }
 
-void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, cudaStream_t s) {
+void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s) {
     const int width = std::max(1, std::min(kSkNQ, h.skel_nq));
     for (int q0 = 0; q0 < nrhs; q0 += width) {
         const int nq = std::min(width, nrhs - q0);
-        if (h.prec == H3D_FP64) matvec_skel_pass<double>(h, (const double *)x, (double *)y, q0, nq, s);
-        else matvec_skel_pass<float>(h, (const float *)x, (float *)y, q0, nq, s);
+        if (h.prec == H3D_FP64) matvec_skel_pass<double>(h, (const double *)x, (double *)y, q0, nq, transpose, s);
+        else matvec_skel_pass<float>(h, (const float *)x, (float *)y, q0, nq, transpose, s);
     }
 }
 
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s, cudaEvent_t *ev) {
     const int64_t n = h.N;
-    if (h.storage == H3D_STORE_SKELETON) {   // transposes are refused by the entry points
-        matvec_skeleton(h, x, y, nrhs, s);
+    if (h.storage == H3D_STORE_SKELETON) {
+        matvec_skeleton(h, x, y, nrhs, transpose, s);
         return;
     }
     if (use_wide(h, nrhs, transpose)) {

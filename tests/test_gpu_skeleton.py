@@ -5,7 +5,8 @@
   storage product of a handle built the same way to 1e-9.
 * FP32 handle: within 1e-6 of the direct sum at tol 1e-7; several right-hand
   sides; forces work unchanged; the stored bytes are far below the factors'.
-* The transpose product and the energy are refused (H3D_ERR_ARG).
+* The transpose product equals the oracle's skeleton transpose (FP64, 1e-10);
+  the energy and its gradient follow from the two products.
 """
 import numpy as np
 import pytest
@@ -39,11 +40,19 @@ def test_skeleton_fp64_matches_oracle_and_factor_storage():
     assert rel(ys, o.matvec_skeleton(x)) <= 1e-10
     assert rel(ys, F.matvec(xt).cpu().numpy()) <= 1e-9
     assert S.stats()["factor_bytes"] < 0.5 * F.stats()["factor_bytes"]
+    yT = S.matvec_T(xt).cpu().numpy()
+    yTo = o.matvec_skeleton(x, transpose=True)
+    assert rel(yT, yTo) <= 1e-10
+    E, g = S.energy(xt)
+    assert abs(E.item() - 0.5 * x @ ys) <= 1e-12 * abs(0.5 * x @ ys)
+    assert rel(g.cpu().numpy(), 0.5 * (o.matvec_skeleton(x) + yTo)) <= 1e-10
+    X3 = np.ascontiguousarray(np.stack([x, 2 * x, -x], axis=1))   # transpose in one 3-column pass
+    YT3 = S.matvec_T(torch.from_numpy(X3).cuda()).cpu().numpy()
+    assert rel(YT3[:, 1], 2 * yT) <= 1e-12
 
 
 def test_skeleton_fp32_vs_direct_multi_rhs_and_forces():
     import torch
-    from paper_2307_16303_gb300.api import H3DError
     n = 20000
     pts = I.uniform(n, 273)
     S = H(pts, leaf_size=64, tol=1e-7, precision="fp32", storage="skeleton")
@@ -58,7 +67,3 @@ def test_skeleton_fp32_vs_direct_multi_rhs_and_forces():
     rows = np.arange(0, n, 97)
     Fx = O.direct_forces_rows(pts, q.double().cpu().numpy(), rows)
     assert rel(Fo.cpu().numpy()[rows], Fx) <= 1e-5
-    with pytest.raises(H3DError):
-        S.matvec_T(q)
-    with pytest.raises(H3DError):
-        S.energy(q)
