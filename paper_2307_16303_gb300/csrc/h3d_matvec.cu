@@ -1614,7 +1614,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) k_tc_stream(TsArgs P) {
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int k = hk + u;
-                    split_tf32_fast((live && k < nk) ? ta[base + k * stride] : 0.f, h[u], l[u]);
+                    split_tf32((live && k < nk) ? ta[base + k * stride] : 0.f, h[u], l[u]);
                 }
                 const uint32_t acol = tmem + tlane + kTmA + 64u * (uint32_t)b + (uint32_t)hk;
                 tmem_st16(acol, h);
@@ -1624,7 +1624,7 @@ __global__ void __launch_bounds__(kTsThreads, 1) k_tc_stream(TsArgs P) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int k = kb + u;
-                        split_tf32_fast(k < nk ? tb[k * kNQW + lane] : 0.f, bh[u], bl[u]);
+                        split_tf32(k < nk ? tb[k * kNQW + lane] : 0.f, bh[u], bl[u]);
                     }
                     unsigned char *bbuf = bops + b * kTsBBuf;
                     const int off = kmajor_off(lane, kb);
