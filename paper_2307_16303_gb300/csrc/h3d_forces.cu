@@ -452,7 +452,7 @@ unsigned gn(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1
 }  // namespace
 
 void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s) {
-    constexpr int kFarCtas = 2;   // per SM
+    constexpr int kFarCtas = 5;   // per SM (43 KB of shared memory each)
     int dev = 0, sms = 0;
     H3D_CUDA(cudaGetDevice(&dev));
     H3D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
