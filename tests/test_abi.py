@@ -52,3 +52,17 @@ def test_oracle_shares_nothing_with_the_cuda_path():
     for f in ("api.py", "build_ext.py", "inputs.py", "__init__.py"):
         s = open(os.path.join(ROOT, "paper_2307_16303_gb300", f)).read()
         assert "import oracle" not in s and "from oracle" not in s
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_gpu():
+    """Argument checks happen before any device work, so they run on the CPU."""
+    import ctypes as C
+    from paper_2307_16303_gb300 import api
+    L = api.lib()
+    d = C.c_double()
+    assert L.h3d_energy(None, None, C.byref(d), None, None) == 1        # H3D_ERR_ARG
+    assert L.h3d_forces(None, None, None, None, None) == 1
+    out = C.c_void_p()
+    assert L.h3d_batch_create(None, 0, C.byref(out)) == 1
+    assert L.h3d_batch_matvec(None, None, None, None) == 1
+    assert L.h3d_batch_free(None) == 0                                  # freeing nothing is fine
