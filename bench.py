@@ -235,25 +235,57 @@ def run_batched(a):
     seq = sum(time_steps(lambda m=m, x=x, y=y: m.matvec(x, out=y), a.steps, a.warmup, torch) for m, x, y in
               zip(mats, xs, ys))
     B = H3DBatch(mats)
+    forms = {}
+    if B.info()["persistent"] == 1:
+        B.set_mode(True)
+        forms["persistent_untuned_ms"] = round(time_steps(lambda: B.matvec(xs, ys), a.steps, a.warmup, torch), 4)
     branches = B.tune(xs, ys)
+    info = B.info()
     with Clocks(torch.cuda.current_device()) as clk:
         ms = time_steps(lambda: B.matvec(xs, ys), a.steps, a.warmup, torch)
+    # the other form, for comparison (then back to the tuned choice)
+    if info["persistent"] == 1:
+        B.set_mode(False)
+        forms["graph_ms"] = round(time_steps(lambda: B.matvec(xs, ys), a.steps, a.warmup, torch), 4)
+        forms["persistent_ms"] = round(ms, 4)
+    else:
+        forms["graph_ms"] = round(ms, 4)
+        if info["persistent"] == 0:
+            B.set_mode(True)
+            forms["persistent_ms"] = round(time_steps(lambda: B.matvec(xs, ys), a.steps, a.warmup, torch), 4)
+    B.set_mode(info["persistent"] == 1)
+    B.matvec(xs, ys)
+    torch.cuda.synchronize()
     errs = []
     for c in (0, 1, 2, 3):
         rows = I.sample_rows(int(sizes[c]), 256, 8 + c)
         ref = O.direct_rows(pts[c], xs[c].double().cpu().numpy(), rows, kernel=kerns[c])
         got = ys[c].double().cpu().numpy()[rows]
         errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
-    out = {"metric": "HODLR3D batched matvec ms, 64 clouds (one graph launch)", "value": round(ms, 4), "unit": "ms",
+    # algorithmic bytes: every factor once, x read and y written once
+    fbytes = sum(m.stats()["factor_bytes"] for m in mats)
+    alg = fbytes + 8 * int(sizes.sum())
+    gbs = alg / (ms * 1e-3) / 1e9
+    peak, src = peaks()
+    persistent = info["persistent"] == 1
+    out = {"metric": "HODLR3D batched matvec ms, 64 clouds (one persistent launch)" if persistent else
+                     "HODLR3D batched matvec ms, 64 clouds (one graph launch)",
+           "value": round(ms, 4), "unit": "ms",
            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"64 clouds, N log-uniform in [8192, {a.batch_nmax}] seed 5, even: uniform cube, "
                                   f"odd: unit sphere; Laplace / Yukawa by pairs; leaf {a.leaf}, tol {a.tol}",
-                      "total_points": int(sizes.sum()), "n_min": int(sizes.min()), "n_max": int(sizes.max())},
-           "separate_products_ms": round(seq, 4), "speedup_vs_separate": round(seq / ms, 3),
-           "graph_branches": branches, "build_s": round(build_s, 1),
+                      "total_points": int(sizes.sum()), "n_min": int(sizes.min()), "n_max": int(sizes.max()),
+                      "l2": "inputs larger than L2 (factors >> 129 MB)"},
+           "form": "persistent" if persistent else "graph", "ctas_per_sm": info["ctas_per_sm"],
+           "graph_branches": branches if branches else info["branches"],
+           "separate_products_ms": round(seq, 4), "speedup_vs_separate": round(seq / ms, 3), "forms": forms,
+           "roofline": {"bound": "hbm", "kernel": "k_batch" if persistent else "graph", "achieved": round(gbs, 1),
+                        "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": src,
+                        "traffic": None, "alg_bytes_per_launch": alg},
+           "factor_bytes": fbytes, "build_s": round(build_s, 1),
            "rel_err_sampled_rows": errs, "clocks": clk.summary(),
-           "gpu_launches": 5 * 64 * a.steps}
+           "gpu_launches": (1 if persistent else 5 * 64) * a.steps}
     print(json.dumps(out), flush=True)
 
 

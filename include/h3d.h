@@ -169,24 +169,46 @@ h3d_status h3d_energy(h3d_handle h, const void *q, double *E, void *grad, void *
 h3d_status h3d_forces(h3d_handle h, const void *q, double *E, double *F, void *stream);
 
 /* ---- Batches of independent operators (many point clouds) ------------------
- * A batch runs the products of several handles (one right-hand side each) as
- * one CUDA graph: the first call captures every handle's product (the same
- * kernels as h3d_matvec) on `branches` concurrent streams, clouds assigned
- * longest first to the least loaded stream; later calls with the same vectors
- * replay it with a single graph launch on `stream` (new vectors re-capture).
- * The handles must outlive the batch and must not be used elsewhere while a
- * batch product is in flight.
+ * A batch runs the products y_i = A~_i x_i of several handles (one right-hand
+ * side each; Alg. 2 for every operator) in one of two forms:
+ *   persistent  ONE launch of a persistent kernel whose CTAs take work items of
+ *               every operator from a device queue (gather, near-field, reduce
+ *               and leaf items; an item waits, with a bounded wait, until the
+ *               items it reads are complete), replayed as a CUDA graph together
+ *               with the reset of the queue.  Available when every handle
+ *               stores factors (H3D_STORE_FACTORS) and all are FP64, or all
+ *               FP32 / FP32_3XTF32; it is then the default.
+ *   graph       every handle's own product (the kernels of h3d_matvec) captured
+ *               once into a CUDA graph on `branches` concurrent streams, clouds
+ *               assigned longest first to the least loaded stream; later calls
+ *               with the same vectors replay it (new vectors re-capture).
+ * The handles must be distinct (H3D_ERR_ARG otherwise), must outlive the batch
+ * and must not be used elsewhere while a batch product is in flight.  A wait that runs out in the persistent kernel
+ * leaves H3D_ERR_TIMEOUT in that handle's error word (reported by the next call).
  *   handles  host array of `count` built handles.
  *   x, y     host arrays of `count` device pointers: x[i], y[i] are N_i values
- *            of handle i's element type (caller's order); y overwritten.
- * h3d_batch_tune times the graph for 1, 2, 4, ... branches (up to 32 and the
- * number of handles; three replays each, CUDA events on `stream`), keeps the
- * fastest and reports it in *branches_out (may be NULL); it synchronises
- * `stream`.  The default is min(count, 8) branches.                          */
+ *            of handle i's element type (caller's order); y overwritten.  In the
+ *            persistent form new pointers are copied to the device, in stream
+ *            order, by the call that first uses them.
+ * h3d_batch_tune times (three runs after a warm-up, CUDA events on `stream`)
+ * the graph form with 1, 2, 4, ... branches (up to 32 and the number of
+ * handles) and, when available, the persistent form for leaves per item
+ * (near, leaf) in {(4,1), (4,2), (8,4)} and the most resident CTAs per SM or
+ * one or two fewer; it keeps the fastest and reports in *branches_out (may be NULL) the
+ * branch count, or 0 for the persistent form.  It synchronises `stream`.
+ * h3d_batch_set_mode selects the form (persistent != 0: the persistent kernel;
+ * H3D_ERR_ARG if it is not available) and, for the persistent form, the CTAs
+ * per SM of its grid (0 keeps the current value; capped at the occupancy
+ * limit).  h3d_batch_info reports the form in use
+ * (*persistent: 1 persistent, 0 graph, -1 graph and persistent unavailable),
+ * the CTAs per SM of the persistent form and the branch count of the graph
+ * form; any pointer may be NULL.                                              */
 typedef struct h3d_batch_s *h3d_batch;
 h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out);
 h3d_status h3d_batch_matvec(h3d_batch b, const void *const *x, void *const *y, void *stream);
 h3d_status h3d_batch_tune(h3d_batch b, const void *const *x, void *const *y, void *stream, int *branches_out);
+h3d_status h3d_batch_set_mode(h3d_batch b, int persistent, int ctas_per_sm);
+h3d_status h3d_batch_info(h3d_batch b, int *persistent, int *ctas_per_sm, int *branches);
 h3d_status h3d_batch_free(h3d_batch b);
 
 /* h3d_matvec with HOST x and y: copies x to the device, runs the product and

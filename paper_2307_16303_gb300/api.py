@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_
 EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3d_matvec_host", "h3d_free",
            "h3d_status_string", "h3d_get_stats", "h3d_matvec_profile", "h3d_export_tree", "h3d_export_lists",
            "h3d_export_pivots", "h3d_morton_order_noalloc", "h3d_energy", "h3d_forces",
-           "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_free")
+           "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_set_mode", "h3d_batch_info",
+           "h3d_batch_free")
 
 
 class H3DError(RuntimeError):
@@ -84,6 +85,8 @@ def lib():
             "h3d_batch_create": (i32, [P, i32, C.POINTER(P)]),
             "h3d_batch_matvec": (i32, [P, P, P, P]),
             "h3d_batch_tune": (i32, [P, P, P, P, C.POINTER(i32)]),
+            "h3d_batch_set_mode": (i32, [P, i32, i32]),
+            "h3d_batch_info": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
             "h3d_batch_free": (i32, [P]),
         }
         for name, (res, args) in sig.items():
@@ -286,8 +289,10 @@ class H3DMatrix:
 
 
 class H3DBatch:
-    """Products of several H3DMatrix operators (independent point clouds) as one
-    CUDA graph (h3d_batch_*).  The matrices must outlive the batch."""
+    """Products of several H3DMatrix operators (independent point clouds), one
+    column each, as one persistent launch (all FP32 or all FP64 factor-storage
+    matrices) or as one CUDA graph of every matrix's own kernels (h3d_batch_*).
+    The matrices must outlive the batch."""
 
     def __init__(self, mats):
         self.mats = list(mats)
@@ -315,12 +320,29 @@ class H3DBatch:
             raise H3DError(st, "h3d_batch_matvec")
 
     def tune(self, xs, ys, stream=None) -> int:
+        """Time both forms and keep the fastest; returns the graph's branch count,
+        or 0 when the persistent form won."""
         xp, yp = self._ptrs(xs, ys)
         nb = C.c_int()
         st = lib().h3d_batch_tune(self._b, xp, yp, _stream_ptr(stream), C.byref(nb))
         if st != 0:
             raise H3DError(st, "h3d_batch_tune")
         return nb.value
+
+    def set_mode(self, persistent: bool, ctas_per_sm: int = 0):
+        """Select the persistent kernel or the graph form (and the persistent
+        grid's CTAs per SM; 0 keeps the current value)."""
+        st = lib().h3d_batch_set_mode(self._b, 1 if persistent else 0, int(ctas_per_sm))
+        if st != 0:
+            raise H3DError(st, "h3d_batch_set_mode")
+
+    def info(self) -> dict:
+        """{"persistent": 1 | 0 | -1 (unavailable), "ctas_per_sm": .., "branches": ..}"""
+        p, c, b = C.c_int(), C.c_int(), C.c_int()
+        st = lib().h3d_batch_info(self._b, C.byref(p), C.byref(c), C.byref(b))
+        if st != 0:
+            raise H3DError(st, "h3d_batch_info")
+        return {"persistent": p.value, "ctas_per_sm": c.value, "branches": b.value}
 
     def free(self):
         if getattr(self, "_b", None) is not None and _lib is not None:

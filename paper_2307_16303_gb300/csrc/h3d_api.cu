@@ -330,11 +330,19 @@ h3d_status h3d_export_pivots(h3d_handle hh, int *rank, int *sigma, int *tau) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Batches of independent operators (many point clouds): the products of every
-// handle, one right-hand side each, are captured once into a CUDA graph whose
-// branches (one stream each) run the clouds side by side; later calls with the
-// same vectors replay the graph with one launch.
+// Batches of independent operators (many point clouds), one right-hand side
+// each.  Two ways to run them:
+//   persistent  one launch of the persistent multi-operator kernel
+//               (h3d_batch.cu), in a CUDA graph with the reset of its queue;
+//               available when every handle stores factors and all are FP32
+//               (or all FP64);
+//   graph       each handle's own kernels captured once into a CUDA graph
+//               whose branches (one stream each) run the clouds side by side;
+//               later calls with the same vectors replay it with one launch.
 struct h3d_batch_s {
+    h3d::BatchPlan *plan = nullptr;               // persistent form, if available
+    bool persistent = false;
+    int ctas_per_sm = 0;
     std::vector<h3d_handle> hs;
     std::vector<int64_t> cost;                    // per handle: factor entries + near interactions
     int branches = 0;                             // streams in the graph
@@ -347,6 +355,7 @@ struct h3d_batch_s {
     std::vector<const void *> xs;
     std::vector<void *> ys;
     ~h3d_batch_s() {
+        h3d::batch_plan_free(plan);
         if (exec) cudaGraphExecDestroy(exec);
         for (cudaEvent_t e : join) cudaEventDestroy(e);
         if (fork) cudaEventDestroy(fork);
@@ -426,14 +435,42 @@ bool same_vectors(const h3d_batch_s &B, const void *const *x, void *const *y) {
     return true;
 }
 
+// persistent form: leaves per near-field / leaf item
+constexpr int kDefaultNearGroup = 4, kDefaultLeafGroup = 2;   // (a near item gives each of 4 warps a leaf)
+
+void batch_run(h3d_batch_s &B, const void *const *x, void *const *y, cudaStream_t s) {
+    if (B.persistent) {
+        h3d::batch_plan_run(*B.plan, x, y, B.ctas_per_sm, s);
+        return;
+    }
+    if (!B.exec || B.exec_branches != B.branches || !same_vectors(B, x, y)) batch_capture(B, x, y, B.branches);
+    H3D_CUDA(cudaGraphLaunch(B.exec, s));
+}
+
+// mean time of three runs after one warm-up (synchronises s)
+float batch_time(h3d_batch_s &B, const void *const *x, void *const *y, cudaStream_t s, cudaEvent_t e0,
+                 cudaEvent_t e1) {
+    batch_run(B, x, y, s);
+    H3D_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) batch_run(B, x, y, s);
+    H3D_CUDA(cudaEventRecord(e1, s));
+    H3D_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    H3D_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms / 3.f;
+}
+
 }  // namespace
 
 extern "C" {
 
 h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out) {
     if (!handles || count < 1 || !out) return H3D_ERR_ARG;
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
         if (!handles[i] || !handles[i]->h.ok) return H3D_ERR_ARG;
+        for (int j = 0; j < i; ++j)   // a handle's scratch serves one product at a time
+            if (handles[j] == handles[i]) return H3D_ERR_ARG;
+    }
     h3d_batch_s *B = new (std::nothrow) h3d_batch_s;
     if (!B) return H3D_ERR_OOM;
     const h3d_status st = guard([&] {
@@ -445,6 +482,13 @@ h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out
         B->branches = std::min(count, 8);
         H3D_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
         H3D_CUDA(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+        std::vector<Handle *> hv;
+        for (int i = 0; i < count; ++i) hv.push_back(&handles[i]->h);
+        B->plan = h3d::batch_plan_create(hv, kDefaultNearGroup, kDefaultLeafGroup);
+        if (B->plan) {
+            B->persistent = true;
+            B->ctas_per_sm = h3d::batch_plan_max_ctas_per_sm(*B->plan);
+        }
     });
     if (st != H3D_OK) {
         delete B;
@@ -456,11 +500,7 @@ h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out
 
 h3d_status h3d_batch_matvec(h3d_batch B, const void *const *x, void *const *y, void *stream) {
     if (h3d_status e = batch_check(B, x, y)) return e;
-    return guard([&] {
-        if (!B->exec || B->exec_branches != B->branches || !same_vectors(*B, x, y))
-            batch_capture(*B, x, y, B->branches);
-        H3D_CUDA(cudaGraphLaunch(B->exec, as_stream(stream)));
-    });
+    return guard([&] { batch_run(*B, x, y, as_stream(stream)); });
 }
 
 h3d_status h3d_batch_tune(h3d_batch B, const void *const *x, void *const *y, void *stream, int *branches_out) {
@@ -470,29 +510,67 @@ h3d_status h3d_batch_tune(h3d_batch B, const void *const *x, void *const *y, voi
         cudaEvent_t e0, e1;
         H3D_CUDA(cudaEventCreate(&e0));
         H3D_CUDA(cudaEventCreate(&e1));
-        float best = 0.f;
+        float best = -1.f;
+        // graph form: 1, 2, 4, ... branches
         int best_nb = 1;
         const int n = (int)B->hs.size();
+        B->persistent = false;
         for (int nb = 1; nb <= std::min(n, 32); nb *= 2) {
-            batch_capture(*B, x, y, nb);
-            H3D_CUDA(cudaGraphLaunch(B->exec, s));   // warm-up
-            H3D_CUDA(cudaEventRecord(e0, s));
-            for (int r = 0; r < 3; ++r) H3D_CUDA(cudaGraphLaunch(B->exec, s));
-            H3D_CUDA(cudaEventRecord(e1, s));
-            H3D_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            H3D_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (nb == 1 || ms < best) {
+            B->branches = nb;
+            const float ms = batch_time(*B, x, y, s, e0, e1);
+            if (best < 0.f || ms < best) {
                 best = ms;
                 best_nb = nb;
             }
         }
+        B->branches = best_nb;
+        // persistent form: leaves per item x CTAs per SM
+        bool use_persistent = false;
+        int best_cps = 0, best_ng = kDefaultNearGroup, best_lg = kDefaultLeafGroup;
+        if (B->plan) {
+            const int cmax = h3d::batch_plan_max_ctas_per_sm(*B->plan);
+            static const int groups[][2] = {{4, 1}, {4, 2}, {8, 4}};
+            B->persistent = true;
+            for (const auto &g : groups) {
+                h3d::batch_plan_regroup(*B->plan, g[0], g[1]);
+                for (int cps : {cmax - 2, cmax - 1, cmax}) {
+                    if (cps < 1) continue;
+                    B->ctas_per_sm = cps;
+                    const float ms = batch_time(*B, x, y, s, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        use_persistent = true;
+                        best_cps = cps;
+                        best_ng = g[0];
+                        best_lg = g[1];
+                    }
+                }
+            }
+            h3d::batch_plan_regroup(*B->plan, best_ng, best_lg);
+            B->ctas_per_sm = use_persistent ? best_cps : cmax;
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        B->branches = best_nb;
-        batch_capture(*B, x, y, best_nb);
-        if (branches_out) *branches_out = best_nb;
+        B->persistent = use_persistent;
+        if (!use_persistent) batch_capture(*B, x, y, best_nb);
+        if (branches_out) *branches_out = use_persistent ? 0 : best_nb;
     });
+}
+
+h3d_status h3d_batch_set_mode(h3d_batch B, int persistent, int ctas_per_sm) {
+    if (!B || (persistent && !B->plan) || ctas_per_sm < 0) return H3D_ERR_ARG;
+    B->persistent = persistent != 0;
+    if (persistent && ctas_per_sm > 0)
+        return guard([&] { B->ctas_per_sm = std::min(ctas_per_sm, h3d::batch_plan_max_ctas_per_sm(*B->plan)); });
+    return H3D_OK;
+}
+
+h3d_status h3d_batch_info(h3d_batch B, int *persistent, int *ctas_per_sm, int *branches) {
+    if (!B) return H3D_ERR_ARG;
+    if (persistent) *persistent = B->persistent ? 1 : B->plan ? 0 : -1;
+    if (ctas_per_sm) *ctas_per_sm = B->ctas_per_sm;
+    if (branches) *branches = B->branches;
+    return H3D_OK;
 }
 
 h3d_status h3d_batch_free(h3d_batch B) {

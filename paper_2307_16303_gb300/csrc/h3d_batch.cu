@@ -1,0 +1,379 @@
+// h3d_batch.cu -- the single-column products y_i = A~_i x_i of many operators
+// (independent point clouds, each with its own tree, kernel and factors) in ONE
+// persistent launch (Alg. 2 for every operator at once), captured with the
+// reset of its queue into a CUDA graph.
+//
+// The work items of all operators sit in one device queue, phase-major:
+//   P  permute a chunk of points: xs = x[perm]                         (A5)
+//   G  one gather task: t_b = V_b^T xs(Y_b) over a row range           (A7)
+//   N  near field of a run of leaves (one leaf per warp) into the near
+//      buffer                                                         (A6)
+//   R  sum of the row-range partials of one split source box           (A7)
+//   L  a run of leaves: y(Z) = sum over levels of U panel * t, plus the
+//      near sum, written in the caller's order                         (A8, A9)
+// The G and N items of an operator are interleaved, so the CTAs that share an
+// SM mix HBM-bound factor streams with ALU-bound near-field tiles; the kernel
+// is held to 72 registers and a three-buffer leaf ring so that seven CTAs fit
+// on an SM (at 64 registers, eight would fit, but the spills cost more than
+// the extra CTA gains).  A CTA takes its next item with one atomic on the queue head
+// (fetched while the current item runs).  An item whose inputs are incomplete
+// waits on its operator's completion counters: G and N wait for every P of the
+// operator, R for every G, L for every G, R and N.  Items wait only on items
+// of earlier phases, which sit earlier in the queue and so were taken by CTAs
+// that are already running; every wait therefore ends.  Each is still bounded
+// (kWaitCycles): a CTA that gives up records H3D_ERR_TIMEOUT in the operator's
+// error word, raises the batch's abort flag (on which the other CTAs stop) and
+// leaves.
+//
+// Visibility: a finished item's CTA synchronises, then one thread fences at GPU
+// scope and adds 1 to the counter; a waiting thread reads the counter with an
+// acquire load, and its CTA synchronises before use.  Values written inside the
+// launch (xs, t, partials, near sums) are never read through the read-only path:
+// through L2 only where they are read once, through L1 (ld.global.ca) where
+// neighbouring leaves read them again (after the acquire).
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
+#include "h3d_async.cuh"
+#include "h3d_internal.cuh"
+#include "h3d_stream.cuh"
+
+namespace h3d {
+
+namespace {
+
+constexpr int kBatchThreads = kLeafThreads;
+constexpr int kPermChunk = 1024;                       // points per P item
+constexpr int kPermPerThread = kPermChunk / kBatchThreads;
+constexpr int kBatchCtasPerSm = 7;   // resident CTAs the register budget is set for (72 registers)
+// k_batch's leaf ring: one buffer fewer than k_leaf's (shared memory for seven or eight CTAs per SM)
+constexpr int kBatchStages = kStages - 1;
+// dynamic shared memory, one region per item kind (they overlap):
+//   L  ring of kBatchStages * kChunkBytes, then the leaf reduction buffer
+//   G  source values (kTaskMaxRows) at 0, reduction buffer at kRedOff
+//   N  per warp: kNearWarpSrc staged sources (32 B each) from 0, then the
+//      near-list prefixes (kNearWarpLists + 1 ints per warp) at kNearPreOff
+constexpr size_t kRedOff = 16384;
+constexpr size_t kNearPreOff = (size_t)(kBatchThreads / 32) * kNearWarpSrc * 32;
+constexpr size_t kLeafRedOff = (size_t)kBatchStages * kChunkBytes;
+constexpr size_t kBatchDynSmem = kLeafRedOff + kLeafThreads * 16;
+
+static_assert(kTaskMaxRows * sizeof(double) <= kRedOff, "gather rows overlap the reduction buffer");
+static_assert(kRedOff + kLeafThreads * 16 <= kBatchDynSmem, "gather reduction buffer out of range");
+static_assert(kNearPreOff + (kBatchThreads / 32) * (kNearWarpLists + 1) * sizeof(int) <= kBatchDynSmem,
+              "near staging out of range");
+static_assert(kPermChunk % kBatchThreads == 0, "P items split evenly over the threads");
+
+enum : int { kItemGather = 0, kItemNear = 1, kItemReduce = 2, kItemLeaf = 3, kItemPerm = 4 };
+
+struct BatchOp {
+    GatherArgs G;
+    SplitArgs S;
+    LeafArgs A;
+    const void *V, *U;
+    void *xs, *t, *partial, *nearbuf;
+    const int *perm;
+    int64_t N;
+    int ngtask, nsplit, nnear, nperm;   // items of the G, R, N and P phases
+};
+
+struct BatchArgs {
+    const BatchOp *ops;
+    const int4 *items;         // (operator, kind, first, count)
+    int nitems;
+    int *head;                 // next free queue slot
+    int *abort;
+    int4 *done;                // per operator: finished (G, R, N, P) items
+    const void *const *xy;     // per operator: x, y (device pointers)
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// true once *cnt >= target; false on abort or after kWaitCycles
+__device__ bool wait_count(const int *cnt, int target, const int *abort) {
+    if (ld_acquire(cnt) >= target) return true;
+    const long long t0 = clock64();
+    while (ld_acquire(cnt) < target) {
+        if (ld_acquire(abort)) return false;
+        if (clock64() - t0 > kWaitCycles) return false;
+        __nanosleep(128);
+    }
+    return true;
+}
+
+// the operator's arguments into shared memory, by the whole CTA
+__device__ __forceinline__ void load_op(const BatchOp *src_op, BatchOp &O) {
+    const int *src = reinterpret_cast<const int *>(src_op);
+    int *dst = reinterpret_cast<int *>(&O);
+    for (int k = threadIdx.x; k < (int)(sizeof(BatchOp) / sizeof(int)); k += blockDim.x) dst[k] = __ldg(src + k);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBatchThreads, kBatchCtasPerSm) k_batch(BatchArgs B) {
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bars[kBatchStages];
+    __shared__ ChunkPlan P;
+    __shared__ int s_next[2], s_ok;
+    __shared__ __align__(16) BatchOp O;   // the current item's operator
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kBatchStages; ++q) mbar_init(&bars[q], 1);
+        mbar_fence_init();
+        s_next[0] = atomicAdd(B.head, 1);
+    }
+    __syncthreads();
+    uint32_t ring = 0;   // chunks taken through the leaf ring so far
+    for (int iter = 0;; ++iter) {
+        const int it = s_next[iter & 1];
+        if (it >= B.nitems) break;
+        const int4 I = B.items[it];
+        int4 *done = B.done + I.x;
+        load_op(B.ops + I.x, O);   // the previous item is finished with O
+        if (threadIdx.x == 0) {
+            s_next[(iter + 1) & 1] = atomicAdd(B.head, 1);
+            bool ok = true;
+            const BatchOp &G = B.ops[I.x];
+            if (I.y == kItemGather || I.y == kItemNear) ok = wait_count(&done->w, G.nperm, B.abort);
+            else if (I.y == kItemReduce) ok = wait_count(&done->x, G.ngtask, B.abort);
+            else if (I.y == kItemLeaf)
+                ok = wait_count(&done->x, G.ngtask, B.abort) && wait_count(&done->y, G.nsplit, B.abort) &&
+                     wait_count(&done->z, G.nnear, B.abort);
+            if (!ok) {
+                if (!ld_acquire(B.abort)) atomicCAS(G.A.err, 0, (int)H3D_ERR_TIMEOUT);
+                atomicExch(B.abort, 1);
+            }
+            __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        if (I.y == kItemPerm) {   // all loads of a thread in flight together
+            const T *x = static_cast<const T *>(B.xy[2 * I.x]);
+            T *xs = static_cast<T *>(O.xs);
+            int idx[kPermPerThread];
+            T v[kPermPerThread];
+#pragma unroll
+            for (int k = 0; k < kPermPerThread; ++k) {
+                const int64_t i = (int64_t)I.z + threadIdx.x + k * kBatchThreads;
+                idx[k] = i < O.N ? O.perm[i] : -1;
+            }
+#pragma unroll
+            for (int k = 0; k < kPermPerThread; ++k) v[k] = idx[k] >= 0 ? x[idx[k]] : T(0);
+#pragma unroll
+            for (int k = 0; k < kPermPerThread; ++k)
+                if (idx[k] >= 0) xs[I.z + threadIdx.x + k * kBatchThreads] = v[k];
+        } else if (I.y == kItemGather) {
+            gather_task<T, kBatchThreads, 8, true>(O.G, I.z, static_cast<const T *>(O.V), static_cast<const T *>(O.xs),
+                                                   static_cast<T *>(O.t), static_cast<T *>(O.partial),
+                                                   reinterpret_cast<T *>(dyn), reinterpret_cast<T *>(dyn + kRedOff));
+        } else if (I.y == kItemNear) {   // one leaf per warp at a time
+            const int w = threadIdx.x >> 5;
+            using Src = typename std::conditional<sizeof(T) == 4, float4, Pt4d>::type;
+            Src *wsrc = reinterpret_cast<Src *>(dyn) + w * (sizeof(T) == 4 ? 2 : 1) * kNearWarpSrc;
+            int *wpre = reinterpret_cast<int *>(dyn + kNearPreOff) + w * (kNearWarpLists + 1);
+            for (int z = I.z + w; z < I.z + I.w; z += kBatchThreads / 32)
+                near_warp(O.A, z, static_cast<const T *>(O.xs), static_cast<T *>(O.nearbuf), wsrc, wpre);
+        } else if (I.y == kItemReduce) {
+            reduce_split<T, true>(O.S, I.z, kBatchThreads, static_cast<const T *>(O.partial), static_cast<T *>(O.t));
+        } else {
+            T *y = static_cast<T *>(const_cast<void *>(B.xy[2 * I.x + 1]));
+            bool ok = true;
+            for (int z = I.z; z < I.z + I.w && ok; ++z) {
+                ok = leaf_task<T, true, kBatchStages>(O.A, z, static_cast<const T *>(O.U), static_cast<const T *>(O.t),
+                                                      static_cast<const T *>(O.nearbuf), y, dyn, bars, P,
+                                                      reinterpret_cast<T *>(dyn + kLeafRedOff), ring);
+                __syncthreads();
+            }
+            if (!ok) {
+                if (threadIdx.x == 0) atomicExch(B.abort, 1);
+                break;
+            }
+        }
+        // the next item may hand this shared memory to bulk copies (async proxy)
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0 && I.y != kItemLeaf) {
+            __threadfence();
+            atomicAdd(I.y == kItemGather ? &done->x : I.y == kItemReduce ? &done->y : I.y == kItemNear ? &done->z
+                                                                                                     : &done->w, 1);
+        }
+    }
+}
+
+}  // namespace
+
+struct BatchPlan {
+    int elem = 4;                            // 4: FP32 operators, 8: FP64
+    int nops = 0;
+    int near_group = 0, leaf_group = 0;
+    std::vector<BatchOp> ops;
+    std::vector<Handle *> hs;
+    Arena mem;
+    void *d_ops = nullptr, *d_items = nullptr, *d_xy = nullptr;
+    int *d_state = nullptr;                  // head, abort, pad, pad, then done[nops] (int4 each)
+    int nitems = 0;
+    std::vector<const void *> xy;            // the pointers last copied to d_xy
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int exec_ctas = 0;
+    ~BatchPlan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+template <class V>
+void *upload(BatchPlan &p, void *old, const std::vector<V> &v) {
+    if (old) p.mem.free_one(old);
+    void *d = p.mem.alloc(std::max<size_t>(1, v.size()) * sizeof(V));
+    if (!v.empty()) H3D_CUDA(cudaMemcpy(d, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return d;
+}
+
+// The queue in phase order (P of every operator, then G and N, then R, then
+// L); within an operator its near runs are spread evenly among its gather
+// tasks.
+void build_items(BatchPlan &p) {
+    std::vector<int4> items;
+    for (int o = 0; o < p.nops; ++o)
+        for (int64_t i = 0; i < p.hs[o]->N; i += kPermChunk) items.push_back(make_int4(o, kItemPerm, (int)i, 0));
+    for (int o = 0; o < p.nops; ++o) {
+        const Handle &h = *p.hs[o];
+        const int ng = h.ngtask, nn = p.ops[o].nnear;
+        int gi = 0, ni = 0;
+        while (gi < ng || ni < nn) {
+            if (ni < nn && (gi >= ng || (int64_t)ni * ng <= (int64_t)gi * nn)) {   // keep ni / nn near gi / ng
+                const int z0 = ni * p.near_group;
+                items.push_back(make_int4(o, kItemNear, z0, std::min(p.near_group, h.nleaf - z0)));
+                ++ni;
+            } else {
+                items.push_back(make_int4(o, kItemGather, gi, 1));
+                ++gi;
+            }
+        }
+    }
+    for (int o = 0; o < p.nops; ++o)
+        for (int q = 0; q < p.hs[o]->nsplit; ++q) items.push_back(make_int4(o, kItemReduce, q, 1));
+    for (int o = 0; o < p.nops; ++o) {
+        const Handle &h = *p.hs[o];
+        for (int z0 = 0; z0 < h.nleaf; z0 += p.leaf_group)
+            items.push_back(make_int4(o, kItemLeaf, z0, std::min(p.leaf_group, h.nleaf - z0)));
+    }
+    p.nitems = (int)items.size();
+    p.d_items = upload(p, p.d_items, items);
+    if (p.exec) {
+        H3D_CUDA(cudaGraphExecDestroy(p.exec));
+        p.exec = nullptr;
+    }
+}
+
+}  // namespace
+
+BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, int leaf_group) {
+    if (hs.empty()) return nullptr;
+    const int elem = hs[0]->prec == H3D_FP64 ? 8 : 4;
+    for (Handle *h : hs)
+        if (h->storage != H3D_STORE_FACTORS || (h->prec == H3D_FP64 ? 8 : 4) != elem) return nullptr;
+    BatchPlan *p = new BatchPlan;
+    try {
+        p->elem = elem;
+        p->hs = hs;
+        p->nops = (int)hs.size();
+        for (int o = 0; o < p->nops; ++o) {
+            const Handle &h = *hs[o];
+            BatchOp op{};
+            op.G = GatherArgs{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
+            op.S = SplitArgs{h.split_box, h.split_ntask, h.split_pbase, h.Rv, h.ldv, h.vcol0, h.map_v};
+            op.A = leaf_args(h);
+            op.V = h.V;
+            op.U = h.U;
+            op.xs = h.xs;
+            op.N = h.N;
+            op.nperm = (int)((h.N + kPermChunk - 1) / kPermChunk);
+            op.t = h.t;
+            op.partial = h.partial;
+            op.nearbuf = h.nearbuf;
+            op.perm = h.perm;
+            op.ngtask = h.ngtask;
+            op.nsplit = h.nsplit;
+            p->ops.push_back(op);
+        }
+        batch_plan_regroup(*p, near_group, leaf_group);
+        p->d_state = p->mem.get<int>((size_t)(p->nops + 1) * 4);
+        p->d_xy = p->mem.alloc((size_t)p->nops * 2 * sizeof(void *));
+        H3D_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    } catch (...) {
+        delete p;
+        throw;
+    }
+    return p;
+}
+
+void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group) {
+    p.near_group = std::max(1, near_group);
+    p.leaf_group = std::max(1, leaf_group);
+    for (int o = 0; o < p.nops; ++o) p.ops[o].nnear = (p.hs[o]->nleaf + p.near_group - 1) / p.near_group;
+    p.d_ops = upload(p, p.d_ops, p.ops);
+    build_items(p);
+}
+
+int batch_plan_max_ctas_per_sm(const BatchPlan &p) {
+    int n = 0;
+    if (p.elem == 8) H3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<double>, kBatchThreads, kBatchDynSmem));
+    else H3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<float>, kBatchThreads, kBatchDynSmem));
+    return std::max(1, n);
+}
+
+void batch_plan_run(BatchPlan &p, const void *const *x, void *const *y, int ctas_per_sm, cudaStream_t s) {
+    ctas_per_sm = std::max(1, std::min(ctas_per_sm, batch_plan_max_ctas_per_sm(p)));
+    bool same = (int)p.xy.size() == 2 * p.nops;
+    for (int o = 0; o < p.nops && same; ++o) same = p.xy[2 * o] == x[o] && p.xy[2 * o + 1] == y[o];
+    if (!same) {
+        p.xy.resize(2 * p.nops);
+        for (int o = 0; o < p.nops; ++o) {
+            p.xy[2 * o] = x[o];
+            p.xy[2 * o + 1] = y[o];
+        }
+        // pageable source: the copy has taken the values when the call returns
+        H3D_CUDA(cudaMemcpyAsync(p.d_xy, p.xy.data(), p.xy.size() * sizeof(void *), cudaMemcpyHostToDevice, s));
+    }
+    if (!p.exec || p.exec_ctas != ctas_per_sm) {
+        if (p.exec) {
+            H3D_CUDA(cudaGraphExecDestroy(p.exec));
+            p.exec = nullptr;
+        }
+        int *st = p.d_state;
+        BatchArgs a{static_cast<const BatchOp *>(p.d_ops), static_cast<const int4 *>(p.d_items), p.nitems, st, st + 1,
+                    reinterpret_cast<int4 *>(st + 4), static_cast<const void *const *>(p.d_xy)};
+        const int grid = std::max(1, std::min(p.nitems, ctas_per_sm * num_sms()));
+        cudaGraph_t g = nullptr;
+        H3D_CUDA(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaMemsetAsync(st, 0, (size_t)(p.nops + 1) * sizeof(int4), p.cap);
+        if (le == cudaSuccess) {
+            if (p.elem == 8) k_batch<double><<<grid, kBatchThreads, kBatchDynSmem, p.cap>>>(a);
+            else k_batch<float><<<grid, kBatchThreads, kBatchDynSmem, p.cap>>>(a);
+            le = cudaGetLastError();
+        }
+        const cudaError_t ce = cudaStreamEndCapture(p.cap, &g);
+        if (le == cudaSuccess) le = ce;
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            H3D_CUDA(le);
+        }
+        const cudaError_t e = cudaGraphInstantiate(&p.exec, g, 0);
+        cudaGraphDestroy(g);
+        H3D_CUDA(e);
+        p.exec_ctas = ctas_per_sm;
+    }
+    H3D_CUDA(cudaGraphLaunch(p.exec, s));
+}
+
+void batch_plan_free(BatchPlan *p) { delete p; }
+
+}  // namespace h3d

@@ -344,4 +344,15 @@ void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, bool transpose
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s,
                 cudaEvent_t *ev = nullptr);  // h3d_matvec.cu; ev: 5 events per rhs
 
+// One persistent launch for the single-column products of many operators
+// (h3d_batch.cu).  batch_plan_create returns nullptr when the handles cannot
+// share one launch (skeleton storage, or FP32 and FP64 handles mixed).  The
+// group sizes are the leaves per near-field item and per leaf item.
+struct BatchPlan;
+BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, int leaf_group);
+void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group);
+int batch_plan_max_ctas_per_sm(const BatchPlan &p);
+void batch_plan_run(BatchPlan &p, const void *const *x, void *const *y, int ctas_per_sm, cudaStream_t s);
+void batch_plan_free(BatchPlan *p);
+
 }  // namespace h3d

@@ -24,60 +24,16 @@
 
 #include "h3d_async.cuh"
 #include "h3d_internal.cuh"
+#include "h3d_stream.cuh"
 
 namespace h3d {
 
 namespace {
 
-constexpr int kGatherThreads = 256;
-constexpr int kLeafThreads = 128;
 constexpr int64_t kTaskElems = 1 << 18;   // factor entries streamed by one gather task
-constexpr int kTaskMaxRows = 2048;
 // 32-column path: rows per gather task (the partial sums of split boxes cost
 // 32 columns of traffic each, so its tasks are tall)
 constexpr int kTaskRowsW = 4096;
-
-struct __align__(16) Pt4d {
-    double x, y, z, w;
-};
-__device__ __forceinline__ Pt4d make_pt4d(double x, double y, double z, double w) { return Pt4d{x, y, z, w}; }
-
-// Sum accumulator.  FP32 sums of hundreds of random-sign products lose about
-// u*sqrt(n/2) relative accuracy when added in sequence, so FP32 uses a
-// compensated (Kahan) sum; FP64 adds plainly.
-template <class T> struct Acc;
-template <> struct Acc<float> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ float get() const { return s - c; }
-};
-template <> struct Acc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double get() const { return s; }
-};
-
-template <class T> struct Vec;
-template <> struct Vec<float> {
-    using type = float4;
-    static constexpr int W = 4;
-    __device__ static __forceinline__ void get(const float4 &v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
-};
-template <> struct Vec<double> {
-    using type = double2;
-    static constexpr int W = 2;
-    __device__ static __forceinline__ void get(const double2 &v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
-};
-
-template <class T>
-__device__ __forceinline__ typename Vec<T>::type ld_stream(const T *p) {
-    return __ldcs(reinterpret_cast<const typename Vec<T>::type *>(p));
-}
 
 template <class T>
 __global__ void k_permute_in(const T *__restrict__ x, const int *__restrict__ perm, int64_t n, T *__restrict__ xs) {
@@ -85,476 +41,35 @@ __global__ void k_permute_in(const T *__restrict__ x, const int *__restrict__ pe
     if (i < n) xs[i] = x[perm[i]];
 }
 
-// ---------------------------------------------------------------------------
-// A7: T_Y = V_Y^T xs(Y) over rows [r0, r1) of Y
-struct GatherArgs {
-    const int4 *task;            // (box, row0, row1, direct?1:0)
-    const int64_t *pbase;        // partial base per task
-    const int *box_start, *Rv, *ldv;
-    const int64_t *vbase, *vcol0, *map_v;
-};
-
+// A7 over the host-built task list: one task per CTA
 template <class T>
 __global__ void __launch_bounds__(kGatherThreads) k_gather(GatherArgs G, const T *__restrict__ V,
                                                            const T *__restrict__ xs, T *__restrict__ t,
                                                            T *__restrict__ partial) {
-    constexpr int W = Vec<T>::W;
     __shared__ T xsm[kTaskMaxRows];
-    __shared__ T red[kGatherThreads * W];
-    const int4 task = G.task[blockIdx.x];
-    const int Y = task.x, r0 = task.y, r1 = task.z;
-    const int nrows = r1 - r0;
-    const int ld = G.ldv[Y], RvY = G.Rv[Y];
-    const int ncv = ld / W;
-    const T *Vb = V + G.vbase[Y] + (int64_t)r0 * ld;
-    const int ys = G.box_start[Y] + r0;
-    for (int r = threadIdx.x; r < nrows; r += kGatherThreads) xsm[r] = xs[ys + r];
-    __syncthreads();
-    const bool direct = task.w != 0;
-    const int64_t pb = G.pbase[blockIdx.x];
-    const int64_t vc0 = G.vcol0[Y];
-    if (ncv >= kGatherThreads) {
-        for (int cv = threadIdx.x; cv < ncv; cv += kGatherThreads) {
-            Acc<T> acc[W];
-            const T *p = Vb + cv * W;
-            int r = 0;
-            for (; r + 4 <= nrows; r += 4) {
-                typename Vec<T>::type v0 = ld_stream(p + (int64_t)r * ld), v1 = ld_stream(p + (int64_t)(r + 1) * ld),
-                                      v2 = ld_stream(p + (int64_t)(r + 2) * ld), v3 = ld_stream(p + (int64_t)(r + 3) * ld);
-                T a0[W], a1[W], a2[W], a3[W];
-                Vec<T>::get(v0, a0); Vec<T>::get(v1, a1); Vec<T>::get(v2, a2); Vec<T>::get(v3, a3);
-#pragma unroll
-                for (int e = 0; e < W; ++e)
-                    acc[e].add(a0[e] * xsm[r] + a1[e] * xsm[r + 1] + a2[e] * xsm[r + 2] + a3[e] * xsm[r + 3]);
-            }
-            for (; r < nrows; ++r) {
-                T a[W];
-                Vec<T>::get(ld_stream(p + (int64_t)r * ld), a);
-#pragma unroll
-                for (int e = 0; e < W; ++e) acc[e].add(a[e] * xsm[r]);
-            }
-#pragma unroll
-            for (int e = 0; e < W; ++e) {
-                const int c = cv * W + e;
-                if (c < RvY) {
-                    if (direct) t[G.map_v[vc0 + c]] = acc[e].get();
-                    else partial[pb + c] = acc[e].get();
-                }
-            }
-        }
-        return;
-    }
-    // few columns: split the rows over G groups, reduce in shared memory
-    const int Gn = kGatherThreads / ncv;
-    const int g = threadIdx.x / ncv, cv = threadIdx.x - g * ncv;
-    Acc<T> acc[W];
-    if (g < Gn) {
-        const T *p = Vb + cv * W;
-        int r = g;
-        for (; r + 3 * Gn < nrows; r += 4 * Gn) {
-            typename Vec<T>::type v0 = ld_stream(p + (int64_t)r * ld), v1 = ld_stream(p + (int64_t)(r + Gn) * ld),
-                                  v2 = ld_stream(p + (int64_t)(r + 2 * Gn) * ld),
-                                  v3 = ld_stream(p + (int64_t)(r + 3 * Gn) * ld);
-            T a0[W], a1[W], a2[W], a3[W];
-            Vec<T>::get(v0, a0); Vec<T>::get(v1, a1); Vec<T>::get(v2, a2); Vec<T>::get(v3, a3);
-#pragma unroll
-            for (int e = 0; e < W; ++e)
-                acc[e].add(a0[e] * xsm[r] + a1[e] * xsm[r + Gn] + a2[e] * xsm[r + 2 * Gn] + a3[e] * xsm[r + 3 * Gn]);
-        }
-        for (; r < nrows; r += Gn) {
-            T a[W];
-            Vec<T>::get(ld_stream(p + (int64_t)r * ld), a);
-#pragma unroll
-            for (int e = 0; e < W; ++e) acc[e].add(a[e] * xsm[r]);
-        }
-#pragma unroll
-        for (int e = 0; e < W; ++e) red[g * ld + cv * W + e] = acc[e].get();
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < RvY; c += kGatherThreads) {
-        T s = 0;
-        for (int q = 0; q < Gn; ++q) s += red[q * ld + c];
-        if (direct) t[G.map_v[vc0 + c]] = s;
-        else partial[pb + c] = s;
-    }
+    __shared__ T red[kGatherThreads * Vec<T>::W];
+    gather_task<T, kGatherThreads, 4, false>(G, blockIdx.x, V, xs, t, partial, xsm, red);
 }
-
-struct SplitArgs {
-    const int *box, *ntask;
-    const int64_t *pbase;
-    const int *Rv, *ldv;
-    const int64_t *vcol0, *map_v;
-};
 
 template <class T>
 __global__ void k_reduce_partials(SplitArgs S, const T *__restrict__ partial, T *__restrict__ t) {
-    const int q = blockIdx.x;
-    const int Y = S.box[q], nt = S.ntask[q], ld = S.ldv[Y], R = S.Rv[Y];
-    const int64_t pb = S.pbase[q], vc0 = S.vcol0[Y];
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        T s = 0;
-        for (int k = 0; k < nt; ++k) s += partial[pb + (int64_t)k * ld + c];
-        t[S.map_v[vc0 + c]] = s;
-    }
+    reduce_split<T, false>(S, blockIdx.x, blockDim.x, partial, t);
 }
 
-// ---------------------------------------------------------------------------
-// near field helpers: stage one source leaf, accumulate over it.
-struct LeafArgs {
-    int L, nleaf, kind;
-    double kappa, hL;
-    int64_t offL;
-    const int *box_start, *box_end, *perm, *leaf_ld, *leaf_anc, *R, *leaf_lo;
-    const int64_t *leaf_lp, *ubase, *tbase;
-    const int *near_ptr, *near_src;
-    const unsigned char *near_dir;
-    const float4 *ploc, *ploc_lo;
-    const double *px, *py, *pz;
-    // transpose
-    const int *Rv, *ldv;
-    const int64_t *vbase, *vcol0, *map_v, *tp_base;
-    int *err;                         // device-visible error word (bounded waits that gave up)
-};
-
-// Near-field sum for targets of leaf z: out[i] = sum over near leaves of
-// K(i,j) xs_j (i in [0, m)).  Thread layout: S source groups x m targets.
-template <class T>
-__device__ void near_field(const LeafArgs &A, int z, int zs, int m, const T *__restrict__ xs, T *outsm,
-                           float4 *srcf, Pt4d *srcd, T *partsm);
-
-// Source points of consecutive near leaves are staged together until the
-// staging buffer (kMaxLeaf points) is full, so a CTA synchronises about
-// (sum of near-leaf sizes) / kMaxLeaf times instead of once per near leaf.
-template <>
-__device__ void near_field<float>(const LeafArgs &A, int z, int zs, int m, const float *__restrict__ xs, float *outsm,
-                                  float4 *srcf, Pt4d *, float *partsm) {
-    // Coordinates are offsets from the leaf centre split into hi + lo floats.
-    // A source point is moved into the target leaf's frame by the exact box
-    // offset shift = (c_Y - c_Z); Fast2Sum keeps the rounding error of hi +
-    // shift (|shift| >= |hi|), so differences keep full FP32 relative accuracy
-    // even for very close pairs.
-    const int T_ = kLeafThreads;
-    const int S = m <= T_ ? max(1, T_ / m) : 1;
-    const int ntg = m <= T_ ? 1 : (m + T_ - 1) / T_;   // targets per thread when m > T
-    const int s = m <= T_ ? threadIdx.x / m : 0;
-    const int i0 = m <= T_ ? threadIdx.x - s * m : threadIdx.x;
-    const bool active = m <= T_ ? (s < S) : true;
-    Acc<float> acc[4];
-    float4 th[4], tl[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int i = i0 + q * T_;
-        const bool ok = active && q < ntg && i < m;
-        th[q] = ok ? A.ploc[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        tl[q] = ok ? A.ploc_lo[zs + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const float kap = (float)A.kappa;
-    const int p1 = A.near_ptr[z + 1];
-    int p = A.near_ptr[z];
-    while (p < p1) {
-        // stage near leaves [p, pe) together
-        int pe = p, cnt = 0;
-        while (pe < p1) {
-            const int y = A.near_src[pe];
-            const int n = A.box_end[A.offL + y] - A.box_start[A.offL + y];
-            if (cnt + n > kMaxLeaf && cnt > 0) break;
-            cnt += n;
-            ++pe;
-        }
-        __syncthreads();
-        int base = 0;
-        for (int q = p; q < pe; ++q) {
-            const int y = A.near_src[q];
-            const int ys = A.box_start[A.offL + y], n = A.box_end[A.offL + y] - ys;
-            const int d = A.near_dir[q];
-            const float sx = (float)((d / 9 - 1) * A.hL), sy = (float)(((d / 3) % 3 - 1) * A.hL),
-                        sz = (float)((d % 3 - 1) * A.hL);
-            for (int j = threadIdx.x; j < n; j += T_) {
-                const float4 h = A.ploc[ys + j], l = A.ploc_lo[ys + j];
-                const float hx = h.x + sx, hy = h.y + sy, hz = h.z + sz;
-                const float ex = h.x - (hx - sx), ey = h.y - (hy - sy), ez = h.z - (hz - sz);
-                srcf[2 * (base + j)] = make_float4(hx, hy, hz, xs[ys + j]);
-                srcf[2 * (base + j) + 1] = make_float4(ex + l.x, ey + l.y, ez + l.z, 0.f);
-            }
-            base += n;
-        }
-        __syncthreads();
-        if (active) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = i0 + q * T_;
-                if (q >= ntg || i >= m) break;
-                auto term = [&](int j) {
-                    const float4 sh = srcf[2 * j], sl = srcf[2 * j + 1];
-                    const float dx = (th[q].x - sh.x) + (tl[q].x - sl.x);
-                    const float dy = (th[q].y - sh.y) + (tl[q].y - sl.y);
-                    const float dz = (th[q].z - sh.z) + (tl[q].z - sl.z);
-                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    return kernel_fast(A.kind, kap, d2) * sh.w;
-                };
-                int j = s;
-                // four independent interactions per compensated add (ILP)
-                for (; j + 3 * S < cnt; j += 4 * S) {
-                    const float a0 = term(j), a1 = term(j + S), a2 = term(j + 2 * S), a3 = term(j + 3 * S);
-                    acc[q].add((a0 + a1) + (a2 + a3));
-                }
-                for (; j < cnt; j += S) acc[q].add(term(j));
-            }
-        }
-        p = pe;
-    }
-    // reduce over source groups
-    __syncthreads();
-    if (m <= T_) {
-        if (active) partsm[threadIdx.x] = acc[0].get();
-        __syncthreads();
-        for (int i = threadIdx.x; i < m; i += T_) {
-            float v = 0.f;
-            for (int g = 0; g < S; ++g) v += partsm[g * m + i];
-            outsm[i] = v;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + q * T_;
-            if (q < ntg && i < m) outsm[i] = acc[q].get();
-        }
-    }
-    __syncthreads();
-}
-
-template <>
-__device__ void near_field<double>(const LeafArgs &A, int z, int zs, int m, const double *__restrict__ xs,
-                                   double *outsm, float4 *, Pt4d *srcd, double *partsm) {
-    const int T_ = kLeafThreads;
-    const int S = m <= T_ ? max(1, T_ / m) : 1;
-    const int ntg = m <= T_ ? 1 : (m + T_ - 1) / T_;
-    const int s = m <= T_ ? threadIdx.x / m : 0;
-    const int i0 = m <= T_ ? threadIdx.x - s * m : threadIdx.x;
-    const bool active = m <= T_ ? (s < S) : true;
-    double acc[4] = {0, 0, 0, 0};
-    double tx[4], ty[4], tz[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int i = i0 + q * T_;
-        const bool ok = active && q < ntg && i < m;
-        tx[q] = ok ? A.px[zs + i] : 0.0;
-        ty[q] = ok ? A.py[zs + i] : 0.0;
-        tz[q] = ok ? A.pz[zs + i] : 0.0;
-    }
-    const int p1 = A.near_ptr[z + 1];
-    int p = A.near_ptr[z];
-    while (p < p1) {
-        int pe = p, cnt = 0;
-        while (pe < p1) {
-            const int y = A.near_src[pe];
-            const int n = A.box_end[A.offL + y] - A.box_start[A.offL + y];
-            if (cnt + n > kMaxLeaf && cnt > 0) break;
-            cnt += n;
-            ++pe;
-        }
-        __syncthreads();
-        int base = 0;
-        for (int q = p; q < pe; ++q) {
-            const int y = A.near_src[q];
-            const int ys = A.box_start[A.offL + y], n = A.box_end[A.offL + y] - ys;
-            for (int j = threadIdx.x; j < n; j += T_)
-                srcd[base + j] = make_pt4d(A.px[ys + j], A.py[ys + j], A.pz[ys + j], xs[ys + j]);
-            base += n;
-        }
-        __syncthreads();
-        if (active) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i = i0 + q * T_;
-                if (q >= ntg || i >= m) break;
-                double a = 0.0;
-                for (int j = s; j < cnt; j += S) {
-                    const Pt4d sp = srcd[j];
-                    const double dx = tx[q] - sp.x, dy = ty[q] - sp.y, dz = tz[q] - sp.z;
-                    const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                    a = fma(kernel_fast(A.kind, A.kappa, d2), sp.w, a);
-                }
-                acc[q] += a;
-            }
-        }
-        p = pe;
-    }
-    __syncthreads();
-    if (m <= T_) {
-        if (active) partsm[threadIdx.x] = acc[0];
-        __syncthreads();
-        for (int i = threadIdx.x; i < m; i += T_) {
-            double v = 0.0;
-            for (int g = 0; g < S; ++g) v += partsm[g * m + i];
-            outsm[i] = v;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + q * T_;
-            if (q < ntg && i < m) outsm[i] = acc[q];
-        }
-    }
-    __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// A6 + A8 + A9: one CTA per leaf.
-//
-// Far field: for every level the leaf reads one contiguous U panel (ld x R_A,
-// column-major).  The panels of all levels are cut into chunks of whole
-// columns (<= kChunkBytes) and streamed through a ring of kStages shared-memory
-// buffers by bulk asynchronous copies (TMA) that complete on one mbarrier per
-// buffer; one elected thread issues the copies kStages-1 chunks ahead.  Threads
-// own W consecutive rows of a column group and accumulate U(rows, c) t_A(c)
-// from shared memory.  Then the near field and y = far + near in caller order.
-constexpr int kStages = 4;
-constexpr int kChunkBytes = 8192;
-constexpr size_t kLeafDynSmem = (size_t)kStages * kChunkBytes;
-
-struct ChunkPlan {
-    const void *panel[kMaxDepth + 1];
-    const void *tA[kMaxDepth + 1];
-    int R[kMaxDepth + 1];
-    int first[kMaxDepth + 2];   // first chunk of level l (l = 1..L), first[L+1] = total
-};
-
-template <class T>
-__device__ __forceinline__ void chunk_of(const ChunkPlan &P, int L, int k, int cpc, int &l, int &c0, int &nc) {
-    while (l < L && k >= P.first[l + 1]) ++l;
-    c0 = (k - P.first[l]) * cpc;
-    nc = min(cpc, P.R[l] - c0);
-}
-
+// A8 + A9: one CTA per leaf
 template <class T>
 __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs A, const T *__restrict__ U, const T *__restrict__ t,
                                                        const T *__restrict__ nearbuf, T *__restrict__ y) {
-    constexpr int W = Vec<T>::W;
     extern __shared__ __align__(128) unsigned char stage[];   // kStages * kChunkBytes
     __shared__ __align__(8) uint64_t bars[kStages];
     __shared__ ChunkPlan P;
-    __shared__ T red[kLeafThreads * W];
-    const int z = blockIdx.x;
-    const int Zg = (int)(A.offL + z);
-    const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
-    const int ld = A.leaf_ld[z];
-    const int nr = ld / W;
-    const int cpc = kChunkBytes / (ld * (int)sizeof(T));   // columns per chunk (ld <= 512)
-    const int L = A.L;
-
-    // per-level panels, one thread per level, then the chunk prefix
-    if (threadIdx.x >= 1 && threadIdx.x <= L) {
-        const int l = threadIdx.x;
-        const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
-        const int RA = A.R[Ag];
-        P.panel[l] = U + A.ubase[Ag] + (A.leaf_lp[z] - A.leaf_lp[A.leaf_lo[Ag]]) * RA;
-        P.tA[l] = t + A.tbase[Ag];
-        P.R[l] = RA;
-    }
+    __shared__ T red[kLeafThreads * Vec<T>::W];
     if (threadIdx.x == 0) {
         for (int q = 0; q < kStages; ++q) mbar_init(&bars[q], 1);
         mbar_fence_init();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int l = 1; l <= L; ++l) {
-            P.first[l] = acc;
-            acc += (P.R[l] + cpc - 1) / cpc;
-        }
-        P.first[L + 1] = acc;
-    }
-    __syncthreads();
-    const int nchunks = P.first[L + 1];
-
-    // one elected thread keeps the ring full
-    int pl = 1;
-    auto issue = [&](int k) {
-        int c0, nc;
-        chunk_of<T>(P, L, k, cpc, pl, c0, nc);
-        const uint32_t bytes = (uint32_t)(nc * ld * (int)sizeof(T));
-        uint64_t *bar = &bars[k % kStages];
-        mbar_arrive_expect_tx(bar, bytes);
-        bulk_copy_g2s(stage + (size_t)(k % kStages) * kChunkBytes,
-                      static_cast<const T *>(P.panel[pl]) + (int64_t)c0 * ld, bytes, bar);
-    };
-    if (threadIdx.x == 0)
-        for (int k = 0; k < min(kStages - 1, nchunks); ++k) issue(k);
-
-    const int Gc = nr <= kLeafThreads ? kLeafThreads / nr : 1;
-    const int g = nr <= kLeafThreads ? threadIdx.x / nr : 0;
-    const int rv0 = nr <= kLeafThreads ? threadIdx.x - g * nr : threadIdx.x;
-    Acc<T> acc[2][W];
-    int cl_level = 1;
-    for (int k = 0; k < nchunks; ++k) {
-        const bool ok = mbar_wait(&bars[k % kStages], (uint32_t)((k / kStages) & 1));
-        // every thread has finished chunk k-1 here, so its buffer may be refilled
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) {
-                *A.err = H3D_ERR_TIMEOUT;
-                for (int j = k; j < min(k + kStages - 1, nchunks); ++j)   // copies still in flight
-                    mbar_wait(&bars[j % kStages], (uint32_t)((j / kStages) & 1));
-            }
-            return;
-        }
-        if (threadIdx.x == 0 && k + kStages - 1 < nchunks) issue(k + kStages - 1);
-        int c0, nc;
-        chunk_of<T>(P, L, k, cpc, cl_level, c0, nc);
-        const T *sm = reinterpret_cast<const T *>(stage + (size_t)(k % kStages) * kChunkBytes);
-        const T *tA = static_cast<const T *>(P.tA[cl_level]) + c0;
-        if (g < Gc) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int rv = rv0 + h * kLeafThreads;
-                if (rv >= nr) break;
-                const T *p = sm + rv * W;
-                int c = g;
-                for (; c + 3 * Gc < nc; c += 4 * Gc) {
-                    typename Vec<T>::type v0 = *reinterpret_cast<const typename Vec<T>::type *>(p + c * ld),
-                                          v1 = *reinterpret_cast<const typename Vec<T>::type *>(p + (c + Gc) * ld),
-                                          v2 = *reinterpret_cast<const typename Vec<T>::type *>(p + (c + 2 * Gc) * ld),
-                                          v3 = *reinterpret_cast<const typename Vec<T>::type *>(p + (c + 3 * Gc) * ld);
-                    const T t0 = __ldg(tA + c), t1 = __ldg(tA + c + Gc), t2 = __ldg(tA + c + 2 * Gc),
-                            t3 = __ldg(tA + c + 3 * Gc);
-                    T a0[W], a1[W], a2[W], a3[W];
-                    Vec<T>::get(v0, a0); Vec<T>::get(v1, a1); Vec<T>::get(v2, a2); Vec<T>::get(v3, a3);
-#pragma unroll
-                    for (int e = 0; e < W; ++e) acc[h][e].add(a0[e] * t0 + a1[e] * t1 + a2[e] * t2 + a3[e] * t3);
-                }
-                for (; c < nc; c += Gc) {
-                    T a[W];
-                    Vec<T>::get(*reinterpret_cast<const typename Vec<T>::type *>(p + c * ld), a);
-                    const T tc = __ldg(tA + c);
-#pragma unroll
-                    for (int e = 0; e < W; ++e) acc[h][e].add(a[e] * tc);
-                }
-            }
-        }
-    }
-    // reduce over column groups, add the near field, write in the caller's order
-    if (Gc > 1) {
-        if (g < Gc)
-#pragma unroll
-            for (int e = 0; e < W; ++e) red[g * ld + rv0 * W + e] = acc[0][e].get();
-        __syncthreads();
-        for (int i = threadIdx.x; i < m; i += kLeafThreads) {
-            T v = 0;
-            for (int q = 0; q < Gc; ++q) v += red[q * ld + i];
-            y[A.perm[zs + i]] = v + nearbuf[zs + i];
-        }
-    } else {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int rv = rv0 + h * kLeafThreads;
-            if (rv < nr)
-#pragma unroll
-                for (int e = 0; e < W; ++e) {
-                    const int i = rv * W + e;
-                    if (i < m) y[A.perm[zs + i]] = acc[h][e].get() + nearbuf[zs + i];
-                }
-        }
-    }
+    uint32_t ring = 0;
+    leaf_task<T, false>(A, blockIdx.x, U, t, nearbuf, y, stage, bars, P, red, ring);
 }
 
 // A6: dense self / face / edge near field into nearbuf (Morton order).  A
@@ -569,11 +84,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_near(LeafArgs A, const T *__re
     __shared__ T partsm[kLeafThreads];
     __shared__ __align__(16) unsigned char srcbuf[kMaxLeaf * 32];
     for (int z = blockIdx.x; z < A.nleaf; z += gridDim.x) {
-        const int Zg = (int)(A.offL + z);
-        const int zs = A.box_start[Zg], m = A.box_end[Zg] - zs;
-        near_field<T>(A, z, zs, m, xs, outsm, reinterpret_cast<float4 *>(srcbuf), reinterpret_cast<Pt4d *>(srcbuf),
-                      partsm);
-        for (int i = threadIdx.x; i < m; i += kLeafThreads) nearbuf[zs + i] = outsm[i];
+        near_task<T>(A, z, xs, nearbuf, outsm, partsm, srcbuf);
         __syncthreads();
     }
 }
@@ -1664,21 +1175,6 @@ __global__ void __launch_bounds__(kTsThreads, 1) k_tc_stream(TsArgs P) {
 }
 
 unsigned gridn(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
-
-LeafArgs leaf_args(const Handle &h) {
-    LeafArgs A{};
-    A.L = h.L; A.nleaf = h.nleaf; A.kind = h.kernel; A.kappa = h.kappa;
-    A.hL = h.side / (double)(1 << h.L);
-    A.offL = h.box_off[h.L];
-    A.box_start = h.box_start; A.box_end = h.box_end; A.perm = h.perm; A.leaf_ld = h.leaf_ld;
-    A.leaf_anc = h.leaf_anc; A.R = h.R; A.leaf_lo = h.box_leaf_lo;
-    A.leaf_lp = h.leaf_lp; A.ubase = h.ubase; A.tbase = h.tbase;
-    A.near_ptr = h.near_ptr; A.near_src = h.near_src; A.near_dir = h.near_dir;
-    A.ploc = h.ploc; A.ploc_lo = h.ploc_lo; A.px = h.px; A.py = h.py; A.pz = h.pz;
-    A.Rv = h.Rv; A.ldv = h.ldv; A.vbase = h.vbase; A.vcol0 = h.vcol0; A.map_v = h.map_v; A.tp_base = h.tp_base;
-    A.err = h.d_async_err;
-    return A;
-}
 
 // transpose reduce work list (host-built)
 struct TPlan {
