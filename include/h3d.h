@@ -193,13 +193,18 @@ h3d_status h3d_forces(h3d_handle h, const void *q, double *E, double *F, void *s
  * h3d_batch_tune times (three runs after a warm-up, CUDA events on `stream`)
  * the graph form with 1, 2, 4, ... branches (up to 32 and the number of
  * handles) and, when available, the persistent form for leaves per item
- * (near, leaf) in {(4,1), (4,2), (8,4)} and the most resident CTAs per SM or
- * one or two fewer; it keeps the fastest and reports in *branches_out (may be NULL) the
- * branch count, or 0 for the persistent form.  It synchronises `stream`.
- * h3d_batch_set_mode selects the form (persistent != 0: the persistent kernel;
- * H3D_ERR_ARG if it is not available) and, for the persistent form, the CTAs
- * per SM of its grid (0 keeps the current value; capped at the occupancy
- * limit).  h3d_batch_info reports the form in use
+ * (near, leaf) in {(4,1), (4,2), (8,4)}, queue orders phase-major or pipelined
+ * over operators (lag 2 or 8), and the most resident CTAs per SM or one fewer
+ * (default: (4,2), lag 0, the most); it keeps the fastest and reports in
+ * *branches_out (may be NULL) the branch count, or 0 for the persistent form.
+ * It synchronises `stream`.
+ * h3d_batch_configure selects the form (persistent != 0: the persistent kernel;
+ * H3D_ERR_ARG if it is not available) and the persistent form's settings: CTAs
+ * per SM of its grid (capped at the occupancy limit), leaves per near-field
+ * item and per leaf item, and the queue order (lag 0: phase-major; d > 0:
+ * pipelined over operators); 0 (-1 for lag) keeps the current value.  The
+ * settings change who computes an item and when, never how: the persistent
+ * form's results are the same bits for every setting.  h3d_batch_info reports the form in use
  * (*persistent: 1 persistent, 0 graph, -1 graph and persistent unavailable),
  * the CTAs per SM of the persistent form and the branch count of the graph
  * form; any pointer may be NULL.                                              */
@@ -207,7 +212,8 @@ typedef struct h3d_batch_s *h3d_batch;
 h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out);
 h3d_status h3d_batch_matvec(h3d_batch b, const void *const *x, void *const *y, void *stream);
 h3d_status h3d_batch_tune(h3d_batch b, const void *const *x, void *const *y, void *stream, int *branches_out);
-h3d_status h3d_batch_set_mode(h3d_batch b, int persistent, int ctas_per_sm);
+h3d_status h3d_batch_configure(h3d_batch b, int persistent, int ctas_per_sm, int near_group, int leaf_group,
+                               int lag);
 h3d_status h3d_batch_info(h3d_batch b, int *persistent, int *ctas_per_sm, int *branches);
 h3d_status h3d_batch_free(h3d_batch b);
 

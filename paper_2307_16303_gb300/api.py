@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_
 EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3d_matvec_host", "h3d_free",
            "h3d_status_string", "h3d_get_stats", "h3d_matvec_profile", "h3d_export_tree", "h3d_export_lists",
            "h3d_export_pivots", "h3d_morton_order_noalloc", "h3d_energy", "h3d_forces",
-           "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_set_mode", "h3d_batch_info",
+           "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_configure", "h3d_batch_info",
            "h3d_batch_free")
 
 
@@ -85,7 +85,7 @@ def lib():
             "h3d_batch_create": (i32, [P, i32, C.POINTER(P)]),
             "h3d_batch_matvec": (i32, [P, P, P, P]),
             "h3d_batch_tune": (i32, [P, P, P, P, C.POINTER(i32)]),
-            "h3d_batch_set_mode": (i32, [P, i32, i32]),
+            "h3d_batch_configure": (i32, [P, i32, i32, i32, i32, i32]),
             "h3d_batch_info": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
             "h3d_batch_free": (i32, [P]),
         }
@@ -329,12 +329,15 @@ class H3DBatch:
             raise H3DError(st, "h3d_batch_tune")
         return nb.value
 
-    def set_mode(self, persistent: bool, ctas_per_sm: int = 0):
-        """Select the persistent kernel or the graph form (and the persistent
-        grid's CTAs per SM; 0 keeps the current value)."""
-        st = lib().h3d_batch_set_mode(self._b, 1 if persistent else 0, int(ctas_per_sm))
+    def set_mode(self, persistent: bool, ctas_per_sm: int = 0, near_group: int = 0, leaf_group: int = 0,
+                 lag: int = -1):
+        """Select the persistent kernel or the graph form, and the persistent
+        form's CTAs per SM, leaves per near / leaf item and queue lag (0, or -1
+        for lag: keep the current value)."""
+        st = lib().h3d_batch_configure(self._b, 1 if persistent else 0, int(ctas_per_sm), int(near_group),
+                                       int(leaf_group), int(lag))
         if st != 0:
-            raise H3DError(st, "h3d_batch_set_mode")
+            raise H3DError(st, "h3d_batch_configure")
 
     def info(self) -> dict:
         """{"persistent": 1 | 0 | -1 (unavailable), "ctas_per_sm": .., "branches": ..}"""

@@ -437,6 +437,7 @@ bool same_vectors(const h3d_batch_s &B, const void *const *x, void *const *y) {
 
 // persistent form: leaves per near-field / leaf item
 constexpr int kDefaultNearGroup = 4, kDefaultLeafGroup = 2;   // (a near item gives each of 4 warps a leaf)
+constexpr int kDefaultLag = 0;                                 // phase-major queue
 
 void batch_run(h3d_batch_s &B, const void *const *x, void *const *y, cudaStream_t s) {
     if (B.persistent) {
@@ -484,7 +485,7 @@ h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out
         H3D_CUDA(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
         std::vector<Handle *> hv;
         for (int i = 0; i < count; ++i) hv.push_back(&handles[i]->h);
-        B->plan = h3d::batch_plan_create(hv, kDefaultNearGroup, kDefaultLeafGroup);
+        B->plan = h3d::batch_plan_create(hv, kDefaultNearGroup, kDefaultLeafGroup, kDefaultLag);
         if (B->plan) {
             B->persistent = true;
             B->ctas_per_sm = h3d::batch_plan_max_ctas_per_sm(*B->plan);
@@ -530,23 +531,26 @@ h3d_status h3d_batch_tune(h3d_batch B, const void *const *x, void *const *y, voi
         if (B->plan) {
             const int cmax = h3d::batch_plan_max_ctas_per_sm(*B->plan);
             static const int groups[][2] = {{4, 1}, {4, 2}, {8, 4}};
+            int best_lag = kDefaultLag;
             B->persistent = true;
-            for (const auto &g : groups) {
-                h3d::batch_plan_regroup(*B->plan, g[0], g[1]);
-                for (int cps : {cmax - 2, cmax - 1, cmax}) {
-                    if (cps < 1) continue;
-                    B->ctas_per_sm = cps;
-                    const float ms = batch_time(*B, x, y, s, e0, e1);
-                    if (ms < best) {
-                        best = ms;
-                        use_persistent = true;
-                        best_cps = cps;
-                        best_ng = g[0];
-                        best_lg = g[1];
+            for (int lag : {0, 2, 8})
+                for (const auto &g : groups) {
+                    h3d::batch_plan_regroup(*B->plan, g[0], g[1], lag);
+                    for (int cps : {cmax - 1, cmax}) {
+                        if (cps < 1) continue;
+                        B->ctas_per_sm = cps;
+                        const float ms = batch_time(*B, x, y, s, e0, e1);
+                        if (ms < best) {
+                            best = ms;
+                            use_persistent = true;
+                            best_cps = cps;
+                            best_ng = g[0];
+                            best_lg = g[1];
+                            best_lag = lag;
+                        }
                     }
                 }
-            }
-            h3d::batch_plan_regroup(*B->plan, best_ng, best_lg);
+            h3d::batch_plan_regroup(*B->plan, best_ng, best_lg, best_lag);
             B->ctas_per_sm = use_persistent ? best_cps : cmax;
         }
         cudaEventDestroy(e0);
@@ -557,12 +561,19 @@ h3d_status h3d_batch_tune(h3d_batch B, const void *const *x, void *const *y, voi
     });
 }
 
-h3d_status h3d_batch_set_mode(h3d_batch B, int persistent, int ctas_per_sm) {
-    if (!B || (persistent && !B->plan) || ctas_per_sm < 0) return H3D_ERR_ARG;
+h3d_status h3d_batch_configure(h3d_batch B, int persistent, int ctas_per_sm, int near_group, int leaf_group, int lag) {
+    if (!B || (persistent && !B->plan) || ctas_per_sm < 0 || near_group < 0 || leaf_group < 0 || lag < -1)
+        return H3D_ERR_ARG;
     B->persistent = persistent != 0;
-    if (persistent && ctas_per_sm > 0)
-        return guard([&] { B->ctas_per_sm = std::min(ctas_per_sm, h3d::batch_plan_max_ctas_per_sm(*B->plan)); });
-    return H3D_OK;
+    if (!B->plan) return H3D_OK;
+    return guard([&] {
+        if (ctas_per_sm > 0) B->ctas_per_sm = std::min(ctas_per_sm, h3d::batch_plan_max_ctas_per_sm(*B->plan));
+        int ng = 0, lg = 0, lo = 0;
+        h3d::batch_plan_groups(*B->plan, &ng, &lg, &lo);
+        const int ng2 = near_group > 0 ? near_group : ng, lg2 = leaf_group > 0 ? leaf_group : lg,
+                  lo2 = lag >= 0 ? lag : lo;
+        if (ng2 != ng || lg2 != lg || lo2 != lo) h3d::batch_plan_regroup(*B->plan, ng2, lg2, lo2);
+    });
 }
 
 h3d_status h3d_batch_info(h3d_batch B, int *persistent, int *ctas_per_sm, int *branches) {

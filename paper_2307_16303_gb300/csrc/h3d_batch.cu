@@ -3,7 +3,8 @@
 // persistent launch (Alg. 2 for every operator at once), captured with the
 // reset of its queue into a CUDA graph.
 //
-// The work items of all operators sit in one device queue, phase-major:
+// The work items of all operators sit in one device queue (P first, then the
+// rest phase-major or pipelined over operators; see build_items):
 //   P  permute a chunk of points: xs = x[perm]                         (A5)
 //   G  one gather task: t_b = V_b^T xs(Y_b) over a row range           (A7)
 //   N  near field of a run of leaves (one leaf per warp) into the near
@@ -19,8 +20,8 @@
 // (fetched while the current item runs).  An item whose inputs are incomplete
 // waits on its operator's completion counters: G and N wait for every P of the
 // operator, R for every G, L for every G, R and N.  Items wait only on items
-// of earlier phases, which sit earlier in the queue and so were taken by CTAs
-// that are already running; every wait therefore ends.  Each is still bounded
+// that sit earlier in the queue and so were taken by CTAs that are already
+// running; every wait therefore ends.  Each is still bounded
 // (kWaitCycles): a CTA that gives up records H3D_ERR_TIMEOUT in the operator's
 // error word, raises the batch's abort flag (on which the other CTAs stop) and
 // leaves.
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchCtasPerSm) k_batch(BatchA
 struct BatchPlan {
     int elem = 4;                            // 4: FP32 operators, 8: FP64
     int nops = 0;
-    int near_group = 0, leaf_group = 0;
+    int near_group = 0, leaf_group = 0, lag = 0;
     std::vector<BatchOp> ops;
     std::vector<Handle *> hs;
     Arena mem;
@@ -236,34 +237,67 @@ void *upload(BatchPlan &p, void *old, const std::vector<V> &v) {
     return d;
 }
 
-// The queue in phase order (P of every operator, then G and N, then R, then
-// L); within an operator its near runs are spread evenly among its gather
-// tasks.
+// Merge two item lists, keeping each list's order and spreading b evenly
+// among a.
+void merge_even(std::vector<int4> &out, const std::vector<int4> &a, const std::vector<int4> &b) {
+    size_t ia = 0, ib = 0;
+    while (ia < a.size() || ib < b.size()) {
+        if (ib < b.size() && (ia >= a.size() || (int64_t)ib * (int64_t)a.size() <= (int64_t)ia * (int64_t)b.size()))
+            out.push_back(b[ib++]);
+        else
+            out.push_back(a[ia++]);
+    }
+}
+
+// The queue: P of every operator first.  Then, with lag 0, phase-major: the G
+// and N items of every operator (an operator's near runs spread evenly among
+// its gather tasks), then every R, then every L.  With lag d > 0, pipelined
+// over operators: round k holds the G and N items of operator k merged with
+// the R and L items of operator k - d, so that operators finish one after
+// another instead of all at the end.  Either way every item comes after the
+// items it waits for.
 void build_items(BatchPlan &p) {
     std::vector<int4> items;
     for (int o = 0; o < p.nops; ++o)
         for (int64_t i = 0; i < p.hs[o]->N; i += kPermChunk) items.push_back(make_int4(o, kItemPerm, (int)i, 0));
-    for (int o = 0; o < p.nops; ++o) {
+    auto stream_items = [&](int o) {   // G and N of operator o
         const Handle &h = *p.hs[o];
-        const int ng = h.ngtask, nn = p.ops[o].nnear;
-        int gi = 0, ni = 0;
-        while (gi < ng || ni < nn) {
-            if (ni < nn && (gi >= ng || (int64_t)ni * ng <= (int64_t)gi * nn)) {   // keep ni / nn near gi / ng
-                const int z0 = ni * p.near_group;
-                items.push_back(make_int4(o, kItemNear, z0, std::min(p.near_group, h.nleaf - z0)));
-                ++ni;
-            } else {
-                items.push_back(make_int4(o, kItemGather, gi, 1));
-                ++gi;
-            }
+        std::vector<int4> g, n, out;
+        for (int k = 0; k < h.ngtask; ++k) g.push_back(make_int4(o, kItemGather, k, 1));
+        for (int z0 = 0; z0 < h.nleaf; z0 += p.near_group)
+            n.push_back(make_int4(o, kItemNear, z0, std::min(p.near_group, h.nleaf - z0)));
+        merge_even(out, g, n);
+        return out;
+    };
+    auto finish_items = [&](int o, bool reduce, bool leaf) {   // R and / or L of operator o
+        const Handle &h = *p.hs[o];
+        std::vector<int4> out;
+        if (reduce)
+            for (int q = 0; q < h.nsplit; ++q) out.push_back(make_int4(o, kItemReduce, q, 1));
+        if (leaf)
+            for (int z0 = 0; z0 < h.nleaf; z0 += p.leaf_group)
+                out.push_back(make_int4(o, kItemLeaf, z0, std::min(p.leaf_group, h.nleaf - z0)));
+        return out;
+    };
+    if (p.lag <= 0) {
+        for (int o = 0; o < p.nops; ++o) {
+            const std::vector<int4> v = stream_items(o);
+            items.insert(items.end(), v.begin(), v.end());
         }
-    }
-    for (int o = 0; o < p.nops; ++o)
-        for (int q = 0; q < p.hs[o]->nsplit; ++q) items.push_back(make_int4(o, kItemReduce, q, 1));
-    for (int o = 0; o < p.nops; ++o) {
-        const Handle &h = *p.hs[o];
-        for (int z0 = 0; z0 < h.nleaf; z0 += p.leaf_group)
-            items.push_back(make_int4(o, kItemLeaf, z0, std::min(p.leaf_group, h.nleaf - z0)));
+        for (int o = 0; o < p.nops; ++o) {
+            const std::vector<int4> v = finish_items(o, true, false);
+            items.insert(items.end(), v.begin(), v.end());
+        }
+        for (int o = 0; o < p.nops; ++o) {
+            const std::vector<int4> v = finish_items(o, false, true);
+            items.insert(items.end(), v.begin(), v.end());
+        }
+    } else {
+        for (int k = 0; k < p.nops + p.lag; ++k) {
+            const std::vector<int4> a = k < p.nops ? stream_items(k) : std::vector<int4>();
+            const std::vector<int4> b = k >= p.lag ? finish_items(k - p.lag, true, true) : std::vector<int4>();
+            merge_even(items, a, b);
+        }
     }
     p.nitems = (int)items.size();
     p.d_items = upload(p, p.d_items, items);
@@ -275,7 +309,7 @@ void build_items(BatchPlan &p) {
 
 }  // namespace
 
-BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, int leaf_group) {
+BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, int leaf_group, int lag) {
     if (hs.empty()) return nullptr;
     const int elem = hs[0]->prec == H3D_FP64 ? 8 : 4;
     for (Handle *h : hs)
@@ -304,7 +338,7 @@ BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, in
             op.nsplit = h.nsplit;
             p->ops.push_back(op);
         }
-        batch_plan_regroup(*p, near_group, leaf_group);
+        batch_plan_regroup(*p, near_group, leaf_group, lag);
         p->d_state = p->mem.get<int>((size_t)(p->nops + 1) * 4);
         p->d_xy = p->mem.alloc((size_t)p->nops * 2 * sizeof(void *));
         H3D_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
@@ -315,12 +349,19 @@ BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, in
     return p;
 }
 
-void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group) {
+void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group, int lag) {
     p.near_group = std::max(1, near_group);
     p.leaf_group = std::max(1, leaf_group);
+    p.lag = std::max(0, lag);
     for (int o = 0; o < p.nops; ++o) p.ops[o].nnear = (p.hs[o]->nleaf + p.near_group - 1) / p.near_group;
     p.d_ops = upload(p, p.d_ops, p.ops);
     build_items(p);
+}
+
+void batch_plan_groups(const BatchPlan &p, int *near_group, int *leaf_group, int *lag) {
+    *near_group = p.near_group;
+    *leaf_group = p.leaf_group;
+    *lag = p.lag;
 }
 
 int batch_plan_max_ctas_per_sm(const BatchPlan &p) {

@@ -347,10 +347,13 @@ void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cud
 // One persistent launch for the single-column products of many operators
 // (h3d_batch.cu).  batch_plan_create returns nullptr when the handles cannot
 // share one launch (skeleton storage, or FP32 and FP64 handles mixed).  The
-// group sizes are the leaves per near-field item and per leaf item.
+// group sizes are the leaves per near-field item and per leaf item; lag 0
+// orders the queue phase-major, lag d > 0 pipelines it over operators with a
+// delay of d operators between an operator's streams and its leaves.
 struct BatchPlan;
-BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, int leaf_group);
-void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group);
+BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, int leaf_group, int lag);
+void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group, int lag);
+void batch_plan_groups(const BatchPlan &p, int *near_group, int *leaf_group, int *lag);
 int batch_plan_max_ctas_per_sm(const BatchPlan &p);
 void batch_plan_run(BatchPlan &p, const void *const *x, void *const *y, int ctas_per_sm, cudaStream_t s);
 void batch_plan_free(BatchPlan *p);

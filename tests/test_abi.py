@@ -65,6 +65,6 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu():
     out = C.c_void_p()
     assert L.h3d_batch_create(None, 0, C.byref(out)) == 1
     assert L.h3d_batch_matvec(None, None, None, None) == 1
-    assert L.h3d_batch_set_mode(None, 1, 0) == 1
+    assert L.h3d_batch_configure(None, 1, 0, 0, 0, -1) == 1
     assert L.h3d_batch_info(None, None, None, None) == 1
     assert L.h3d_batch_free(None) == 0                                  # freeing nothing is fine

@@ -122,9 +122,10 @@ def test_persistent_form_same_bits_for_every_cta_count():
     B.set_mode(True, 1)
     assert B.info()["ctas_per_sm"] == 1
     first = run(B, xs, ys)
-    # a CTA count changes only which CTA runs an item, never how it is computed
-    for cps in (2, 3, 64):
-        B.set_mode(True, cps)
+    # a CTA count, item size or queue order changes only which CTA runs an item
+    # and when, never how it is computed
+    for cps, ng, lg, lag in ((2, 0, 0, -1), (3, 8, 1, 0), (64, 4, 4, 1), (5, 1, 3, 8), (7, 4, 2, 2)):
+        B.set_mode(True, cps, ng, lg, lag)
         for y, f in zip(run(B, xs, ys), first):
             assert torch.equal(y, f)
     assert 2 <= B.info()["ctas_per_sm"] < 64          # capped at the occupancy limit
