@@ -25,12 +25,44 @@ namespace {
 constexpr int kFThreads = 128;
 constexpr int kFWarps = kFThreads / 32;
 
-// 1/sqrt(d2) to FP64 accuracy: an FP32 seed and two Newton steps (avoids the
-// FP64 square root and division)
+// 1/sqrt(d2) to FP64 accuracy without the FP64 square root or division: an
+// FP32 seed y0 = y (1 + delta), |delta| < 2^-21, then one third-order step of
+// the binomial series y = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3 e^2/8 + ...) with
+// e = 1 - d2 y0^2 (y0^2 is exact in FP64: y0 has 24 significant bits); the
+// neglected terms are below 5/16 |e|^3 < 2^-60.  Five FP64 operations.
 __device__ __forceinline__ double rsqrt64(double d2) {
-    double y = (double)rsqrtf((float)d2);
-    y = y * (1.5 - 0.5 * d2 * y * y);
-    return y * (1.5 - 0.5 * d2 * y * y);
+    const double y0 = (double)rsqrtf((float)d2);
+    const double e = fma(-d2, y0 * y0, 1.0);
+    return fma(y0 * e, fma(0.375, e, 0.5), y0);
+}
+
+// K(rho) and f'(rho) / rho from rho^2 (both 0 at rho = 0): the gradient of
+// K(|a - b|) with respect to a is fr (a - b).
+__device__ __forceinline__ double kval_fr(int kind, double kappa, double d2, double &fr) {
+    if (d2 == 0.0) {
+        fr = 0.0;
+        return 0.0;
+    }
+    const double ir = rsqrt64(d2), ir2 = ir * ir;
+    double f;
+    switch (kind) {
+    case H3D_LAPLACE: f = H3D_INV4PI * ir; fr = -f * ir2; break;
+    case H3D_YUKAWA: {
+        const double r = d2 * ir;
+        f = H3D_INV4PI * exp(-kappa * r) * ir;
+        fr = -f * (1.0 + kappa * r) * ir2;
+        break;
+    }
+    case H3D_INV_R4: f = ir2 * ir2; fr = -4.0 * f * ir2; break;
+    default: {
+        const double r = d2 * ir;
+        double sn, cs;
+        sincos(r, &sn, &cs);
+        f = cs * ir;
+        fr = -(r * sn + cs) * ir2 * ir;
+    }
+    }
+    return f;
 }
 
 // K(a, b) and dK/da = (f'(rho) / rho) (a - b) for a - b = (dx, dy, dz)
@@ -121,6 +153,7 @@ struct ForceArgs {
     double *Mscr;              // mr^2 per CTA
     int mr;                    // largest rank of the handle
     double *Epart;             // per leaf (near), then per block (far)
+    int *next;                 // far-field work queue head (zero before the launch)
 };
 
 // p_i - p_j in the evaluation type: FP64 directly; FP32 from the hi + lo split
@@ -224,18 +257,24 @@ __device__ __forceinline__ void gadd(double *G, int p, double s, double gx, doub
     atomicAdd(G + 3 * (int64_t)p + 2, s * gz);
 }
 
-// far field: one block at a time per CTA (grid-stride), M in this CTA's scratch,
-// everything in FP64
+// far field: one block at a time per CTA (taken from a queue), M in this CTA's
+// scratch, everything in FP64
 __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
     using T = double;
     __shared__ int sp[kMaxRank], tp[kMaxRank], piv[kMaxRank];
     __shared__ double c[kMaxRank], a[kMaxRank], u0[kMaxRank];
     __shared__ double gs[kMaxRank][3], gt[kMaxRank][3];   // sum_j q_j dK(sigma_k, p_j), sum_i q_i dK(p_i, tau_k)
     __shared__ double red[kFWarps];
-    __shared__ int pmax;
+    __shared__ int pmax, sblk[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     double *M = A.Mscr + (size_t)blockIdx.x * A.mr * A.mr;
-    for (int64_t b = blockIdx.x; b < A.nblk; b += gridDim.x) {
+    for (int it = 0;; ++it) {
+        // blocks in list order (largest first) from a queue: a CTA takes the next
+        // block when it is done, so uneven blocks balance over the CTAs
+        if (tid == 0) sblk[it & 1] = atomicAdd(A.next, 1);
+        __syncthreads();
+        const int64_t b = sblk[it & 1];
+        if (b >= A.nblk) break;
         const int r = A.rank[b];
         if (r == 0) {
             if (tid == 0) A.Epart[A.nleaf + b] = 0.0;
@@ -256,23 +295,33 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
         for (int k = warp; k < r; k += kFWarps) {
             const int ps = sp[k], pt = tp[k];
             double sv = 0.0, uv = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0;
-            for (int j = y0 + lane; j < y0 + n; j += 32) {
-                double dx, dy, dz, hx, hy, hz;
-                pdiff(A, ps, j, dx, dy, dz);
-                const double f = kval_grad(A.kind, A.kappa, dx, dy, dz, hx, hy, hz), qj = A.qs[j];
-                sv += f * qj;
-                s0 += qj * hx;
-                s1 += qj * hy;
-                s2 += qj * hz;
-            }
-            for (int i = x0 + lane; i < x0 + m; i += 32) {
-                double dx, dy, dz, hx, hy, hz;
-                pdiff(A, i, pt, dx, dy, dz);
-                const double f = kval_grad(A.kind, A.kappa, dx, dy, dz, hx, hy, hz), qi = A.qs[i];
-                uv += qi * f;
-                t0 += qi * hx;
-                t1 += qi * hy;
-                t2 += qi * hz;
+            // the row of sigma_k and the column of tau_k side by side: two independent
+            // evaluation chains per lane (the FP64 pipe's latency is long)
+            for (int o = lane; o < max(m, n); o += 32) {
+                if (o < n) {
+                    const int j = y0 + o;
+                    double dx, dy, dz, fr;
+                    pdiff(A, ps, j, dx, dy, dz);
+                    const double qj = A.qs[j];
+                    const double f = kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                    const double w = qj * fr;
+                    sv = fma(f, qj, sv);
+                    s0 = fma(w, dx, s0);
+                    s1 = fma(w, dy, s1);
+                    s2 = fma(w, dz, s2);
+                }
+                if (o < m) {
+                    const int i = x0 + o;
+                    double dx, dy, dz, fr;
+                    pdiff(A, i, pt, dx, dy, dz);
+                    const double qi = A.qs[i];
+                    const double f = kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                    const double w = qi * fr;
+                    uv = fma(qi, f, uv);
+                    t0 = fma(w, dx, t0);
+                    t1 = fma(w, dy, t1);
+                    t2 = fma(w, dz, t2);
+                }
             }
             sv = warp_sum(sv); uv = warp_sum(uv);
             s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2);
@@ -285,12 +334,19 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
                 gt[k][0] = t0; gt[k][1] = t1; gt[k][2] = t2;
             }
         }
-        // M = K(sigma, tau), row-major r x r, FP64
-        for (int e = tid; e < r * r; e += kFThreads) {
+        // M = K(sigma, tau), row-major r x r, FP64 (two entries per thread and step)
+        for (int e = tid; e < r * r; e += 2 * kFThreads) {
+            const int e2 = e + kFThreads;
             const int k = e / r, l = e - k * r;
-            double dx, dy, dz, gx, gy, gz;
+            double dx, dy, dz, fr;
             pdiff(A, sp[k], tp[l], dx, dy, dz);
-            M[e] = kval_grad(A.kind, A.kappa, dx, dy, dz, gx, gy, gz);
+            const double v = kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+            if (e2 < r * r) {
+                const int k2 = e2 / r, l2 = e2 - k2 * r;
+                pdiff(A, sp[k2], tp[l2], dx, dy, dz);
+                M[e2] = kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+            }
+            M[e] = v;
         }
         for (int k = tid; k < r; k += kFThreads) piv[k] = k;
         __syncthreads();
@@ -370,49 +426,66 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
         __syncthreads();
         for (int k = tid; k < r; k += kFThreads) a[piv[k]] = u0[k];
         __syncthreads();
-        // first term: q_X^T dK(X,tau) c
+        // first term: q_X^T dK(X,tau) c (pivots in pairs: two independent chains)
         for (int i = x0 + tid; i < x0 + m; i += kFThreads) {
-            KSum<T> gx, gy, gz;
-            for (int k = 0; k < r; ++k) {
-                T hx, hy, hz;
-                kg<T>(A, i, tp[k], hx, hy, hz);
-                const T ck = (T)c[k];
-                gx.add(ck * hx);
-                gy.add(ck * hy);
-                gz.add(ck * hz);
+            T gx = 0, gy = 0, gz = 0, fx = 0, fy = 0, fz = 0;
+            int k = 0;
+            for (; k + 1 < r; k += 2) {
+                double dx, dy, dz, ex, ey, ez, fr, fr1;
+                pdiff(A, i, tp[k], dx, dy, dz);
+                pdiff(A, i, tp[k + 1], ex, ey, ez);
+                kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                kval_fr(A.kind, A.kappa, fma(ez, ez, fma(ey, ey, ex * ex)), fr1);
+                const T w = (T)c[k] * fr, w1 = (T)c[k + 1] * fr1;
+                gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+                fx = fma(w1, ex, fx); fy = fma(w1, ey, fy); fz = fma(w1, ez, fz);
             }
-            gadd(A.G, i, 0.5 * A.qs[i], gx.get(), gy.get(), gz.get());
+            if (k < r) {
+                double dx, dy, dz, fr;
+                pdiff(A, i, tp[k], dx, dy, dz);
+                kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                const T w = (T)c[k] * fr;
+                gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+            }
+            gadd(A.G, i, 0.5 * A.qs[i], gx + fx, gy + fy, gz + fz);
         }
         for (int k = tid; k < r; k += kFThreads) gadd(A.G, tp[k], -0.5 * c[k], gt[k][0], gt[k][1], gt[k][2]);
         // second term: a^T dK(sigma,Y) q_Y
         for (int k = tid; k < r; k += kFThreads) gadd(A.G, sp[k], 0.5 * a[k], gs[k][0], gs[k][1], gs[k][2]);
         for (int j = y0 + tid; j < y0 + n; j += kFThreads) {
-            KSum<T> gx, gy, gz;
-            for (int k = 0; k < r; ++k) {
-                T hx, hy, hz;
-                kg<T>(A, sp[k], j, hx, hy, hz);
-                const T ak = (T)a[k];
-                gx.add(ak * hx);
-                gy.add(ak * hy);
-                gz.add(ak * hz);
+            T gx = 0, gy = 0, gz = 0, fx = 0, fy = 0, fz = 0;
+            int k = 0;
+            for (; k + 1 < r; k += 2) {
+                double dx, dy, dz, ex, ey, ez, fr, fr1;
+                pdiff(A, sp[k], j, dx, dy, dz);
+                pdiff(A, sp[k + 1], j, ex, ey, ez);
+                kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                kval_fr(A.kind, A.kappa, fma(ez, ez, fma(ey, ey, ex * ex)), fr1);
+                const T w = (T)a[k] * fr, w1 = (T)a[k + 1] * fr1;
+                gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+                fx = fma(w1, ex, fx); fy = fma(w1, ey, fy); fz = fma(w1, ez, fz);
             }
-            gadd(A.G, j, -0.5 * A.qs[j], gx.get(), gy.get(), gz.get());
+            if (k < r) {
+                double dx, dy, dz, fr;
+                pdiff(A, sp[k], j, dx, dy, dz);
+                kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                const T w = (T)a[k] * fr;
+                gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+            }
+            gadd(A.G, j, -0.5 * A.qs[j], gx + fx, gy + fy, gz + fz);
         }
         // third term: - a^T dM c (FP64: these entries are those of M)
         for (int k = tid; k < r; k += kFThreads) {
             double gx = 0.0, gy = 0.0, gz = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
             for (int l = 0; l < r; ++l) {
-                double dx, dy, dz, hx, hy, hz;
+                double dx, dy, dz, ex, ey, ez, fr, fr1;
                 pdiff(A, sp[k], tp[l], dx, dy, dz);
-                kval_grad(A.kind, A.kappa, dx, dy, dz, hx, hy, hz);
-                gx += c[l] * hx;
-                gy += c[l] * hy;
-                gz += c[l] * hz;
-                pdiff(A, sp[l], tp[k], dx, dy, dz);
-                kval_grad(A.kind, A.kappa, dx, dy, dz, hx, hy, hz);
-                fx += a[l] * hx;
-                fy += a[l] * hy;
-                fz += a[l] * hz;
+                pdiff(A, sp[l], tp[k], ex, ey, ez);
+                kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                kval_fr(A.kind, A.kappa, fma(ez, ez, fma(ey, ey, ex * ex)), fr1);
+                const double w = c[l] * fr, w1 = a[l] * fr1;
+                gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+                fx = fma(w1, ex, fx); fy = fma(w1, ey, fy); fz = fma(w1, ez, fz);
             }
             gadd(A.G, sp[k], -0.5 * a[k], gx, gy, gz);
             gadd(A.G, tp[k], 0.5 * c[k], fx, fy, fz);
@@ -465,6 +538,7 @@ void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s) {
         h.fG = h.mem.get<double>((size_t)std::max<int64_t>(h.N, 1) * 3);
         h.fE = h.mem.get<double>((size_t)std::max<int64_t>(nparts, 1) + 1024);
         h.fM = h.mem.get<double>((size_t)grid * std::max(1, h.max_rank) * std::max(1, h.max_rank));
+        h.fctr = h.mem.get<int>(1);
         if (fp32) {
             h.fph = h.mem.get<float4>((size_t)std::max<int64_t>(h.N, 1));
             h.fpl = h.mem.get<float4>((size_t)std::max<int64_t>(h.N, 1));
@@ -494,13 +568,17 @@ void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s) {
     A.Mscr = h.fM;
     A.mr = std::max(1, h.max_rank);
     A.Epart = h.fE + 1024;
+    A.next = h.fctr;
     // the near kernel writes every point's gradient (each point lies in one leaf),
     // the far kernel then adds to it
     if (fp32)
         k_force_near<float><<<h.nleaf, kFThreads, 0, s>>>(A);
     else
         k_force_near<double><<<h.nleaf, kFThreads, 0, s>>>(A);
-    if (h.nblk > 0) k_force_far<<<grid, kFThreads, 0, s>>>(A);
+    if (h.nblk > 0) {
+        H3D_CUDA(cudaMemsetAsync(h.fctr, 0, sizeof(int), s));
+        k_force_far<<<grid, kFThreads, 0, s>>>(A);
+    }
     k_forces_out<<<gn(N, 256), 256, 0, s>>>(h.fG, h.perm, N, F);
     const int nout = (int)std::min<int64_t>(1024, std::max<int64_t>(1, nparts));
     k_sum_parts<<<nout, 256, 0, s>>>(h.fE + 1024, nparts, h.fE, nout);

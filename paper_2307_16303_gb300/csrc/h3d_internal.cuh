@@ -240,6 +240,7 @@ struct Handle {
     double *epart = nullptr;                      // energy partial sums
     double *fqs = nullptr, *fG = nullptr;         // forces: charges and dE/dp in Morton order
     double *fE = nullptr, *fM = nullptr;          // forces: energy partials, K(sigma,tau) scratch
+    int *fctr = nullptr;                          // forces: next far-field block (work queue head)
     float4 *fph = nullptr, *fpl = nullptr;        // forces (FP32 handles): coordinates hi / lo, charge
     void *hx = nullptr, *hy = nullptr;
     int64_t host_cols = 0;
