@@ -1325,11 +1325,14 @@ void matvec_mr(Handle &h, const T *x, T *y, int q0, int nq, cudaStream_t s, cuda
 // solve's output carries the condition of M (up to ~1e7), which FP32 entries of
 // K(X,tau) would turn into O(1) errors.
 
-// 1/sqrt(d2) to FP64 accuracy from an FP32 seed and two Newton steps
+// 1/sqrt(d2) to FP64 accuracy without the FP64 square root or division
 __device__ __forceinline__ double skel_rsqrt(double d2) {
-    double y = (double)rsqrtf((float)d2);
-    y = y * (1.5 - 0.5 * d2 * y * y);
-    return y * (1.5 - 0.5 * d2 * y * y);
+    // FP32 seed y0 (|relative error| < 2^-21), then one third-order step of
+    // y = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3 e^2/8 + ...), e = 1 - d2 y0^2 (y0^2
+    // exact in FP64); the neglected terms are below 2^-60
+    const double y0 = (double)rsqrtf((float)d2);
+    const double e = fma(-d2, y0 * y0, 1.0);
+    return fma(y0 * e, fma(0.375, e, 0.5), y0);
 }
 
 __device__ __forceinline__ double skel_k(int kind, double kappa, const double *px, const double *py,
