@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 # N = 125,000 uniform case (same per-leaf shape as N = 1M; FP32, one right-hand
 # side): traffic grows with the factor entries, so a launch's traffic is this
 # ratio times its algorithmic bytes.  Kernels without a capture report None.
-NCU_TRAFFIC_RATIO: dict = {"k_leaf": 1.052, "k_gather": 1.055}
+NCU_TRAFFIC_RATIO: dict = {"k_leaf": 1.052, "k_gather": 1.058}
 
 
 def parse():
