@@ -128,6 +128,7 @@ struct Handle {
     void *skel_xs = nullptr, *skel_near = nullptr; // pass columns: permuted x point-major, near field
     int skel_nq = 16;                             // columns per skeleton pass (memory-bound choice)
     int64_t *skel_src_ptr = nullptr, *skel_src_order = nullptr;   // blocks by source box (transpose)
+    int *skel_next = nullptr;                     // next block of the source-side pass (work queue head)
     double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
     int L = 0;
 

@@ -1361,7 +1361,17 @@ struct SkelArgs {
     double *sbuf, *cbuf;
     int mr;                   // largest rank (per-warp scratch stride)
     int cst;                  // columns per pass (cbuf stride per pivot)
+    int *next;                // source-side pass: next block (zero before the launch)
 };
+
+// next block for a warp of a source-side pass: blocks in list order (largest,
+// level 1, first) from one queue, so that a few large blocks do not leave the
+// warps that drew them running long after the rest
+__device__ __forceinline__ int64_t skel_next_block(const SkelArgs &S, int lane) {
+    int b = 0;
+    if (lane == 0) b = atomicAdd(S.next, 1);
+    return __shfl_sync(0xffffffffu, b, 0);
+}
 
 constexpr int kSkThreads = 128;
 
@@ -1448,8 +1458,9 @@ template <class T, int NQ>
 __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__restrict__ xs, int nq) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * kSkThreads + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * kSkThreads) >> 5;
-    for (int64_t b = w0; b < S.nblk; b += nw) {
+    for (;;) {
+        const int64_t b = skel_next_block(S, lane);
+        if (b >= S.nblk) break;
         const int r = S.rank[b];
         if (r == 0) continue;
         const int X = S.blk_tgt[b], Y = S.blk_src[b];
@@ -1480,7 +1491,29 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
             }
         }
         __syncwarp();
-        if constexpr (NQ == 1) {   // one column: the warp shares each dot product
+        if (NQ == 1 && r <= 64) {   // one column, rank <= 64: lane k holds z_k and z_(k+32)
+            // column-oriented substitutions: one FMA per lane and column instead of a
+            // dot product and a five-step FP64 warp sum per row
+            const int k0 = lane, k1 = lane + 32;
+            double z0 = k0 < r ? sv[(int64_t)pv[k0] * kSkNQ] : 0.0, z1 = k1 < r ? sv[(int64_t)pv[k1] * kSkNQ] : 0.0;
+            const double i0 = k0 < r ? 1.0 / M[(size_t)k0 * r + k0] : 0.0, i1 = k1 < r ? 1.0 / M[(size_t)k1 * r + k1] : 0.0;
+            for (int l = 0; l < r; ++l) {   // L z = P s (unit lower)
+                const double zl = __shfl_sync(0xffffffffu, l < 32 ? z0 : z1, l & 31);
+                if (k0 > l && k0 < r) z0 = fma(-M[(size_t)k0 * r + l], zl, z0);
+                if (k1 > l && k1 < r) z1 = fma(-M[(size_t)k1 * r + l], zl, z1);
+            }
+            for (int l = r - 1; l >= 0; --l) {   // U c = z
+                if (lane == (l & 31)) {
+                    if (l < 32) z0 *= i0;
+                    else z1 *= i1;
+                }
+                const double cl = __shfl_sync(0xffffffffu, l < 32 ? z0 : z1, l & 31);
+                if (k0 < l) z0 = fma(-M[(size_t)k0 * r + l], cl, z0);
+                if (k1 < l) z1 = fma(-M[(size_t)k1 * r + l], cl, z1);
+            }
+            if (k0 < r) cv[(int64_t)k0 * S.cst] = z0;
+            if (k1 < r) cv[(int64_t)k1 * S.cst] = z1;
+        } else if (NQ == 1) {   // one column, larger rank: the warp shares each dot product
             for (int k = 0; k < r; ++k) {   // L z = P s (unit lower)
                 double acc = 0.0;
                 for (int l = lane; l < k; l += 32) acc += M[(size_t)k * r + l] * cv[(int64_t)l * S.cst];
@@ -1567,8 +1600,9 @@ template <class T, int NQ>
 __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *__restrict__ xs, int nq) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * kSkThreads + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * kSkThreads) >> 5;
-    for (int64_t b = w0; b < S.nblk; b += nw) {
+    for (;;) {
+        const int64_t b = skel_next_block(S, lane);
+        if (b >= S.nblk) break;
         const int r = S.rank[b];
         if (r == 0) continue;
         const int X = S.blk_tgt[b], Y = S.blk_src[b];
@@ -1600,7 +1634,27 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *_
         }
         __syncwarp();
         // z and w overwrite u in sv; a is scattered into cv by the row order
-        if constexpr (NQ == 1) {
+        if (NQ == 1 && r <= 64) {   // one column, rank <= 64: lane k holds entries k and k + 32
+            const int k0 = lane, k1 = lane + 32;
+            double z0 = k0 < r ? sv[(int64_t)k0 * kSkNQ] : 0.0, z1 = k1 < r ? sv[(int64_t)k1 * kSkNQ] : 0.0;
+            const double i0 = k0 < r ? 1.0 / M[(size_t)k0 * r + k0] : 0.0, i1 = k1 < r ? 1.0 / M[(size_t)k1 * r + k1] : 0.0;
+            for (int l = 0; l < r; ++l) {   // U^T z = u (column l of U^T is row l of U)
+                if (lane == (l & 31)) {
+                    if (l < 32) z0 *= i0;
+                    else z1 *= i1;
+                }
+                const double zl = __shfl_sync(0xffffffffu, l < 32 ? z0 : z1, l & 31);
+                if (k0 > l && k0 < r) z0 = fma(-M[(size_t)l * r + k0], zl, z0);
+                if (k1 > l && k1 < r) z1 = fma(-M[(size_t)l * r + k1], zl, z1);
+            }
+            for (int l = r - 1; l >= 0; --l) {   // L^T w = z (unit diagonal)
+                const double wl = __shfl_sync(0xffffffffu, l < 32 ? z0 : z1, l & 31);
+                if (k0 < l) z0 = fma(-M[(size_t)l * r + k0], wl, z0);
+                if (k1 < l) z1 = fma(-M[(size_t)l * r + k1], wl, z1);
+            }
+            if (k0 < r) cv[(int64_t)pv[k0] * S.cst] = z0;
+            if (k1 < r) cv[(int64_t)pv[k1] * S.cst] = z1;
+        } else if (NQ == 1) {
             for (int k = 0; k < r; ++k) {   // U^T z = u
                 double acc = 0.0;
                 for (int l = lane; l < k; l += 32) acc += M[(size_t)l * r + k] * sv[(int64_t)l * kSkNQ];
@@ -1697,6 +1751,7 @@ SkelArgs skel_args(Handle &h) {
     S.sbuf = h.skel_s; S.cbuf = h.skel_c;
     S.mr = std::max(1, h.max_rank);
     S.cst = std::max(1, h.skel_nq);
+    S.next = h.skel_next;
     return S;
 }
 
@@ -1724,6 +1779,7 @@ void matvec_skel_pass(Handle &h, const T *x, T *y, int q0, int nq, bool transpos
     SkelArgs S = skel_args(h);
     if (h.nblk > 0) {
         const int grid = skel_src_grid(h);
+        H3D_CUDA(cudaMemsetAsync(h.skel_next, 0, sizeof(int), s));
         if (transpose) {
             if (nq == 1) k_skelT_src<T, 1><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
             else k_skelT_src<T, kSkNQ><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
@@ -2012,6 +2068,7 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
         while (h.skel_nq > 1 && (double)h.sum_rank * h.skel_nq * 8.0 > avail / 3.0) h.skel_nq /= 2;
     }
     h.skel_s = h.mem.get<double>((size_t)skel_src_grid(h) * (kSkThreads / 32) * std::max(1, h.max_rank) * kSkNQ);
+    h.skel_next = h.mem.get<int>(1);
     h.skel_c = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1) * h.skel_nq);
     h.skel_xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
     h.skel_near = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
