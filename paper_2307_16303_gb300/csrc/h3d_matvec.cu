@@ -1335,6 +1335,19 @@ __device__ __forceinline__ double skel_rsqrt(double d2) {
     return fma(y0 * e, fma(0.375, e, 0.5), y0);
 }
 
+// K(p_i, p_j) from the coordinate differences p_i - p_j
+__device__ __forceinline__ double skel_kd(int kind, double kappa, double dx, double dy, double dz) {
+    const double d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 == 0.0) return 0.0;
+    const double ir = skel_rsqrt(d2);
+    switch (kind) {
+    case H3D_LAPLACE: return H3D_INV4PI * ir;
+    case H3D_YUKAWA: return H3D_INV4PI * exp(-kappa * d2 * ir) * ir;
+    case H3D_INV_R4: return (ir * ir) * (ir * ir);
+    default: return cos(d2 * ir) * ir;
+    }
+}
+
 __device__ __forceinline__ double skel_k(int kind, double kappa, const double *px, const double *py,
                                          const double *pz, int i, int j) {
     const double dx = px[i] - px[j], dy = py[i] - py[j], dz = pz[i] - pz[j];
@@ -1374,6 +1387,7 @@ __device__ __forceinline__ int64_t skel_next_block(const SkelArgs &S, int lane) 
 }
 
 constexpr int kSkThreads = 128;
+constexpr int kSkLeafStage = 128;   // pivots staged per warp at a time (single-column leaf pass)
 
 // M = K(sigma,tau) of every block, factored P M = L U in place (partial pivoting)
 __global__ void __launch_bounds__(kSkThreads) k_skel_factor(SkelArgs S) {
@@ -1470,7 +1484,32 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
         double *sv = S.sbuf + w0 * (int64_t)S.mr * kSkNQ, *cv = S.cbuf + po * S.cst;
         const double *M = S.lu + S.lu_off[b];
         const int *pv = S.lu_piv + po;
-        for (int k = 0; k < r; ++k) {
+        int kb = 0;
+        if (NQ == 1)   // four pivots at a time: each source point is loaded once per four entries
+            for (; kb + 4 <= r; kb += 4) {
+                double sx[4], sy[4], sz[4], a4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int ps = x0 + sg[kb + u];
+                    sx[u] = S.px[ps];
+                    sy[u] = S.py[ps];
+                    sz[u] = S.pz[ps];
+                    a4[u] = 0.0;
+                }
+                for (int j = y0 + lane; j < y1; j += 32) {
+                    const double jx = S.px[j], jy = S.py[j], jz = S.pz[j], xv = (double)xs[j];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        a4[u] += skel_kd(S.kind, S.kappa, sx[u] - jx, sy[u] - jy, sz[u] - jz) * xv;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    double v = a4[u];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) sv[(int64_t)(kb + u) * kSkNQ] = v;
+                }
+            }
+        for (int k = kb; k < r; ++k) {
             const int ps = x0 + sg[k];
             double acc[NQ];
 #pragma unroll
@@ -1553,6 +1592,7 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A
                                                           const T *__restrict__ nearbuf, T *__restrict__ y, int64_t n,
                                                           int nq) {
     __shared__ double red[kSkThreads / 32][32][NQ];
+    __shared__ Pt4d piv[kSkThreads / 32][NQ == 1 ? kSkLeafStage : 1];   // one column: a warp's staged pivots
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int z = blockIdx.x;
     const int Zg = (int)(A.offL + z);
@@ -1563,6 +1603,7 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A
         double acc[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+        const double ix = row ? S.px[i] : 0.0, iy = row ? S.py[i] : 0.0, iz = row ? S.pz[i] : 0.0;
         int cnt = 0;
         for (int l = 1; l <= A.L; ++l) {
             const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
@@ -1571,6 +1612,23 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A
                 const int r = S.rank[b];
                 const int y0 = S.box_start[S.blk_src[b]];
                 const int64_t po = S.piv_off[b];
+                if (NQ == 1) {   // pivots (coordinates and coefficient) staged in shared memory
+                    for (int k0 = 0; k0 < r; k0 += kSkLeafStage) {
+                        const int kn = min(kSkLeafStage, r - k0);
+                        __syncwarp();
+                        for (int k = lane; k < kn; k += 32) {
+                            const int pt = y0 + S.tau[po + k0 + k];
+                            piv[warp][k] = make_pt4d(S.px[pt], S.py[pt], S.pz[pt], S.cbuf[(po + k0 + k) * S.cst]);
+                        }
+                        __syncwarp();
+                        if (row)
+                            for (int k = 0; k < kn; ++k) {
+                                const Pt4d p = piv[warp][k];
+                                acc[0] += skel_kd(S.kind, S.kappa, ix - p.x, iy - p.y, iz - p.z) * p.w;
+                            }
+                    }
+                    continue;
+                }
                 for (int k = 0; k < r; ++k) {
                     const double kv = row ? skel_k(S.kind, S.kappa, S.px, S.py, S.pz, i, y0 + S.tau[po + k]) : 0.0;
                     const double *cv = S.cbuf + (po + k) * S.cst;
