@@ -68,24 +68,8 @@ __device__ __forceinline__ double kval_fr(int kind, double kappa, double d2, dou
 // K(a, b) and dK/da = (f'(rho) / rho) (a - b) for a - b = (dx, dy, dz)
 __device__ __forceinline__ double kval_grad(int kind, double kappa, double dx, double dy, double dz, double &gx,
                                             double &gy, double &gz) {
-    const double d2 = dx * dx + dy * dy + dz * dz;
-    if (d2 == 0.0) {
-        gx = gy = gz = 0.0;
-        return 0.0;
-    }
-    const double ir = rsqrt64(d2), r = d2 * ir;
-    double f, fr;   // f and f'(rho) / rho
-    switch (kind) {
-    case H3D_LAPLACE: f = H3D_INV4PI * ir; fr = -f * ir * ir; break;
-    case H3D_YUKAWA: f = H3D_INV4PI * exp(-kappa * r) * ir; fr = -f * (1.0 + kappa * r) * ir * ir; break;
-    case H3D_INV_R4: f = (ir * ir) * (ir * ir); fr = -4.0 * f * ir * ir; break;
-    default: {
-        double sn, cs;
-        sincos(r, &sn, &cs);
-        f = cs * ir;
-        fr = -(r * sn + cs) * ir * ir * ir;
-    }
-    }
+    double fr;
+    const double f = kval_fr(kind, kappa, dx * dx + dy * dy + dz * dz, fr);
     gx = fr * dx;
     gy = fr * dy;
     gz = fr * dz;
@@ -173,19 +157,6 @@ __device__ __forceinline__ void pdiff(const ForceArgs &A, int i, int j, float &d
 template <class T> __device__ __forceinline__ T charge(const ForceArgs &A, int i);
 template <> __device__ __forceinline__ double charge<double>(const ForceArgs &A, int i) { return A.qs[i]; }
 template <> __device__ __forceinline__ float charge<float>(const ForceArgs &A, int i) { return A.ph[i].w; }
-
-template <class T>
-__device__ __forceinline__ T kv(const ForceArgs &A, int i, int j) {
-    T dx, dy, dz, gx, gy, gz;
-    pdiff(A, i, j, dx, dy, dz);
-    return kval_grad(A.kind, (T)A.kappa, dx, dy, dz, gx, gy, gz);
-}
-template <class T>
-__device__ __forceinline__ void kg(const ForceArgs &A, int i, int j, T &gx, T &gy, T &gz) {
-    T dx, dy, dz;
-    pdiff(A, i, j, dx, dy, dz);
-    kval_grad(A.kind, (T)A.kappa, dx, dy, dz, gx, gy, gz);
-}
 
 template <class T>
 __global__ void k_charges_sorted(const T *__restrict__ q, const int *__restrict__ perm, const double *__restrict__ px,
