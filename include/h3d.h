@@ -215,6 +215,22 @@ h3d_status h3d_batch_tune(h3d_batch b, const void *const *x, void *const *y, voi
 h3d_status h3d_batch_configure(h3d_batch b, int persistent, int ctas_per_sm, int near_group, int leaf_group,
                                int lag);
 h3d_status h3d_batch_info(h3d_batch b, int *persistent, int *ctas_per_sm, int *branches);
+
+/* The persistent batch form's work queue for operators of the given sizes
+ * (host only, no device work; for tests and inspection).  Operator o has
+ * n_points[o] >= 1 points, n_gather[o] gather tasks, n_split[o] split source
+ * boxes and n_leaves[o] >= 1 leaves; near_group, leaf_group >= 1 and lag >= 0
+ * as in h3d_batch_configure.  items (host, 4 ints per item, capacity `cap`
+ * items; NULL: only count) receives (operator, kind, first, count) with kind 0
+ * gather task, 1 near-field leaf run, 2 split-box reduction, 3 leaf run,
+ * 4 permute chunk (first point; count unused); *count the number of items.
+ * H3D_ERR_ARG on bad sizes or a capacity below the count.  Every item comes
+ * after the items it waits for: an operator's permute chunks before its gather
+ * and near-field items, its gathers before its reductions, and its gathers,
+ * reductions and near-field runs before its leaf runs.                       */
+h3d_status h3d_batch_queue(int nops, const int64_t *n_points, const int *n_gather, const int *n_split,
+                           const int *n_leaves, int near_group, int leaf_group, int lag, int *items, int64_t cap,
+                           int64_t *count);
 h3d_status h3d_batch_free(h3d_batch b);
 
 /* h3d_matvec with HOST x and y: copies x to the device, runs the product and

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_
 EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3d_matvec_host", "h3d_free",
            "h3d_status_string", "h3d_get_stats", "h3d_matvec_profile", "h3d_export_tree", "h3d_export_lists",
            "h3d_export_pivots", "h3d_morton_order_noalloc", "h3d_energy", "h3d_forces",
-           "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_configure", "h3d_batch_info",
+           "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_configure", "h3d_batch_info", "h3d_batch_queue",
            "h3d_batch_free")
 
 
@@ -87,6 +87,7 @@ def lib():
             "h3d_batch_tune": (i32, [P, P, P, P, C.POINTER(i32)]),
             "h3d_batch_configure": (i32, [P, i32, i32, i32, i32, i32]),
             "h3d_batch_info": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+            "h3d_batch_queue": (i32, [i32, P, P, P, P, i32, i32, i32, P, C.c_int64, C.POINTER(C.c_int64)]),
             "h3d_batch_free": (i32, [P]),
         }
         for name, (res, args) in sig.items():
@@ -286,6 +287,27 @@ class H3DMatrix:
         if st != 0:
             raise H3DError(st, "h3d_export_pivots")
         return rank[:s["n_blocks"]], sig[:s["sum_rank"]], tau[:s["sum_rank"]]
+
+
+def batch_queue(n_points, n_gather, n_split, n_leaves, near_group=4, leaf_group=2, lag=0) -> np.ndarray:
+    """The persistent batch form's work queue for operators of these sizes
+    (h3d_batch_queue; host only): an (items x 4) int32 array of (operator,
+    kind, first, count), kind 0 gather, 1 near field, 2 reduce, 3 leaf,
+    4 permute."""
+    n = len(n_points)
+    npts = np.ascontiguousarray(n_points, np.int64)
+    ng, ns, nl = (np.ascontiguousarray(v, np.int32) for v in (n_gather, n_split, n_leaves))
+    cnt = C.c_int64()
+    st = lib().h3d_batch_queue(n, _np(npts), _np(ng), _np(ns), _np(nl), near_group, leaf_group, lag, None, 0,
+                               C.byref(cnt))
+    if st != 0:
+        raise H3DError(st, "h3d_batch_queue")
+    out = np.zeros((max(cnt.value, 1), 4), np.int32)
+    st = lib().h3d_batch_queue(n, _np(npts), _np(ng), _np(ns), _np(nl), near_group, leaf_group, lag, _np(out),
+                               cnt.value, C.byref(cnt))
+    if st != 0:
+        raise H3DError(st, "h3d_batch_queue")
+    return out[:cnt.value]
 
 
 class H3DBatch:

@@ -256,49 +256,60 @@ void merge_even(std::vector<int4> &out, const std::vector<int4> &a, const std::v
 // the R and L items of operator k - d, so that operators finish one after
 // another instead of all at the end.  Either way every item comes after the
 // items it waits for.
-void build_items(BatchPlan &p) {
+struct QueueCounts {
+    int64_t n;             // points
+    int ngtask, nsplit, nleaf;
+};
+
+std::vector<int4> batch_queue(const std::vector<QueueCounts> &c, int near_group, int leaf_group, int lag) {
+    const int nops = (int)c.size();
     std::vector<int4> items;
-    for (int o = 0; o < p.nops; ++o)
-        for (int64_t i = 0; i < p.hs[o]->N; i += kPermChunk) items.push_back(make_int4(o, kItemPerm, (int)i, 0));
+    for (int o = 0; o < nops; ++o)
+        for (int64_t i = 0; i < c[o].n; i += kPermChunk) items.push_back(make_int4(o, kItemPerm, (int)i, 0));
     auto stream_items = [&](int o) {   // G and N of operator o
-        const Handle &h = *p.hs[o];
         std::vector<int4> g, n, out;
-        for (int k = 0; k < h.ngtask; ++k) g.push_back(make_int4(o, kItemGather, k, 1));
-        for (int z0 = 0; z0 < h.nleaf; z0 += p.near_group)
-            n.push_back(make_int4(o, kItemNear, z0, std::min(p.near_group, h.nleaf - z0)));
+        for (int k = 0; k < c[o].ngtask; ++k) g.push_back(make_int4(o, kItemGather, k, 1));
+        for (int z0 = 0; z0 < c[o].nleaf; z0 += near_group)
+            n.push_back(make_int4(o, kItemNear, z0, std::min(near_group, c[o].nleaf - z0)));
         merge_even(out, g, n);
         return out;
     };
     auto finish_items = [&](int o, bool reduce, bool leaf) {   // R and / or L of operator o
-        const Handle &h = *p.hs[o];
         std::vector<int4> out;
         if (reduce)
-            for (int q = 0; q < h.nsplit; ++q) out.push_back(make_int4(o, kItemReduce, q, 1));
+            for (int q = 0; q < c[o].nsplit; ++q) out.push_back(make_int4(o, kItemReduce, q, 1));
         if (leaf)
-            for (int z0 = 0; z0 < h.nleaf; z0 += p.leaf_group)
-                out.push_back(make_int4(o, kItemLeaf, z0, std::min(p.leaf_group, h.nleaf - z0)));
+            for (int z0 = 0; z0 < c[o].nleaf; z0 += leaf_group)
+                out.push_back(make_int4(o, kItemLeaf, z0, std::min(leaf_group, c[o].nleaf - z0)));
         return out;
     };
-    if (p.lag <= 0) {
-        for (int o = 0; o < p.nops; ++o) {
+    if (lag <= 0) {
+        for (int o = 0; o < nops; ++o) {
             const std::vector<int4> v = stream_items(o);
             items.insert(items.end(), v.begin(), v.end());
         }
-        for (int o = 0; o < p.nops; ++o) {
+        for (int o = 0; o < nops; ++o) {
             const std::vector<int4> v = finish_items(o, true, false);
             items.insert(items.end(), v.begin(), v.end());
         }
-        for (int o = 0; o < p.nops; ++o) {
+        for (int o = 0; o < nops; ++o) {
             const std::vector<int4> v = finish_items(o, false, true);
             items.insert(items.end(), v.begin(), v.end());
         }
     } else {
-        for (int k = 0; k < p.nops + p.lag; ++k) {
-            const std::vector<int4> a = k < p.nops ? stream_items(k) : std::vector<int4>();
-            const std::vector<int4> b = k >= p.lag ? finish_items(k - p.lag, true, true) : std::vector<int4>();
+        for (int k = 0; k < nops + lag; ++k) {
+            const std::vector<int4> a = k < nops ? stream_items(k) : std::vector<int4>();
+            const std::vector<int4> b = k >= lag ? finish_items(k - lag, true, true) : std::vector<int4>();
             merge_even(items, a, b);
         }
     }
+    return items;
+}
+
+void build_items(BatchPlan &p) {
+    std::vector<QueueCounts> c;
+    for (const Handle *h : p.hs) c.push_back(QueueCounts{h->N, h->ngtask, h->nsplit, h->nleaf});
+    const std::vector<int4> items = batch_queue(c, p.near_group, p.leaf_group, p.lag);
     p.nitems = (int)items.size();
     p.d_items = upload(p, p.d_items, items);
     if (p.exec) {
@@ -418,3 +429,31 @@ void batch_plan_run(BatchPlan &p, const void *const *x, void *const *y, int ctas
 void batch_plan_free(BatchPlan *p) { delete p; }
 
 }  // namespace h3d
+
+extern "C" h3d_status h3d_batch_queue(int nops, const int64_t *n_points, const int *n_gather, const int *n_split,
+                                      const int *n_leaves, int near_group, int leaf_group, int lag, int *items,
+                                      int64_t cap, int64_t *count) {
+    if (nops < 1 || !n_points || !n_gather || !n_split || !n_leaves || near_group < 1 || leaf_group < 1 || lag < 0 ||
+        !count || cap < 0)
+        return H3D_ERR_ARG;
+    std::vector<h3d::QueueCounts> c;
+    for (int o = 0; o < nops; ++o) {
+        if (n_points[o] < 1 || n_gather[o] < 0 || n_split[o] < 0 || n_leaves[o] < 1) return H3D_ERR_ARG;
+        c.push_back(h3d::QueueCounts{n_points[o], n_gather[o], n_split[o], n_leaves[o]});
+    }
+    try {
+        const std::vector<int4> q = h3d::batch_queue(c, near_group, leaf_group, lag);
+        *count = (int64_t)q.size();
+        if (!items) return H3D_OK;
+        if (cap < (int64_t)q.size()) return H3D_ERR_ARG;
+        for (size_t k = 0; k < q.size(); ++k) {
+            items[4 * k] = q[k].x;
+            items[4 * k + 1] = q[k].y;
+            items[4 * k + 2] = q[k].z;
+            items[4 * k + 3] = q[k].w;
+        }
+    } catch (const std::bad_alloc &) {
+        return H3D_ERR_OOM;
+    }
+    return H3D_OK;
+}
