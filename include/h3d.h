@@ -172,10 +172,10 @@ h3d_status h3d_forces(h3d_handle h, const void *q, double *E, double *F, void *s
  * A batch runs the products y_i = A~_i x_i of several handles (one right-hand
  * side each; Alg. 2 for every operator) in one of two forms:
  *   persistent  ONE launch of a persistent kernel whose CTAs take work items of
- *               every operator from a device queue (gather, near-field, reduce
- *               and leaf items; an item waits, with a bounded wait, until the
- *               items it reads are complete), replayed as a CUDA graph together
- *               with the reset of the queue.  Available when every handle
+ *               every operator from a device queue (permute, gather,
+ *               near-field, reduce and leaf items; an item waits, with a
+ *               bounded wait, until the items it reads are complete), replayed
+ *               as a CUDA graph together with the reset of the queue.  Available when every handle
  *               stores factors (H3D_STORE_FACTORS) and all are FP64, or all
  *               FP32 / FP32_3XTF32; it is then the default.
  *   graph       every handle's own product (the kernels of h3d_matvec) captured
@@ -183,8 +183,9 @@ h3d_status h3d_forces(h3d_handle h, const void *q, double *E, double *F, void *s
  *               assigned longest first to the least loaded stream; later calls
  *               with the same vectors replay it (new vectors re-capture).
  * The handles must be distinct (H3D_ERR_ARG otherwise), must outlive the batch
- * and must not be used elsewhere while a batch product is in flight.  A wait that runs out in the persistent kernel
- * leaves H3D_ERR_TIMEOUT in that handle's error word (reported by the next call).
+ * and must not be used elsewhere while a batch product is in flight.  A wait
+ * that runs out in the persistent kernel leaves H3D_ERR_TIMEOUT in that
+ * handle's error word (reported by the next call).
  *   handles  host array of `count` built handles.
  *   x, y     host arrays of `count` device pointers: x[i], y[i] are N_i values
  *            of handle i's element type (caller's order); y overwritten.  In the
@@ -204,8 +205,9 @@ h3d_status h3d_forces(h3d_handle h, const void *q, double *E, double *F, void *s
  * item and per leaf item, and the queue order (lag 0: phase-major; d > 0:
  * pipelined over operators); 0 (-1 for lag) keeps the current value.  The
  * settings change who computes an item and when, never how: the persistent
- * form's results are the same bits for every setting.  h3d_batch_info reports the form in use
- * (*persistent: 1 persistent, 0 graph, -1 graph and persistent unavailable),
+ * form's results are the same bits for every setting.  h3d_batch_info reports
+ * the form in use (*persistent: 1 persistent, 0 graph, -1 graph and persistent
+ * unavailable),
  * the CTAs per SM of the persistent form and the branch count of the graph
  * form; any pointer may be NULL.                                              */
 typedef struct h3d_batch_s *h3d_batch;
