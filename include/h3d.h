@@ -17,12 +17,14 @@
  *     the library permutes internally.
  *   - Multi-column vectors are N x nrhs, column-major (column c starts at c*N).
  *   - Element type of x and y is double for H3D_FP64 handles and float for
- *     H3D_FP32 handles.
+ *     H3D_FP32 and H3D_FP32_3XTF32 handles.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Products
  *     are stream-ordered and asynchronous; the build synchronises the stream.
  *   - Errors are returned as h3d_status, never by abort.  A device-side error
  *     (for example a point outside the domain) is reported by the call that
- *     detects it.
+ *     detects it; a bounded device wait of an asynchronous product that gave
+ *     up leaves H3D_ERR_TIMEOUT in the handle's error word, which the next
+ *     call on the handle reports once (and clears).
  *   - A handle may be used by one stream at a time; concurrent calls on one
  *     handle race on its internal scratch buffers.
  */
@@ -44,7 +46,7 @@ typedef enum {
     H3D_ERR_OOM = 3,       /* a device allocation failed                                   */
     H3D_ERR_CUDA = 4,      /* a CUDA runtime call or kernel launch failed                  */
     H3D_ERR_ACA_RANK = 5,  /* an admissible block did not reach the tolerance by rank_cap  */
-    H3D_ERR_TIMEOUT = 6,   /* a bounded device wait gave up (reserved)                     */
+    H3D_ERR_TIMEOUT = 6,   /* a bounded device wait of an earlier product gave up          */
     H3D_ERR_STATE = 7,     /* handle in an unusable state (an earlier call failed)         */
     H3D_ERR_DEPTH = 8      /* more than leaf_size coincident points: depth would exceed 21 */
 } h3d_status;
@@ -59,10 +61,20 @@ typedef enum {
 } h3d_kernel;
 
 /* Storage and arithmetic type of the factors, the near field and x / y.
- * ACA pivots, residuals and stopping tests are always FP64.                  */
+ * ACA pivots, residuals and stopping tests are always FP64.
+ *   FP64         FP64 factors and arithmetic on CUDA cores.
+ *   FP32         FP32 factors and arithmetic on CUDA cores (products of several
+ *                columns in passes of 8 right-hand sides).
+ *   FP32_3XTF32  FP32 factors; products of more than 8 columns (leaf_size <=
+ *                128) take the factor products to the tensor cores in passes of
+ *                32 right-hand sides, each FP32 operand split into two TF32
+ *                parts (hi + lo) and the three significant partial products
+ *                accumulated in FP32; products of up to 8 columns are those of
+ *                FP32.  The default.                                          */
 typedef enum {
     H3D_FP64 = 0,
-    H3D_FP32 = 1
+    H3D_FP32 = 1,
+    H3D_FP32_3XTF32 = 2
 } h3d_precision;
 
 /* Which same-level box pairs are stored as low-rank blocks.  HODLR3D is the
@@ -92,12 +104,12 @@ typedef enum {
 } h3d_storage;
 
 typedef struct {
-    int precision;          /* h3d_precision, default H3D_FP32                          */
+    int precision;          /* h3d_precision, default H3D_FP32_3XTF32                   */
     double kappa;           /* Yukawa decay, default 1.0                                 */
     int rank_cap;           /* largest ACA rank per block, 1..512, default 512           */
     double lo[3];           /* lower corner of the domain cube, default (-1,-1,-1)       */
     double side;            /* edge length of the domain cube, default 2.0               */
-    int64_t workspace_bytes;/* device scratch budget for the build; 0 = automatic        */
+    int64_t workspace_bytes;/* device scratch budget for the build; 0 = automatic, >= 0  */
     int admissibility;      /* h3d_admissibility, default H3D_ADM_HODLR3D                */
     int storage;            /* h3d_storage, default H3D_STORE_FACTORS                    */
 } h3d_options;
@@ -127,11 +139,11 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
  *   x  device, N x nrhs in the caller's order (read only).
  *   y  device, N x nrhs, overwritten (not accumulated).  Must not alias x.
  *   nrhs >= 1.  Several right-hand sides share each pass over the factors (up
- *   to 8 per pass, or 32 for FP32 handles with leaf_size <= 128).
+ *   to 8 per pass, or 32 for H3D_FP32_3XTF32 handles with leaf_size <= 128).
  * Enqueues kernels on `stream` and returns.  Allocates nothing, except that the
- * first call with nrhs > 8 on an FP32 handle allocates (and keeps) the scratch
- * of the 32-column passes after synchronising `stream`; make that first call
- * before capturing products into a CUDA graph.                               */
+ * first call with nrhs > 8 on an H3D_FP32_3XTF32 handle allocates (and keeps)
+ * the scratch of the 32-column passes after synchronising `stream`; make that
+ * first call before capturing products into a CUDA graph.                    */
 h3d_status h3d_matvec(h3d_handle h, const void *x, void *y, int nrhs, void *stream);
 
 /* y = A~^T x: the same blocks with the roles of the two factors exchanged (the
@@ -177,15 +189,18 @@ h3d_status h3d_forces(h3d_handle h, const void *q, double *E, double *F, void *s
  *               bounded wait, until the items it reads are complete), replayed
  *               as a CUDA graph together with the reset of the queue.  Available when every handle
  *               stores factors (H3D_STORE_FACTORS) and all are FP64, or all
- *               FP32 / FP32_3XTF32; it is then the default.
+ *               FP32 or FP32_3XTF32 (the two may be mixed: a batch runs one
+ *               column per handle); it is then the default.
  *   graph       every handle's own product (the kernels of h3d_matvec) captured
  *               once into a CUDA graph on `branches` concurrent streams, clouds
  *               assigned longest first to the least loaded stream; later calls
  *               with the same vectors replay it (new vectors re-capture).
  * The handles must be distinct (H3D_ERR_ARG otherwise), must outlive the batch
- * and must not be used elsewhere while a batch product is in flight.  A wait
- * that runs out in the persistent kernel leaves H3D_ERR_TIMEOUT in that
- * handle's error word (reported by the next call).
+ * and must not be used elsewhere while a batch product is in flight, and
+ * h3d_import_pivots on a member invalidates the batch (free and re-create it).
+ * A wait that runs out in the persistent kernel leaves H3D_ERR_TIMEOUT in
+ * that handle's error word (reported once by the next call on the batch or
+ * the handle).
  *   handles  host array of `count` built handles.
  *   x, y     host arrays of `count` device pointers: x[i], y[i] are N_i values
  *            of handle i's element type (caller's order); y overwritten.  In the
@@ -217,6 +232,27 @@ h3d_status h3d_batch_tune(h3d_batch b, const void *const *x, void *const *y, voi
 h3d_status h3d_batch_configure(h3d_batch b, int persistent, int ctas_per_sm, int near_group, int leaf_group,
                                int lag);
 h3d_status h3d_batch_info(h3d_batch b, int *persistent, int *ctas_per_sm, int *branches);
+
+/* Bound of every wait of the persistent kernel on the completion counters of
+ * the items it depends on, in nanoseconds of the GPU's global timer
+ * (default 2e9, i.e. 2 s; 1e3 <= ns <= 6e10, else H3D_ERR_ARG).  A wait that
+ * runs out stops the launch: the handle of the waiting item gets
+ * H3D_ERR_TIMEOUT, the results of that product are not valid, and the handles
+ * and the batch stay usable.  Without a persistent form it is H3D_OK and has
+ * no effect.                                                                  */
+h3d_status h3d_batch_set_wait_limit(h3d_batch b, int64_t ns);
+
+/* The persistent form's work queue (for tests and inspection).
+ * h3d_batch_get_queue: *count = items in the queue; items (host, 4 ints per
+ * item as in h3d_batch_queue, capacity `cap` items; NULL: only count).
+ * h3d_batch_set_queue: run the persistent kernel on the caller's `count` items
+ * (host, same format) instead; each item must name an operator of the batch
+ * and lie inside its work (H3D_ERR_ARG otherwise), but nothing checks that
+ * every item comes after the items it waits for: a queue that breaks that
+ * order ends in the bounded waits (H3D_ERR_TIMEOUT).  items = NULL returns to
+ * the queue of the current settings.  H3D_ERR_ARG without a persistent form. */
+h3d_status h3d_batch_get_queue(h3d_batch b, int *items, int64_t cap, int64_t *count);
+h3d_status h3d_batch_set_queue(h3d_batch b, const int *items, int64_t count);
 
 /* The persistent batch form's work queue for operators of the given sizes
  * (host only, no device work; for tests and inspection).  Operator o has
@@ -300,6 +336,39 @@ h3d_status h3d_export_lists(h3d_handle h, int *blk_level, int *blk_tgt, int *blk
  * row indices local to the target box, tau column indices local to the source. */
 h3d_status h3d_export_pivots(h3d_handle h, int *rank, int *sigma, int *tau);
 
+/* Re-form the handle from given ACA pivots (Sec. 4.1, Eq. prank: a block is
+ * determined by its pivot rows sigma and columns tau): the same tree and lists,
+ * the caller's ranks and pivots, and the factors (or, for skeleton storage,
+ * the LU of K(sigma,tau)) formed from them by the ACA recurrences without the
+ * pivot search.  Used to compare against pivots found elsewhere (for example
+ * by an independent CPU search) and to restore pivots saved earlier.
+ *   rank, sigma, tau  host, in the format of h3d_export_pivots; 0 <= rank[b] <=
+ *          min(m_b, n_b, rank_cap), indices inside the block, no row or column
+ *          twice in one block; otherwise H3D_ERR_ARG.  Pivots that ACA could
+ *          not have chosen (a vanishing residual at a pivot) give non-finite
+ *          factors.
+ * Builds the replacement first (synchronising `stream` and the device) and
+ * swaps it in only on success; on error the handle is unchanged.  Batches that
+ * hold the handle must be re-created afterwards.                              */
+h3d_status h3d_import_pivots(h3d_handle h, const int *rank, const int *sigma, const int *tau, void *stream);
+
+/* Move the points: new coordinates for the same N points, keeping the build's
+ * tree, lists, ranks and pivots (frozen) and re-forming the factors (or the LU
+ * of K(sigma,tau)) from them at the new positions.  The operator is then the
+ * function of the positions that h3d_forces differentiates; points may leave
+ * their boxes (nothing is re-sorted), at the cost of accuracy if they move far.
+ *   points  device, N x 3 row-major FP64, the caller's order (read only).
+ * Coordinates equal to the current ones bit for bit cost one comparison pass
+ * and change nothing.  H3D_ERR_DOMAIN (handle unchanged) for a non-finite
+ * coordinate.  Synchronises `stream`.                                        */
+h3d_status h3d_set_points(h3d_handle h, const double *points, void *stream);
+
+/* Test hook: the next `after` device allocations made by the library succeed
+ * and the one after them fails as if the device were out of memory (the call
+ * that makes it returns H3D_ERR_OOM and releases what it allocated); after < 0
+ * switches the injection off.  Process-wide, not thread-safe.                */
+void h3d_debug_fail_alloc(int64_t after);
+
 /* ---- Morton order without allocation (the paper has no counterpart) --------
  * For callers that cannot allocate device memory (a host application that owns
  * a fixed memory pool, a plugin that only receives pre-allocated buffers): the
@@ -319,7 +388,8 @@ h3d_status h3d_export_pivots(h3d_handle h, int *rank, int *sigma, int *tau);
  * The scratch array is held by every GPU that loads the library until the
  * process exits and is shared by all calls: calls that overlap on the GPU race
  * and must be serialised by the caller.  The first call on a device resolves
- * the array's device address; make that first call before any stream capture. */
+ * the array's device address.  Every call synchronises its stream, so it must
+ * not be made while that stream is being captured into a CUDA graph.         */
 #define H3D_NOALLOC_MAX_POINTS (1 << 20)
 #define H3D_NOALLOC_SCRATCH_BYTES (14 << 20)
 h3d_status h3d_morton_order_noalloc(const double *points, int64_t N, const double *lo, double side,

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libh3d.so")
 
 KERNELS = {"laplace": 0, "yukawa": 1, "inv_r4": 2, "cos_r": 3}
-PRECISIONS = {"fp64": 0, "fp32": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_3xtf32": 2}
 ADMISSIBILITY = {"hodlr3d": 0, "strong": 1, "weak": 2}
 STORAGE = {"factors": 0, "skeleton": 1}
 STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_OOM", 4: "H3D_ERR_CUDA",
@@ -24,8 +24,10 @@ STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_
 # every entry point declared in include/h3d.h
 EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3d_matvec_host", "h3d_free",
            "h3d_status_string", "h3d_get_stats", "h3d_matvec_profile", "h3d_export_tree", "h3d_export_lists",
-           "h3d_export_pivots", "h3d_morton_order_noalloc", "h3d_energy", "h3d_forces",
-           "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_configure", "h3d_batch_info", "h3d_batch_queue",
+           "h3d_export_pivots", "h3d_import_pivots", "h3d_set_points", "h3d_debug_fail_alloc",
+           "h3d_morton_order_noalloc", "h3d_energy", "h3d_forces",
+           "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_configure", "h3d_batch_info",
+           "h3d_batch_queue", "h3d_batch_set_wait_limit", "h3d_batch_get_queue", "h3d_batch_set_queue",
            "h3d_batch_free")
 
 
@@ -79,6 +81,9 @@ def lib():
             "h3d_export_tree": (i32, [P, P, P, P, P, P, P]),
             "h3d_export_lists": (i32, [P, P, P, P, P, P, P, P]),
             "h3d_export_pivots": (i32, [P, P, P, P]),
+            "h3d_import_pivots": (i32, [P, P, P, P, P]),
+            "h3d_set_points": (i32, [P, P, P]),
+            "h3d_debug_fail_alloc": (None, [i64]),
             "h3d_morton_order_noalloc": (i32, [P, i64, P, f64, P, P, P]),
             "h3d_energy": (i32, [P, P, P, P, P]),
             "h3d_forces": (i32, [P, P, P, P, P]),
@@ -88,6 +93,9 @@ def lib():
             "h3d_batch_configure": (i32, [P, i32, i32, i32, i32, i32]),
             "h3d_batch_info": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
             "h3d_batch_queue": (i32, [i32, P, P, P, P, i32, i32, i32, P, C.c_int64, C.POINTER(C.c_int64)]),
+            "h3d_batch_set_wait_limit": (i32, [P, i64]),
+            "h3d_batch_get_queue": (i32, [P, P, i64, C.POINTER(i64)]),
+            "h3d_batch_set_queue": (i32, [P, P, i64]),
             "h3d_batch_free": (i32, [P]),
         }
         for name, (res, args) in sig.items():
@@ -113,7 +121,7 @@ class H3DMatrix:
     """A built HODLR3D operator.  ``points``: (N, 3) float64 CUDA tensor."""
 
     def __init__(self, points, kernel: str = "laplace", leaf_size: int = 128, tol: float = 1e-7,
-                 precision: str = "fp32", rank_cap: int = 512, kappa: float = 1.0, lo=(-1.0, -1.0, -1.0),
+                 precision: str = "fp32_3xtf32", rank_cap: int = 512, kappa: float = 1.0, lo=(-1.0, -1.0, -1.0),
                  side: float = 2.0, workspace_bytes: int = 0, admissibility: str = "hodlr3d",
                  storage: str = "factors", stream=None):
         import torch
@@ -138,6 +146,7 @@ class H3DMatrix:
         if st != 0:
             raise H3DError(st, "h3d_build")
         self._h = h
+        self.points = points            # the coordinates the operator currently holds
         self.N = pts.shape[0]
         self.precision = precision
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
@@ -208,6 +217,33 @@ class H3DMatrix:
         if st != 0:
             raise H3DError(st, "h3d_forces")
         return E, F
+
+    def import_pivots(self, rank, sigma, tau, stream=None):
+        """Re-form the operator from the given ACA pivots (format of export_pivots):
+        same tree and lists, the factors formed from these pivots."""
+        r = np.ascontiguousarray(rank, np.int32)
+        sg = np.ascontiguousarray(sigma, np.int32)
+        ta = np.ascontiguousarray(tau, np.int32)
+        if sg.size != int(r.sum()) or ta.size != sg.size:
+            raise ValueError("pivot arrays do not match the ranks")
+        st = lib().h3d_import_pivots(self._h, _np(r), _np(sg) if sg.size else None, _np(ta) if ta.size else None,
+                                     _stream_ptr(stream))
+        if st != 0:
+            raise H3DError(st, "h3d_import_pivots")
+
+    def set_points(self, points, stream=None):
+        """Move the points (N x 3 float64 CUDA tensor, the caller's order), keeping
+        the tree, lists and pivots; the factors are re-formed at the new positions.
+        Costs one comparison pass when the coordinates are unchanged."""
+        import torch
+        if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float64
+                and tuple(points.shape) == (self.N, 3)):
+            raise ValueError("points must be an (N, 3) float64 CUDA tensor")
+        pts = points.detach().contiguous()
+        st = lib().h3d_set_points(self._h, pts.data_ptr(), _stream_ptr(stream))
+        if st != 0:
+            raise H3DError(st, "h3d_set_points")
+        self.points = points
 
     def matvec_raw(self, x_ptr: int, y_ptr: int, nrhs: int, stream=None, transpose: bool = False):
         """Call the C ABI directly on device pointers (column-major N x nrhs)."""
@@ -289,6 +325,12 @@ class H3DMatrix:
         return rank[:s["n_blocks"]], sig[:s["sum_rank"]], tau[:s["sum_rank"]]
 
 
+def debug_fail_alloc(after: int):
+    """Test hook: the next `after` device allocations of the library succeed and the
+    one after them fails (H3D_ERR_OOM); a negative value switches it off."""
+    lib().h3d_debug_fail_alloc(int(after))
+
+
 def batch_queue(n_points, n_gather, n_split, n_leaves, near_group=4, leaf_group=2, lag=0) -> np.ndarray:
     """The persistent batch form's work queue for operators of these sizes
     (h3d_batch_queue; host only): an (items x 4) int32 array of (operator,
@@ -368,6 +410,35 @@ class H3DBatch:
         if st != 0:
             raise H3DError(st, "h3d_batch_info")
         return {"persistent": p.value, "ctas_per_sm": c.value, "branches": b.value}
+
+    def set_wait_limit(self, ns: int):
+        """Bound of every wait of the persistent kernel, in nanoseconds."""
+        st = lib().h3d_batch_set_wait_limit(self._b, int(ns))
+        if st != 0:
+            raise H3DError(st, "h3d_batch_set_wait_limit")
+
+    def queue(self) -> np.ndarray:
+        """The persistent form's work queue, (items x 4) int32: (operator, kind, first, count)."""
+        cnt = C.c_int64()
+        st = lib().h3d_batch_get_queue(self._b, None, 0, C.byref(cnt))
+        if st != 0:
+            raise H3DError(st, "h3d_batch_get_queue")
+        out = np.zeros((max(cnt.value, 1), 4), np.int32)
+        st = lib().h3d_batch_get_queue(self._b, _np(out), cnt.value, C.byref(cnt))
+        if st != 0:
+            raise H3DError(st, "h3d_batch_get_queue")
+        return out[:cnt.value]
+
+    def set_queue(self, items=None):
+        """Run the persistent kernel on these items ((k x 4) int32), or, with None,
+        on the queue of the current settings."""
+        if items is None:
+            st = lib().h3d_batch_set_queue(self._b, None, 0)
+        else:
+            it = np.ascontiguousarray(items, np.int32).reshape(-1, 4)
+            st = lib().h3d_batch_set_queue(self._b, _np(it), it.shape[0])
+        if st != 0:
+            raise H3DError(st, "h3d_batch_set_queue")
 
     def free(self):
         if getattr(self, "_b", None) is not None and _lib is not None:

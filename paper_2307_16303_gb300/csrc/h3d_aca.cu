@@ -403,7 +403,138 @@ void run_batch(const std::vector<AcaJob> &small, const std::vector<AcaJob> &larg
 
 }  // namespace
 
-void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget) {
+namespace {
+
+// host copies of the block geometry (for batch planning)
+struct BlockGeometry {
+    std::vector<int> tgt, src, bstart, bend;
+    int m(int64_t b) const { return bend[tgt[b]] - bstart[tgt[b]]; }
+    int n(int64_t b) const { return bend[src[b]] - bstart[src[b]]; }
+};
+
+BlockGeometry block_geometry(const Handle &h, cudaStream_t s) {
+    const int64_t nblk = h.nblk, nboxes = h.n_boxes;
+    BlockGeometry g;
+    g.tgt.resize(nblk);
+    g.src.resize(nblk);
+    g.bstart.resize(nboxes);
+    g.bend.resize(nboxes);
+    if (nblk > 0) {
+        H3D_CUDA(cudaMemcpyAsync(g.tgt.data(), h.blk_tgt, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+        H3D_CUDA(cudaMemcpyAsync(g.src.data(), h.blk_src, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    H3D_CUDA(cudaMemcpyAsync(g.bstart.data(), h.box_start, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaMemcpyAsync(g.bend.data(), h.box_end, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+    H3D_CUDA(cudaStreamSynchronize(s));
+    return g;
+}
+
+constexpr int64_t kMaxJobs = 1 << 16;
+
+// pass 2: U and V of every block from its frozen pivots (same arithmetic as the
+// search), written into the final layout; U and V are cleared first (padding)
+void form_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const BlockGeometry &g,
+                  const std::vector<int> &rk, const std::vector<int64_t> &poff_h) {
+    const int64_t nblk = h.nblk;
+    const size_t es = h.elem();
+    H3D_CUDA(cudaMemsetAsync(h.U, 0, (size_t)std::max<int64_t>(h.u_elems, 4) * es, s));
+    H3D_CUDA(cudaMemsetAsync(h.V, 0, (size_t)std::max<int64_t>(h.v_elems, 4) * es, s));
+    size_t free_b = 0, total_b = 0;
+    H3D_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    int64_t ws2 = budget > 0 ? budget : std::min<int64_t>((int64_t)(free_b * 0.6), (int64_t)48 << 30);
+    int64_t dbl2 = std::max<int64_t>(ws2 / 8, (int64_t)8 << 20);
+    int64_t maxneed = 0;
+    for (int64_t b = 0; b < nblk; ++b) maxneed = std::max(maxneed, (int64_t)rk[b] * (g.m(b) + g.n(b)));
+    dbl2 = std::max(dbl2, maxneed);
+    double *scratch2 = (double *)tmp.alloc((size_t)dbl2 * 8);
+    AcaJob *d_jobs = tmp.get<AcaJob>((size_t)kMaxJobs);
+    AcaArgs A{};
+    A.px = h.px; A.py = h.py; A.pz = h.pz;
+    A.kind = h.kernel; A.kappa = h.kappa; A.tol = h.tol;
+    A.rank = h.rank; A.err = h.d_err;
+    A.scratch = scratch2; A.flags = nullptr; A.sig = h.sigma; A.tau = h.tau;
+    const int64_t offL = h.box_off[h.L];
+    PackArgs P{h.blk_tgt, h.blk_src, h.cu, h.cv, h.R, h.ldv, h.box_leaf_lo, h.leaf_ld, h.point_leaf, h.box_start,
+               h.ubase, h.vbase, h.leaf_lp, offL};
+    std::vector<AcaJob> small, large, all;
+    int mcs = 0, mcl = 0;
+    int64_t used = 0;
+    auto flush = [&]() {
+        if (small.empty() && large.empty()) return;
+        run_batch<true>(small, large, mcs, mcl, A, d_jobs, s);
+        all.clear();
+        all.insert(all.end(), small.begin(), small.end());
+        all.insert(all.end(), large.begin(), large.end());
+        if (h.prec == H3D_FP64)
+            k_pack<double><<<(unsigned)all.size(), kThreads, 0, s>>>(d_jobs, (int)all.size(), scratch2, P,
+                                                                     (double *)h.U, (double *)h.V);
+        else
+            k_pack<float><<<(unsigned)all.size(), kThreads, 0, s>>>(d_jobs, (int)all.size(), scratch2, P,
+                                                                    (float *)h.U, (float *)h.V);
+        H3D_LAUNCH_CHECK();
+        H3D_CUDA(cudaStreamSynchronize(s));
+        small.clear(); large.clear();
+        mcs = mcl = 0; used = 0;
+    };
+    for (int64_t b = 0; b < nblk; ++b) {
+        const int r = rk[b];
+        if (r == 0) continue;
+        const int m = g.m(b), n = g.n(b);
+        const int64_t need = (int64_t)r * (m + n);
+        if (used + need > dbl2 || (int64_t)(small.size() + large.size()) >= kMaxJobs) flush();
+        AcaJob J;
+        J.blk = (int)b; J.m = m; J.n = n; J.cap = r;
+        J.xs = g.bstart[g.tgt[b]]; J.ys = g.bstart[g.src[b]];
+        J.uoff = used; J.voff = used + (int64_t)r * m; J.foff = 0;
+        J.poff = poff_h[b];  // frozen pivots are read from the final arrays
+        used += need;
+        if (std::max(m, n) <= kSmallMax) { small.push_back(J); mcs = std::max(mcs, r); }
+        else { large.push_back(J); mcl = std::max(mcl, r); }
+    }
+    flush();
+    tmp.free_one(d_jobs);
+    tmp.free_one(scratch2);
+}
+
+// Pivots given by the caller: checked (0 <= r <= min(m, n, rank_cap), indices
+// inside the block, no index twice in one block) and uploaded.
+void import_pivots(Handle &h, const FrozenPivots &fp, const BlockGeometry &g, std::vector<int> &rk,
+                   std::vector<int64_t> &poff_h, cudaStream_t s) {
+    const int64_t nblk = h.nblk;
+    int maxdim = 1;
+    for (int64_t b = 0; b < nblk; ++b) maxdim = std::max(maxdim, std::max(g.m(b), g.n(b)));
+    std::vector<int64_t> seen_row((size_t)maxdim, -1), seen_col((size_t)maxdim, -1);
+    for (int64_t b = 0; b < nblk; ++b) {
+        const int r = fp.rank[b], m = g.m(b), n = g.n(b);
+        if (r < 0 || r > std::min(std::min(m, n), h.rank_cap)) fail(H3D_ERR_ARG);
+        rk[b] = r;
+        poff_h[b + 1] = poff_h[b] + r;
+        for (int64_t k = poff_h[b]; k < poff_h[b + 1]; ++k) {
+            const int i = fp.sigma[k], j = fp.tau[k];
+            if (i < 0 || i >= m || j < 0 || j >= n || seen_row[i] == b || seen_col[j] == b) fail(H3D_ERR_ARG);
+            seen_row[i] = b;
+            seen_col[j] = b;
+        }
+    }
+    h.sum_rank = poff_h[nblk];
+    if (nblk > 0) {
+        H3D_CUDA(cudaMemcpyAsync(h.rank, rk.data(), nblk * sizeof(int), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.piv_off, poff_h.data(), (nblk + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    } else {
+        H3D_CUDA(cudaMemcpyAsync(h.piv_off, poff_h.data(), sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
+    h.sigma = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
+    h.tau = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
+    if (h.sum_rank > 0) {
+        H3D_CUDA(cudaMemcpyAsync(h.sigma, fp.sigma, h.sum_rank * sizeof(int), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaMemcpyAsync(h.tau, fp.tau, h.sum_rank * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    H3D_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const FrozenPivots *fp) {
     const int64_t nblk = h.nblk, nboxes = h.n_boxes;
     const int vw = h.prec == H3D_FP64 ? 2 : 4;
     const int64_t offL = h.box_off[h.L];
@@ -411,99 +542,95 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget) {
     h.piv_off = h.mem.get<int64_t>((size_t)nblk + 1);
     H3D_CUDA(cudaMemsetAsync(h.rank, 0, sizeof(int) * (size_t)std::max<int64_t>(nblk, 1), s));
 
-    // block geometry on the host for batch planning
-    std::vector<int> tgt(nblk), src(nblk), bstart(nboxes), bend(nboxes);
-    if (nblk > 0) {
-        H3D_CUDA(cudaMemcpyAsync(tgt.data(), h.blk_tgt, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
-        H3D_CUDA(cudaMemcpyAsync(src.data(), h.blk_src, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
-    }
-    H3D_CUDA(cudaMemcpyAsync(bstart.data(), h.box_start, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
-    H3D_CUDA(cudaMemcpyAsync(bend.data(), h.box_end, nboxes * sizeof(int), cudaMemcpyDeviceToHost, s));
-    H3D_CUDA(cudaStreamSynchronize(s));
-
-    size_t free_b = 0, total_b = 0;
-    H3D_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    int64_t ws = budget > 0 ? budget : std::min<int64_t>((int64_t)(free_b * 0.45), (int64_t)48 << 30);
-    ws = std::max<int64_t>(ws, (int64_t)64 << 20);
-
-    AcaArgs A{};
-    A.px = h.px; A.py = h.py; A.pz = h.pz;
-    A.kind = h.kernel; A.kappa = h.kappa; A.tol = h.tol;
-    A.rank = h.rank; A.err = h.d_err;
-
-    // ---------------- pass 1: pivots and ranks
-    int64_t piv_slots = 0;
-    std::vector<int64_t> slot(nblk);
-    for (int64_t b = 0; b < nblk; ++b) {
-        const int m = bend[tgt[b]] - bstart[tgt[b]], n = bend[src[b]] - bstart[src[b]];
-        slot[b] = piv_slots;
-        piv_slots += std::min(std::min(m, n), h.rank_cap);
-    }
-    int *ssig = tmp.get<int>((size_t)std::max<int64_t>(piv_slots, 1));
-    int *stau = tmp.get<int>((size_t)std::max<int64_t>(piv_slots, 1));
-    const int64_t flag_ws = std::max<int64_t>(ws / 16, (int64_t)16 << 20);
-    const int64_t dbl_ws = (ws - flag_ws) / 8;
-    double *scratch = (double *)tmp.alloc((size_t)dbl_ws * 8);
-    unsigned char *flags = tmp.get<unsigned char>((size_t)flag_ws);
-    A.scratch = scratch; A.flags = flags; A.sig = ssig; A.tau = stau;
-    H3D_CUDA(cudaMemsetAsync(h.d_err, 0, sizeof(int), s));
-
-    int64_t max_jobs = 1 << 16;
-    AcaJob *d_jobs = tmp.get<AcaJob>((size_t)max_jobs);
-    {
-        std::vector<AcaJob> small, large;
-        int mcs = 0, mcl = 0;
-        int64_t used = 0, fused = 0;
-        auto flush = [&]() {
-            if (small.empty() && large.empty()) return;
-            run_batch<false>(small, large, mcs, mcl, A, d_jobs, s);
-            H3D_CUDA(cudaStreamSynchronize(s));  // job arrays are reused
-            small.clear(); large.clear();
-            mcs = mcl = 0; used = fused = 0;
-        };
-        for (int64_t b = 0; b < nblk; ++b) {
-            const int m = bend[tgt[b]] - bstart[tgt[b]], n = bend[src[b]] - bstart[src[b]];
-            const int cap = std::min(std::min(m, n), h.rank_cap);
-            const int64_t need = (int64_t)cap * (m + n);
-            if (need > dbl_ws || (int64_t)(m + n) > flag_ws) fail(H3D_ERR_OOM);
-            if (used + need > dbl_ws || fused + m + n > flag_ws ||
-                (int64_t)(small.size() + large.size()) >= max_jobs)
-                flush();
-            AcaJob J;
-            J.blk = (int)b; J.m = m; J.n = n; J.cap = cap;
-            J.xs = bstart[tgt[b]]; J.ys = bstart[src[b]];
-            J.uoff = used; J.voff = used + (int64_t)cap * m; J.foff = fused; J.poff = slot[b];
-            used += need; fused += m + n;
-            if (std::max(m, n) <= kSmallMax) { small.push_back(J); mcs = std::max(mcs, cap); }
-            else { large.push_back(J); mcl = std::max(mcl, cap); }
-        }
-        flush();
-    }
-    if (read_scalar(h.d_err, s) & (1 << H3D_ERR_ACA_RANK)) fail(H3D_ERR_ACA_RANK);
-
-    // ranks -> pivot offsets, compact pivots
+    const BlockGeometry g = block_geometry(h, s);
     std::vector<int> rk(nblk);
-    if (nblk > 0) H3D_CUDA(cudaMemcpyAsync(rk.data(), h.rank, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
-    h.sum_rank = scan_exclusive(h.rank, h.piv_off, nblk, s, tmp);
-    H3D_CUDA(cudaMemcpyAsync(h.piv_off + nblk, &h.sum_rank, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    H3D_CUDA(cudaStreamSynchronize(s));
     std::vector<int64_t> poff_h(nblk + 1, 0);
-    for (int64_t b = 0; b < nblk; ++b) poff_h[b + 1] = poff_h[b] + rk[b];
+    if (fp) {
+        import_pivots(h, *fp, g, rk, poff_h, s);
+    } else {
+        size_t free_b = 0, total_b = 0;
+        H3D_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        int64_t ws = budget > 0 ? budget : std::min<int64_t>((int64_t)(free_b * 0.45), (int64_t)48 << 30);
+        ws = std::max<int64_t>(ws, (int64_t)64 << 20);
+
+        AcaArgs A{};
+        A.px = h.px; A.py = h.py; A.pz = h.pz;
+        A.kind = h.kernel; A.kappa = h.kappa; A.tol = h.tol;
+        A.rank = h.rank; A.err = h.d_err;
+
+        // ---------------- pass 1: pivots and ranks
+        int64_t piv_slots = 0;
+        std::vector<int64_t> slot(nblk);
+        for (int64_t b = 0; b < nblk; ++b) {
+            slot[b] = piv_slots;
+            piv_slots += std::min(std::min(g.m(b), g.n(b)), h.rank_cap);
+        }
+        int *ssig = tmp.get<int>((size_t)std::max<int64_t>(piv_slots, 1));
+        int *stau = tmp.get<int>((size_t)std::max<int64_t>(piv_slots, 1));
+        const int64_t flag_ws = std::max<int64_t>(ws / 16, (int64_t)16 << 20);
+        const int64_t dbl_ws = (ws - flag_ws) / 8;
+        double *scratch = (double *)tmp.alloc((size_t)dbl_ws * 8);
+        unsigned char *flags = tmp.get<unsigned char>((size_t)flag_ws);
+        A.scratch = scratch; A.flags = flags; A.sig = ssig; A.tau = stau;
+        H3D_CUDA(cudaMemsetAsync(h.d_err, 0, sizeof(int), s));
+
+        AcaJob *d_jobs = tmp.get<AcaJob>((size_t)kMaxJobs);
+        {
+            std::vector<AcaJob> small, large;
+            int mcs = 0, mcl = 0;
+            int64_t used = 0, fused = 0;
+            auto flush = [&]() {
+                if (small.empty() && large.empty()) return;
+                run_batch<false>(small, large, mcs, mcl, A, d_jobs, s);
+                H3D_CUDA(cudaStreamSynchronize(s));  // job arrays are reused
+                small.clear(); large.clear();
+                mcs = mcl = 0; used = fused = 0;
+            };
+            for (int64_t b = 0; b < nblk; ++b) {
+                const int m = g.m(b), n = g.n(b);
+                const int cap = std::min(std::min(m, n), h.rank_cap);
+                const int64_t need = (int64_t)cap * (m + n);
+                if (need > dbl_ws || (int64_t)(m + n) > flag_ws) fail(H3D_ERR_OOM);
+                if (used + need > dbl_ws || fused + m + n > flag_ws ||
+                    (int64_t)(small.size() + large.size()) >= kMaxJobs)
+                    flush();
+                AcaJob J;
+                J.blk = (int)b; J.m = m; J.n = n; J.cap = cap;
+                J.xs = g.bstart[g.tgt[b]]; J.ys = g.bstart[g.src[b]];
+                J.uoff = used; J.voff = used + (int64_t)cap * m; J.foff = fused; J.poff = slot[b];
+                used += need; fused += m + n;
+                if (std::max(m, n) <= kSmallMax) { small.push_back(J); mcs = std::max(mcs, cap); }
+                else { large.push_back(J); mcl = std::max(mcl, cap); }
+            }
+            flush();
+        }
+        if (read_scalar(h.d_err, s) & (1 << H3D_ERR_ACA_RANK)) fail(H3D_ERR_ACA_RANK);
+
+        // ranks -> pivot offsets, compact pivots
+        if (nblk > 0) H3D_CUDA(cudaMemcpyAsync(rk.data(), h.rank, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+        h.sum_rank = scan_exclusive(h.rank, h.piv_off, nblk, s, tmp);
+        H3D_CUDA(cudaMemcpyAsync(h.piv_off + nblk, &h.sum_rank, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        H3D_CUDA(cudaStreamSynchronize(s));
+        for (int64_t b = 0; b < nblk; ++b) poff_h[b + 1] = poff_h[b] + rk[b];
+        h.sigma = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
+        h.tau = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
+        for (int64_t b0 = 0; b0 < nblk; b0 += kMaxJobs) {
+            const int64_t nb = std::min(kMaxJobs, nblk - b0);
+            std::vector<AcaJob> jobs(nb);
+            for (int64_t q = 0; q < nb; ++q) { jobs[q].blk = (int)(b0 + q); jobs[q].poff = slot[b0 + q]; }
+            H3D_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), nb * sizeof(AcaJob), cudaMemcpyHostToDevice, s));
+            k_copy_pivots<<<(unsigned)nb, 64, 0, s>>>(d_jobs, (int)nb, h.rank, h.piv_off, ssig, stau, h.sigma, h.tau);
+            H3D_LAUNCH_CHECK();
+            H3D_CUDA(cudaStreamSynchronize(s));
+        }
+        tmp.free_one(ssig);
+        tmp.free_one(stau);
+        tmp.free_one(d_jobs);
+        tmp.free_one(scratch);
+        tmp.free_one(flags);
+    }
     h.max_rank = 0;
     for (int64_t b = 0; b < nblk; ++b) h.max_rank = std::max(h.max_rank, rk[b]);
-    h.sigma = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
-    h.tau = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
-    for (int64_t b0 = 0; b0 < nblk; b0 += max_jobs) {
-        const int64_t nb = std::min(max_jobs, nblk - b0);
-        std::vector<AcaJob> jobs(nb);
-        for (int64_t q = 0; q < nb; ++q) { jobs[q].blk = (int)(b0 + q); jobs[q].poff = slot[b0 + q]; }
-        H3D_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), nb * sizeof(AcaJob), cudaMemcpyHostToDevice, s));
-        k_copy_pivots<<<(unsigned)nb, 64, 0, s>>>(d_jobs, (int)nb, h.rank, h.piv_off, ssig, stau, h.sigma, h.tau);
-        H3D_LAUNCH_CHECK();
-        H3D_CUDA(cudaStreamSynchronize(s));
-    }
-    tmp.free_one(ssig);
-    tmp.free_one(stau);
 
     // ---------------- layout
     h.R = h.mem.get<int>((size_t)nboxes);
@@ -513,6 +640,7 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget) {
     h.cv = h.mem.get<int>((size_t)std::max<int64_t>(nblk, 1));
     k_target_cols<<<gridn(nboxes), kThreads, 0, s>>>(h.tgt_ptr, h.rank, nboxes, h.R, h.cu);
     H3D_LAUNCH_CHECK();
+    H3D_CUDA(cudaMemsetAsync(h.d_err, 0, sizeof(int), s));
     k_source_cols<<<gridn(nboxes), kThreads, 0, s>>>(h.tgt_ptr, h.blk_partner, h.rank, nboxes, vw, h.Rv, h.ldv, h.cv,
                                                       h.d_err);
     H3D_LAUNCH_CHECK();
@@ -537,6 +665,8 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget) {
     h.vbase = h.mem.get<int64_t>((size_t)nboxes);
     h.u_elems = scan_exclusive(usz, h.ubase, nboxes, s, tmp);
     h.v_elems = scan_exclusive(vsz, h.vbase, nboxes, s, tmp);
+    tmp.free_one(usz);
+    tmp.free_one(vsz);
     h.map_v = h.mem.get<int64_t>((size_t)std::max<int64_t>(h.sum_rank, 1));
     if (nblk > 0) {
         k_map_v<<<gridn(nblk), kThreads, 0, s>>>(h.blk_src, h.rank, h.cv, h.vcol0, h.tofs, nblk, h.map_v);
@@ -544,12 +674,10 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget) {
     }
     h.u_entries = h.v_entries = 0;
     for (int64_t b = 0; b < nblk; ++b) {
-        h.u_entries += (int64_t)rk[b] * (bend[tgt[b]] - bstart[tgt[b]]);
-        h.v_entries += (int64_t)rk[b] * (bend[src[b]] - bstart[src[b]]);
+        h.u_entries += (int64_t)rk[b] * g.m(b);
+        h.v_entries += (int64_t)rk[b] * g.n(b);
     }
     h.factor_entries = h.u_entries + h.v_entries;
-    tmp.free_one(scratch);
-    tmp.free_one(flags);
 
     if (h.storage == H3D_STORE_SKELETON) {   // pivots and K(sigma,tau) only: no U, V
         build_skeleton(h, s, tmp);
@@ -558,62 +686,22 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget) {
     const size_t es = h.elem();
     h.U = h.mem.alloc((size_t)std::max<int64_t>(h.u_elems, 4) * es);
     h.V = h.mem.alloc((size_t)std::max<int64_t>(h.v_elems, 4) * es);
-    H3D_CUDA(cudaMemsetAsync(h.U, 0, (size_t)std::max<int64_t>(h.u_elems, 4) * es, s));
-    H3D_CUDA(cudaMemsetAsync(h.V, 0, (size_t)std::max<int64_t>(h.v_elems, 4) * es, s));
 
     // ---------------- pass 2: frozen pivots -> U, V -> final layout
-    H3D_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    int64_t ws2 = budget > 0 ? budget : std::min<int64_t>((int64_t)(free_b * 0.6), (int64_t)48 << 30);
-    int64_t dbl2 = std::max<int64_t>(ws2 / 8, (int64_t)8 << 20);
-    int64_t maxneed = 0;
-    for (int64_t b = 0; b < nblk; ++b) {
-        const int m = bend[tgt[b]] - bstart[tgt[b]], n = bend[src[b]] - bstart[src[b]];
-        maxneed = std::max(maxneed, (int64_t)rk[b] * (m + n));
+    form_factors(h, s, tmp, budget, g, rk, poff_h);
+}
+
+void reform_factors(Handle &h, cudaStream_t s, Arena &tmp) {
+    const int64_t nblk = h.nblk;
+    const BlockGeometry g = block_geometry(h, s);
+    std::vector<int> rk(nblk);
+    std::vector<int64_t> poff_h(nblk + 1, 0);
+    if (nblk > 0) {
+        H3D_CUDA(cudaMemcpyAsync(rk.data(), h.rank, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+        H3D_CUDA(cudaStreamSynchronize(s));
     }
-    dbl2 = std::max(dbl2, maxneed);
-    double *scratch2 = (double *)tmp.alloc((size_t)dbl2 * 8);
-    A.scratch = scratch2; A.flags = nullptr; A.sig = h.sigma; A.tau = h.tau;
-    PackArgs P{h.blk_tgt, h.blk_src, h.cu, h.cv, h.R, h.ldv, h.box_leaf_lo, h.leaf_ld, h.point_leaf, h.box_start,
-               h.ubase, h.vbase, h.leaf_lp, offL};
-    {
-        std::vector<AcaJob> small, large, all;
-        int mcs = 0, mcl = 0;
-        int64_t used = 0;
-        auto flush = [&]() {
-            if (small.empty() && large.empty()) return;
-            run_batch<true>(small, large, mcs, mcl, A, d_jobs, s);
-            all.clear();
-            all.insert(all.end(), small.begin(), small.end());
-            all.insert(all.end(), large.begin(), large.end());
-            if (h.prec == H3D_FP64)
-                k_pack<double><<<(unsigned)all.size(), kThreads, 0, s>>>(d_jobs, (int)all.size(), scratch2, P,
-                                                                         (double *)h.U, (double *)h.V);
-            else
-                k_pack<float><<<(unsigned)all.size(), kThreads, 0, s>>>(d_jobs, (int)all.size(), scratch2, P,
-                                                                        (float *)h.U, (float *)h.V);
-            H3D_LAUNCH_CHECK();
-            H3D_CUDA(cudaStreamSynchronize(s));
-            small.clear(); large.clear();
-            mcs = mcl = 0; used = 0;
-        };
-        for (int64_t b = 0; b < nblk; ++b) {
-            const int r = rk[b];
-            if (r == 0) continue;
-            const int m = bend[tgt[b]] - bstart[tgt[b]], n = bend[src[b]] - bstart[src[b]];
-            const int64_t need = (int64_t)r * (m + n);
-            if (used + need > dbl2 || (int64_t)(small.size() + large.size()) >= max_jobs) flush();
-            AcaJob J;
-            J.blk = (int)b; J.m = m; J.n = n; J.cap = r;
-            J.xs = bstart[tgt[b]]; J.ys = bstart[src[b]];
-            J.uoff = used; J.voff = used + (int64_t)r * m; J.foff = 0;
-            J.poff = poff_h[b];  // frozen pivots are read from the final arrays
-            used += need;
-            if (std::max(m, n) <= kSmallMax) { small.push_back(J); mcs = std::max(mcs, r); }
-            else { large.push_back(J); mcl = std::max(mcl, r); }
-        }
-        flush();
-    }
-    tmp.free_one(scratch2);
+    for (int64_t b = 0; b < nblk; ++b) poff_h[b + 1] = poff_h[b] + rk[b];
+    form_factors(h, s, tmp, h.budget, g, rk, poff_h);
 }
 
 }  // namespace h3d

@@ -10,8 +10,11 @@
 
 using h3d::Handle;
 
+// The handle owns its Handle through a pointer, so that h3d_import_pivots can
+// build a replacement and swap it in only once that build has succeeded.
 struct h3d_handle_s {
-    Handle h;
+    Handle *p = nullptr;
+    ~h3d_handle_s() { delete p; }
 };
 
 namespace {
@@ -45,7 +48,7 @@ extern "C" {
 
 void h3d_default_options(h3d_options *opt) {
     if (!opt) return;
-    opt->precision = H3D_FP32;
+    opt->precision = H3D_FP32_3XTF32;
     opt->kappa = 1.0;
     opt->rank_cap = h3d::kMaxRank;
     opt->lo[0] = opt->lo[1] = opt->lo[2] = -1.0;
@@ -70,39 +73,12 @@ const char *h3d_status_string(h3d_status s) {
     return "unknown status";
 }
 
-h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int leaf_size, double tol,
-                     const h3d_options *opt, void *stream, h3d_handle *out) {
-    if (!out || !points || N < 1 || N >= (int64_t)1 << 31) return H3D_ERR_ARG;
-    if (leaf_size < 1 || leaf_size > h3d::kMaxLeaf || !(tol >= 0.0) || !std::isfinite(tol)) return H3D_ERR_ARG;
-    if ((int)kernel < 0 || (int)kernel > 3) return H3D_ERR_ARG;
-    h3d_options o;
-    h3d_default_options(&o);
-    if (opt) o = *opt;
-    if (o.precision != H3D_FP32 && o.precision != H3D_FP64) return H3D_ERR_ARG;
-    if (o.rank_cap < 1 || o.rank_cap > h3d::kMaxRank) return H3D_ERR_ARG;
-    if (!(o.side > 0.0) || !std::isfinite(o.side)) return H3D_ERR_ARG;
-    for (int d = 0; d < 3; ++d)
-        if (!std::isfinite(o.lo[d])) return H3D_ERR_ARG;
-    if (!(o.kappa >= 0.0) || !std::isfinite(o.kappa)) return H3D_ERR_ARG;
-    if (o.admissibility < H3D_ADM_HODLR3D || o.admissibility > H3D_ADM_WEAK) return H3D_ERR_ARG;
-    if (o.storage != H3D_STORE_FACTORS && o.storage != H3D_STORE_SKELETON) return H3D_ERR_ARG;
-    if (!is_device_ptr(points)) return H3D_ERR_ARG;
+namespace {
 
-    h3d_handle_s *hs = new (std::nothrow) h3d_handle_s;
-    if (!hs) return H3D_ERR_OOM;
-    Handle &h = hs->h;
-    h.N = N;
-    h.kernel = kernel;
-    h.prec = o.precision;
-    h.leaf_size = leaf_size;
-    h.rank_cap = o.rank_cap;
-    h.adm = o.admissibility;
-    h.storage = o.storage;
-    h.tol = tol;
-    h.kappa = o.kappa;
-    h.side = o.side;
-    for (int d = 0; d < 3; ++d) h.lo[d] = o.lo[d];
-    cudaStream_t s = as_stream(stream);
+// Everything the build computes, into the parameters already set in h: tree,
+// lists, ACA (pivots searched, or the caller's when fp is given), factor layout
+// and product plan.  Synchronises s.
+h3d_status build_into(Handle &h, const double *points, cudaStream_t s, const h3d::FrozenPivots *fp) {
     const auto t0 = std::chrono::steady_clock::now();
     h3d_status st = guard([&] {
         h3d::Arena tmp;
@@ -112,30 +88,102 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
         H3D_CUDA(cudaHostGetDevicePointer((void **)&h.d_async_err, h.h_async_err, 0));
         h3d::build_tree(h, points, s, tmp);
         h3d::build_lists(h, s, tmp);
-        h3d::build_factors(h, s, tmp, o.workspace_bytes);
+        h3d::build_factors(h, s, tmp, h.budget, fp);
         h3d::build_matvec_plan(h, s, tmp);
         H3D_CUDA(cudaStreamSynchronize(s));
     });
     if (st != H3D_OK) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
-        delete hs;
         return st;
     }
     h.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     h.ok = true;
+    return H3D_OK;
+}
+
+// a new Handle with the parameters of h (nothing built)
+Handle *same_parameters(const Handle &h) {
+    Handle *n = new (std::nothrow) Handle;
+    if (!n) return nullptr;
+    n->N = h.N;
+    n->kernel = h.kernel;
+    n->prec = h.prec;
+    n->tf32 = h.tf32;
+    n->leaf_size = h.leaf_size;
+    n->rank_cap = h.rank_cap;
+    n->adm = h.adm;
+    n->storage = h.storage;
+    n->budget = h.budget;
+    n->tol = h.tol;
+    n->kappa = h.kappa;
+    n->side = h.side;
+    for (int d = 0; d < 3; ++d) n->lo[d] = h.lo[d];
+    return n;
+}
+
+}  // namespace
+
+h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int leaf_size, double tol,
+                     const h3d_options *opt, void *stream, h3d_handle *out) {
+    if (!out || !points || N < 1 || N >= (int64_t)1 << 31) return H3D_ERR_ARG;
+    if (leaf_size < 1 || leaf_size > h3d::kMaxLeaf || !(tol >= 0.0) || !std::isfinite(tol)) return H3D_ERR_ARG;
+    if ((int)kernel < 0 || (int)kernel > 3) return H3D_ERR_ARG;
+    h3d_options o;
+    h3d_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != H3D_FP32 && o.precision != H3D_FP64 && o.precision != H3D_FP32_3XTF32) return H3D_ERR_ARG;
+    if (o.rank_cap < 1 || o.rank_cap > h3d::kMaxRank) return H3D_ERR_ARG;
+    if (!(o.side > 0.0) || !std::isfinite(o.side)) return H3D_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(o.lo[d])) return H3D_ERR_ARG;
+    if (!(o.kappa >= 0.0) || !std::isfinite(o.kappa)) return H3D_ERR_ARG;
+    if (o.admissibility < H3D_ADM_HODLR3D || o.admissibility > H3D_ADM_WEAK) return H3D_ERR_ARG;
+    if (o.storage != H3D_STORE_FACTORS && o.storage != H3D_STORE_SKELETON) return H3D_ERR_ARG;
+    if (o.workspace_bytes < 0) return H3D_ERR_ARG;
+    if (!is_device_ptr(points)) return H3D_ERR_ARG;
+
+    h3d_handle_s *hs = new (std::nothrow) h3d_handle_s;
+    if (!hs) return H3D_ERR_OOM;
+    hs->p = new (std::nothrow) Handle;
+    if (!hs->p) {
+        delete hs;
+        return H3D_ERR_OOM;
+    }
+    Handle &h = *hs->p;
+    h.N = N;
+    h.kernel = kernel;
+    h.prec = o.precision == H3D_FP64 ? H3D_FP64 : H3D_FP32;
+    h.tf32 = o.precision == H3D_FP32_3XTF32;
+    h.leaf_size = leaf_size;
+    h.rank_cap = o.rank_cap;
+    h.adm = o.admissibility;
+    h.storage = o.storage;
+    h.budget = o.workspace_bytes;
+    h.tol = tol;
+    h.kappa = o.kappa;
+    h.side = o.side;
+    for (int d = 0; d < 3; ++d) h.lo[d] = o.lo[d];
+    const h3d_status st = build_into(h, points, as_stream(stream), nullptr);
+    if (st != H3D_OK) {
+        delete hs;
+        return st;
+    }
     *out = hs;
     return H3D_OK;
 }
 
+// The status a product kernel left in the handle's error word (a bounded wait
+// that gave up), reported once: reading it clears it.
 static h3d_status async_error(const Handle &h) {
-    const int e = *(volatile int *)h.h_async_err;
+    if (*(volatile int *)h.h_async_err == 0) return H3D_OK;
+    const int e = __atomic_exchange_n(h.h_async_err, 0, __ATOMIC_SEQ_CST);
     return e ? (h3d_status)e : H3D_OK;
 }
 
 static h3d_status matvec_common(h3d_handle hh, const void *x, void *y, int nrhs, void *stream, bool transpose) {
     if (!hh) return H3D_ERR_ARG;
-    Handle &h = hh->h;
+    Handle &h = *hh->p;
     if (!h.ok) return H3D_ERR_STATE;
     if (h3d_status e = async_error(h)) return e;
     if (!x || !y || nrhs < 1 || x == y) return H3D_ERR_ARG;
@@ -152,7 +200,7 @@ h3d_status h3d_matvec_T(h3d_handle h, const void *x, void *y, int nrhs, void *st
 
 h3d_status h3d_energy(h3d_handle hh, const void *q, double *E, void *grad, void *stream) {
     if (!hh) return H3D_ERR_ARG;
-    Handle &h = hh->h;
+    Handle &h = *hh->p;
     if (!h.ok) return H3D_ERR_STATE;
     if (h3d_status e = async_error(h)) return e;
     if (!q || !E || q == grad) return H3D_ERR_ARG;
@@ -161,7 +209,7 @@ h3d_status h3d_energy(h3d_handle hh, const void *q, double *E, void *grad, void 
 
 h3d_status h3d_forces(h3d_handle hh, const void *q, double *E, double *F, void *stream) {
     if (!hh) return H3D_ERR_ARG;
-    Handle &h = hh->h;
+    Handle &h = *hh->p;
     if (!h.ok) return H3D_ERR_STATE;
     if (h3d_status e = async_error(h)) return e;
     if (!q || !E || !F) return H3D_ERR_ARG;
@@ -170,8 +218,9 @@ h3d_status h3d_forces(h3d_handle hh, const void *q, double *E, double *F, void *
 
 h3d_status h3d_matvec_host(h3d_handle hh, const void *x_host, void *y_host, int nrhs, void *stream) {
     if (!hh) return H3D_ERR_ARG;
-    Handle &h = hh->h;
+    Handle &h = *hh->p;
     if (!h.ok) return H3D_ERR_STATE;
+    if (h3d_status e = async_error(h)) return e;
     if (!x_host || !y_host || nrhs < 1) return H3D_ERR_ARG;
     cudaStream_t s = as_stream(stream);
     return guard([&] {
@@ -196,7 +245,7 @@ h3d_status h3d_matvec_host(h3d_handle hh, const void *x_host, void *y_host, int 
 h3d_status h3d_matvec_profile(h3d_handle hh, const void *x, void *y, int nrhs, void *stream, float *phase_ms,
                               int nphase) {
     if (!hh || !phase_ms || nphase < 1) return H3D_ERR_ARG;
-    Handle &h = hh->h;
+    Handle &h = *hh->p;
     if (!h.ok) return H3D_ERR_STATE;
     if (h.storage == H3D_STORE_SKELETON) return H3D_ERR_ARG;   // phases of the factor-streaming product only
     if (!x || !y || nrhs < 1 || x == y) return H3D_ERR_ARG;
@@ -221,6 +270,8 @@ h3d_status h3d_matvec_profile(h3d_handle hh, const void *x, void *y, int nrhs, v
     return st;
 }
 
+void h3d_debug_fail_alloc(int64_t after) { h3d::fail_alloc_countdown() = after < 0 ? -1 : after; }
+
 h3d_status h3d_free(h3d_handle hh) {
     if (!hh) return H3D_OK;
     cudaDeviceSynchronize();
@@ -230,12 +281,12 @@ h3d_status h3d_free(h3d_handle hh) {
 
 h3d_status h3d_get_stats(h3d_handle hh, h3d_stats *st) {
     if (!hh || !st) return H3D_ERR_ARG;
-    const Handle &h = hh->h;
+    const Handle &h = *hh->p;
     if (!h.ok) return H3D_ERR_STATE;
     std::memset(st, 0, sizeof(*st));
     st->N = h.N;
     st->depth = h.L;
-    st->precision = h.prec;
+    st->precision = h.tf32 ? H3D_FP32_3XTF32 : h.prec;
     st->kernel = h.kernel;
     st->leaf_size = h.leaf_size;
     st->tol = h.tol;
@@ -265,7 +316,7 @@ h3d_status h3d_get_stats(h3d_handle hh, h3d_stats *st) {
 h3d_status h3d_export_tree(h3d_handle hh, int64_t *perm, uint64_t *keys, int *nbox, uint64_t *box_key,
                            int64_t *box_start, int64_t *box_end) {
     if (!hh || !perm || !keys || !nbox || !box_key || !box_start || !box_end) return H3D_ERR_ARG;
-    const Handle &h = hh->h;
+    const Handle &h = *hh->p;
     if (!h.ok) return H3D_ERR_STATE;
     return guard([&] {
         const size_t n = (size_t)h.N, nb = (size_t)h.n_boxes;
@@ -284,7 +335,7 @@ h3d_status h3d_export_tree(h3d_handle hh, int64_t *perm, uint64_t *keys, int *nb
 h3d_status h3d_export_lists(h3d_handle hh, int *blk_level, int *blk_tgt, int *blk_src, int *blk_cls, int *near_tgt,
                             int *near_src, int *near_cls) {
     if (!hh) return H3D_ERR_ARG;
-    const Handle &h = hh->h;
+    const Handle &h = *hh->p;
     if (!h.ok) return H3D_ERR_STATE;
     if (h.nblk > 0 && (!blk_level || !blk_tgt || !blk_src || !blk_cls)) return H3D_ERR_ARG;
     if (!near_tgt || !near_src || !near_cls) return H3D_ERR_ARG;
@@ -315,7 +366,7 @@ h3d_status h3d_export_lists(h3d_handle hh, int *blk_level, int *blk_tgt, int *bl
 
 h3d_status h3d_export_pivots(h3d_handle hh, int *rank, int *sigma, int *tau) {
     if (!hh) return H3D_ERR_ARG;
-    const Handle &h = hh->h;
+    const Handle &h = *hh->p;
     if (!h.ok) return H3D_ERR_STATE;
     if ((h.nblk > 0 && !rank) || (h.sum_rank > 0 && (!sigma || !tau))) return H3D_ERR_ARG;
     return guard([&] {
@@ -325,6 +376,62 @@ h3d_status h3d_export_pivots(h3d_handle hh, int *rank, int *sigma, int *tau) {
             H3D_CUDA(cudaMemcpy(tau, h.tau, (size_t)h.sum_rank * sizeof(int), cudaMemcpyDeviceToHost));
         }
     });
+}
+
+h3d_status h3d_import_pivots(h3d_handle hh, const int *rank, const int *sigma, const int *tau, void *stream) {
+    if (!hh) return H3D_ERR_ARG;
+    Handle &h = *hh->p;
+    if (!h.ok) return H3D_ERR_STATE;
+    if (h3d_status e = async_error(h)) return e;
+    if (h.nblk > 0 && !rank) return H3D_ERR_ARG;
+    int64_t total = 0;
+    for (int64_t b = 0; b < h.nblk; ++b) {
+        if (rank[b] < 0) return H3D_ERR_ARG;
+        total += rank[b];
+    }
+    if (total > 0 && (!sigma || !tau)) return H3D_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    Handle *n = same_parameters(h);
+    if (!n) return H3D_ERR_OOM;
+    // the same points in the caller's order, from the handle's sorted copy: the
+    // new build reproduces the tree and the lists bit for bit
+    double *pts = nullptr;
+    h3d_status st = guard([&] {
+        H3D_CUDA(cudaStreamSynchronize(s));
+        H3D_CUDA(cudaMalloc((void **)&pts, (size_t)h.N * 3 * sizeof(double)));
+        h3d::unsorted_points(h, pts, s);
+    });
+    if (st == H3D_OK) {
+        const h3d::FrozenPivots fp{rank, sigma, tau};
+        st = build_into(*n, pts, s, &fp);
+    }
+    if (pts) cudaFree(pts);
+    if (st != H3D_OK) {
+        delete n;
+        return st;
+    }
+    cudaDeviceSynchronize();   // nothing may still use the old handle's memory
+    delete hh->p;
+    hh->p = n;
+    return H3D_OK;
+}
+
+h3d_status h3d_set_points(h3d_handle hh, const double *points, void *stream) {
+    if (!hh || !points) return H3D_ERR_ARG;
+    Handle &h = *hh->p;
+    if (!h.ok) return H3D_ERR_STATE;
+    if (h3d_status e = async_error(h)) return e;
+    if (!is_device_ptr(points)) return H3D_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    const h3d_status st = guard([&] {
+        h3d::Arena tmp;
+        if (!h3d::update_points(h, points, s, tmp)) return;   // the same coordinates: nothing to re-form
+        if (h.storage == H3D_STORE_SKELETON) h3d::refactor_skeleton(h, s);
+        else h3d::reform_factors(h, s, tmp);
+        H3D_CUDA(cudaStreamSynchronize(s));
+    });
+    if (st != H3D_OK && st != H3D_ERR_DOMAIN) h.ok = false;   // factors may be half re-formed
+    return st;
 }
 
 }  // extern "C"
@@ -399,7 +506,7 @@ void batch_capture(h3d_batch_s &B, const void *const *x, void *const *y, int nb)
     try {
         H3D_CUDA(cudaEventRecord(B.fork, B.cap));
         for (int b = 0; b < nb; ++b) H3D_CUDA(cudaStreamWaitEvent(B.st[b], B.fork, 0));
-        for (size_t i = 0; i < B.hs.size(); ++i) h3d::run_matvec(B.hs[i]->h, x[i], y[i], 1, false, B.st[owner[i]]);
+        for (size_t i = 0; i < B.hs.size(); ++i) h3d::run_matvec(*B.hs[i]->p, x[i], y[i], 1, false, B.st[owner[i]]);
         for (int b = 0; b < nb; ++b) {
             H3D_CUDA(cudaEventRecord(B.join[b], B.st[b]));
             H3D_CUDA(cudaStreamWaitEvent(B.cap, B.join[b], 0));
@@ -421,7 +528,7 @@ void batch_capture(h3d_batch_s &B, const void *const *x, void *const *y, int nb)
 h3d_status batch_check(h3d_batch B, const void *const *x, void *const *y) {
     if (!B || !x || !y) return H3D_ERR_ARG;
     for (size_t i = 0; i < B->hs.size(); ++i) {
-        const Handle &h = B->hs[i]->h;
+        const Handle &h = *B->hs[i]->p;
         if (!h.ok) return H3D_ERR_STATE;
         if (h3d_status e = async_error(h)) return e;
         if (!x[i] || !y[i] || x[i] == y[i]) return H3D_ERR_ARG;
@@ -468,7 +575,7 @@ extern "C" {
 h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out) {
     if (!handles || count < 1 || !out) return H3D_ERR_ARG;
     for (int i = 0; i < count; ++i) {
-        if (!handles[i] || !handles[i]->h.ok) return H3D_ERR_ARG;
+        if (!handles[i] || !handles[i]->p->ok) return H3D_ERR_ARG;
         for (int j = 0; j < i; ++j)   // a handle's scratch serves one product at a time
             if (handles[j] == handles[i]) return H3D_ERR_ARG;
     }
@@ -477,14 +584,14 @@ h3d_status h3d_batch_create(const h3d_handle *handles, int count, h3d_batch *out
     const h3d_status st = guard([&] {
         B->hs.assign(handles, handles + count);
         for (int i = 0; i < count; ++i) {   // work estimate: factor entries plus the near field
-            const Handle &h = handles[i]->h;
+            const Handle &h = *handles[i]->p;
             B->cost.push_back(h.factor_entries + h.N * 32);
         }
         B->branches = std::min(count, 8);
         H3D_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
         H3D_CUDA(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
         std::vector<Handle *> hv;
-        for (int i = 0; i < count; ++i) hv.push_back(&handles[i]->h);
+        for (int i = 0; i < count; ++i) hv.push_back(handles[i]->p);
         B->plan = h3d::batch_plan_create(hv, kDefaultNearGroup, kDefaultLeafGroup, kDefaultLag);
         if (B->plan) {
             B->persistent = true;
@@ -574,6 +681,29 @@ h3d_status h3d_batch_configure(h3d_batch B, int persistent, int ctas_per_sm, int
                   lo2 = lag >= 0 ? lag : lo;
         if (ng2 != ng || lg2 != lg || lo2 != lo) h3d::batch_plan_regroup(*B->plan, ng2, lg2, lo2);
     });
+}
+
+h3d_status h3d_batch_set_wait_limit(h3d_batch B, int64_t ns) {
+    if (!B || ns < 1000 || ns > (int64_t)60 * 1000000000LL) return H3D_ERR_ARG;
+    if (!B->plan) return H3D_OK;
+    return guard([&] { h3d::batch_plan_set_wait(*B->plan, (long long)ns); });
+}
+
+h3d_status h3d_batch_set_queue(h3d_batch B, const int *items, int64_t count) {
+    if (!B || !B->plan || (items && count < 1) || count < 0) return H3D_ERR_ARG;
+    h3d_status st = H3D_OK;
+    const h3d_status g = guard([&] {
+        if (!h3d::batch_plan_set_queue(*B->plan, items, count)) st = H3D_ERR_ARG;
+    });
+    return g != H3D_OK ? g : st;
+}
+
+h3d_status h3d_batch_get_queue(h3d_batch B, int *items, int64_t cap, int64_t *count) {
+    if (!B || !B->plan || !count || cap < 0) return H3D_ERR_ARG;
+    h3d::batch_plan_get_queue(*B->plan, nullptr, 0, count);
+    if (items && cap < *count) return H3D_ERR_ARG;
+    if (items) h3d::batch_plan_get_queue(*B->plan, items, cap, count);
+    return H3D_OK;
 }
 
 h3d_status h3d_batch_info(h3d_batch B, int *persistent, int *ctas_per_sm, int *branches) {

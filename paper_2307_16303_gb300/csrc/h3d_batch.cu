@@ -21,10 +21,10 @@
 // waits on its operator's completion counters: G and N wait for every P of the
 // operator, R for every G, L for every G, R and N.  Items wait only on items
 // that sit earlier in the queue and so were taken by CTAs that are already
-// running; every wait therefore ends.  Each is still bounded
-// (kWaitCycles): a CTA that gives up records H3D_ERR_TIMEOUT in the operator's
-// error word, raises the batch's abort flag (on which the other CTAs stop) and
-// leaves.
+// running; every wait therefore ends.  Each is still bounded (by a limit in
+// nanoseconds of the GPU's global timer, 2 s unless the caller sets another):
+// a CTA that gives up records H3D_ERR_TIMEOUT in the operator's error word,
+// raises the batch's abort flag (on which the other CTAs stop) and leaves.
 //
 // Visibility: a finished item's CTA synchronises, then one thread fences at GPU
 // scope and adds 1 to the counter; a waiting thread reads the counter with an
@@ -87,6 +87,7 @@ struct BatchArgs {
     int *abort;
     int4 *done;                // per operator: finished (G, R, N, P) items
     const void *const *xy;     // per operator: x, y (device pointers)
+    long long wait_ns;         // bound of every wait on a completion counter
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -95,13 +96,19 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     return v;
 }
 
-// true once *cnt >= target; false on abort or after kWaitCycles
-__device__ bool wait_count(const int *cnt, int target, const int *abort) {
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+// true once *cnt >= target; false on abort or after wait_ns nanoseconds
+__device__ bool wait_count(const int *cnt, int target, const int *abort, long long wait_ns) {
     if (ld_acquire(cnt) >= target) return true;
-    const long long t0 = clock64();
+    const long long t0 = global_ns();
     while (ld_acquire(cnt) < target) {
         if (ld_acquire(abort)) return false;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (global_ns() - t0 > wait_ns) return false;
         __nanosleep(128);
     }
     return true;
@@ -138,11 +145,12 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchCtasPerSm) k_batch(BatchA
             s_next[(iter + 1) & 1] = atomicAdd(B.head, 1);
             bool ok = true;
             const BatchOp &G = B.ops[I.x];
-            if (I.y == kItemGather || I.y == kItemNear) ok = wait_count(&done->w, G.nperm, B.abort);
-            else if (I.y == kItemReduce) ok = wait_count(&done->x, G.ngtask, B.abort);
+            const long long lim = B.wait_ns;
+            if (I.y == kItemGather || I.y == kItemNear) ok = wait_count(&done->w, G.nperm, B.abort, lim);
+            else if (I.y == kItemReduce) ok = wait_count(&done->x, G.ngtask, B.abort, lim);
             else if (I.y == kItemLeaf)
-                ok = wait_count(&done->x, G.ngtask, B.abort) && wait_count(&done->y, G.nsplit, B.abort) &&
-                     wait_count(&done->z, G.nnear, B.abort);
+                ok = wait_count(&done->x, G.ngtask, B.abort, lim) && wait_count(&done->y, G.nsplit, B.abort, lim) &&
+                     wait_count(&done->z, G.nnear, B.abort, lim);
             if (!ok) {
                 if (!ld_acquire(B.abort)) atomicCAS(G.A.err, 0, (int)H3D_ERR_TIMEOUT);
                 atomicExch(B.abort, 1);
@@ -217,6 +225,9 @@ struct BatchPlan {
     void *d_ops = nullptr, *d_items = nullptr, *d_xy = nullptr;
     int *d_state = nullptr;                  // head, abort, pad, pad, then done[nops] (int4 each)
     int nitems = 0;
+    std::vector<int4> items;                 // the queue on the device
+    bool custom = false;                     // queue given by the caller (batch_plan_set_queue)
+    long long wait_ns = 2000000000LL;        // bound of every wait (2 s)
     std::vector<const void *> xy;            // the pointers last copied to d_xy
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -306,16 +317,25 @@ std::vector<int4> batch_queue(const std::vector<QueueCounts> &c, int near_group,
     return items;
 }
 
-void build_items(BatchPlan &p) {
-    std::vector<QueueCounts> c;
-    for (const Handle *h : p.hs) c.push_back(QueueCounts{h->N, h->ngtask, h->nsplit, h->nleaf});
-    const std::vector<int4> items = batch_queue(c, p.near_group, p.leaf_group, p.lag);
-    p.nitems = (int)items.size();
-    p.d_items = upload(p, p.d_items, items);
+void drop_graph(BatchPlan &p) {
     if (p.exec) {
         H3D_CUDA(cudaGraphExecDestroy(p.exec));
         p.exec = nullptr;
     }
+}
+
+void set_items(BatchPlan &p, const std::vector<int4> &items) {
+    p.items = items;
+    p.nitems = (int)items.size();
+    p.d_items = upload(p, p.d_items, items);
+    drop_graph(p);
+}
+
+void build_items(BatchPlan &p) {
+    std::vector<QueueCounts> c;
+    for (const Handle *h : p.hs) c.push_back(QueueCounts{h->N, h->ngtask, h->nsplit, h->nleaf});
+    set_items(p, batch_queue(c, p.near_group, p.leaf_group, p.lag));
+    p.custom = false;
 }
 
 }  // namespace
@@ -369,6 +389,49 @@ void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group, int lag) {
     build_items(p);
 }
 
+bool batch_plan_set_queue(BatchPlan &p, const int *items, int64_t count) {
+    if (!items) {   // back to the queue of the current settings
+        build_items(p);
+        return true;
+    }
+    std::vector<int4> q;
+    for (int64_t k = 0; k < count; ++k) {
+        const int4 it = make_int4(items[4 * k], items[4 * k + 1], items[4 * k + 2], items[4 * k + 3]);
+        if (it.x < 0 || it.x >= p.nops) return false;
+        const Handle &h = *p.hs[it.x];
+        bool ok = false;
+        switch (it.y) {
+        case kItemGather: ok = it.z >= 0 && it.z < h.ngtask; break;
+        case kItemReduce: ok = it.z >= 0 && it.z < h.nsplit; break;
+        case kItemNear:
+        case kItemLeaf: ok = it.z >= 0 && it.w >= 1 && (int64_t)it.z + it.w <= h.nleaf; break;
+        case kItemPerm: ok = it.z >= 0 && it.z < h.N; break;
+        default: ok = false;
+        }
+        if (!ok) return false;
+        q.push_back(it);
+    }
+    set_items(p, q);
+    p.custom = true;
+    return true;
+}
+
+void batch_plan_get_queue(const BatchPlan &p, int *items, int64_t cap, int64_t *count) {
+    *count = (int64_t)p.items.size();
+    if (!items) return;
+    for (int64_t k = 0; k < std::min<int64_t>(cap, (int64_t)p.items.size()); ++k) {
+        items[4 * k] = p.items[k].x;
+        items[4 * k + 1] = p.items[k].y;
+        items[4 * k + 2] = p.items[k].z;
+        items[4 * k + 3] = p.items[k].w;
+    }
+}
+
+void batch_plan_set_wait(BatchPlan &p, long long ns) {
+    p.wait_ns = ns;
+    drop_graph(p);
+}
+
 void batch_plan_groups(const BatchPlan &p, int *near_group, int *leaf_group, int *lag) {
     *near_group = p.near_group;
     *leaf_group = p.leaf_group;
@@ -402,7 +465,7 @@ void batch_plan_run(BatchPlan &p, const void *const *x, void *const *y, int ctas
         }
         int *st = p.d_state;
         BatchArgs a{static_cast<const BatchOp *>(p.d_ops), static_cast<const int4 *>(p.d_items), p.nitems, st, st + 1,
-                    reinterpret_cast<int4 *>(st + 4), static_cast<const void *const *>(p.d_xy)};
+                    reinterpret_cast<int4 *>(st + 4), static_cast<const void *const *>(p.d_xy), p.wait_ns};
         const int grid = std::max(1, std::min(p.nitems, ctas_per_sm * num_sms()));
         cudaGraph_t g = nullptr;
         H3D_CUDA(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeThreadLocal));

@@ -54,9 +54,9 @@ void energy(Handle &h, const void *q, double *E, void *grad, cudaStream_t s) {
     const size_t es = h.elem();
     if (!h.ey) {   // scratch kept by the handle: A~ q, A~^T q, partial sums
         H3D_CUDA(cudaStreamSynchronize(s));
-        h.ey = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * es);
-        h.eyT = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * es);
-        h.epart = h.mem.get<double>(kEnergyBlocks);
+        alloc_all(h.mem, {{&h.ey, (size_t)std::max<int64_t>(h.N, 4) * es},
+                          {&h.eyT, (size_t)std::max<int64_t>(h.N, 4) * es},
+                          {(void **)&h.epart, kEnergyBlocks * sizeof(double)}});
     }
     run_matvec(h, q, h.ey, 1, false, s);
     if (grad) run_matvec(h, q, h.eyT, 1, true, s);

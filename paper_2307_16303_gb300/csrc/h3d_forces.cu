@@ -505,14 +505,18 @@ void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s) {
     const bool fp32 = h.prec != H3D_FP64;
     if (!h.fG) {   // scratch kept by the handle
         H3D_CUDA(cudaStreamSynchronize(s));
-        h.fqs = h.mem.get<double>((size_t)std::max<int64_t>(h.N, 1));
-        h.fG = h.mem.get<double>((size_t)std::max<int64_t>(h.N, 1) * 3);
-        h.fE = h.mem.get<double>((size_t)std::max<int64_t>(nparts, 1) + 1024);
-        h.fM = h.mem.get<double>((size_t)grid * std::max(1, h.max_rank) * std::max(1, h.max_rank));
-        h.fctr = h.mem.get<int>(1);
+        const size_t n1 = (size_t)std::max<int64_t>(h.N, 1), mr = (size_t)std::max(1, h.max_rank);
+        void *ph = nullptr, *pl = nullptr;
+        alloc_all(h.mem, {{(void **)&h.fqs, n1 * sizeof(double)},
+                          {(void **)&h.fE, ((size_t)std::max<int64_t>(nparts, 1) + 1024) * sizeof(double)},
+                          {(void **)&h.fM, (size_t)grid * mr * mr * sizeof(double)},
+                          {(void **)&h.fctr, sizeof(int)},
+                          {&ph, fp32 ? n1 * sizeof(float4) : 16},
+                          {&pl, fp32 ? n1 * sizeof(float4) : 16},
+                          {(void **)&h.fG, n1 * 3 * sizeof(double)}});   // fG last: it marks the scratch as made
         if (fp32) {
-            h.fph = h.mem.get<float4>((size_t)std::max<int64_t>(h.N, 1));
-            h.fpl = h.mem.get<float4>((size_t)std::max<int64_t>(h.N, 1));
+            h.fph = static_cast<float4 *>(ph);
+            h.fpl = static_cast<float4 *>(pl);
         }
     }
     const int64_t N = h.N;

@@ -22,6 +22,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <initializer_list>
 #include <vector>
 
 #include "../../include/h3d.h"
@@ -62,11 +63,21 @@ struct DevMem {
     size_t bytes = 0;
 };
 
+// Allocation-failure injection for tests (h3d_debug_fail_alloc): when >= 0,
+// the number of device allocations that still succeed before one fails.
+int64_t &fail_alloc_countdown();
+
 class Arena {
   public:
     ~Arena() { release(); }
     void *alloc(size_t bytes) {
         if (bytes == 0) bytes = 16;
+        int64_t &cd = fail_alloc_countdown();
+        if (cd == 0) {
+            cd = -1;
+            fail(H3D_ERR_OOM);
+        }
+        if (cd > 0) --cd;
         void *p = nullptr;
         cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) {
@@ -100,6 +111,25 @@ class Arena {
     size_t total_ = 0;
 };
 
+// Scratch a call allocates on first use: every request is made, or, if one
+// fails, the ones already made are released and the error is passed on (so a
+// later call never finds the scratch half allocated).
+struct AllocReq {
+    void **dst;
+    size_t bytes;
+};
+inline void alloc_all(Arena &m, std::initializer_list<AllocReq> req) {
+    std::vector<void *> got;
+    try {
+        for (const AllocReq &r : req) got.push_back(m.alloc(r.bytes));
+    } catch (...) {
+        for (void *p : got) m.free_one(p);
+        throw;
+    }
+    size_t i = 0;
+    for (const AllocReq &r : req) *r.dst = got[i++];
+}
+
 // ----------------------------------------------------------------------------
 // the handle
 // One tensor-core gather work item: rows [r0, r0 + nrows) of source box Y's V
@@ -118,6 +148,8 @@ struct Handle {
     int64_t N = 0;
     int kernel = H3D_LAPLACE, prec = H3D_FP32, leaf_size = 0, rank_cap = kMaxRank, adm = H3D_ADM_HODLR3D;
     int storage = H3D_STORE_FACTORS;
+    bool tf32 = false;            // H3D_FP32_3XTF32: products of more than 8 columns on the tensor cores
+    int64_t budget = 0;           // build workspace budget (h3d_options.workspace_bytes)
     // skeleton storage: per block the LU of K(sigma,tau) (row-major, L unit lower,
     // at lu_off[b]) and its row order (at piv_off[b]); product scratch per block
     double *lu = nullptr;
@@ -333,10 +365,26 @@ T read_scalar(const T *d, cudaStream_t s) {
 }
 int num_sms();
 
+// Pivots given by the caller instead of searched (h3d_import_pivots): host
+// arrays in the format of h3d_export_pivots.
+struct FrozenPivots {
+    const int *rank, *sigma, *tau;
+};
+
 // build stages
 void build_tree(Handle &h, const double *points, cudaStream_t s, Arena &tmp);   // h3d_tree.cu
 void build_lists(Handle &h, cudaStream_t s, Arena &tmp);                         // h3d_tree.cu
-void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget);      // h3d_aca.cu
+// ACA of every admissible block (pass 1: pivot search, skipped when fp is
+// given) and the factors formed from the frozen pivots (pass 2)   h3d_aca.cu
+void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const FrozenPivots *fp = nullptr);
+// New coordinates for the same points (tree, lists and pivots kept): false if
+// they equal the current ones bit for bit; H3D_ERR_DOMAIN for a non-finite one
+bool update_points(Handle &h, const double *points, cudaStream_t s, Arena &tmp);   // h3d_tree.cu
+// pass 2 again into the handle's U and V (their layout is kept)       h3d_aca.cu
+void reform_factors(Handle &h, cudaStream_t s, Arena &tmp);
+void refactor_skeleton(Handle &h, cudaStream_t s);                                // h3d_matvec.cu
+// the points in the caller's order (device, N x 3) from the sorted copy   h3d_tree.cu
+void unsorted_points(const Handle &h, double *out, cudaStream_t s);
 void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp);                   // h3d_matvec.cu
 int matvec_passes(const Handle &h, int nrhs, bool transpose);  // kernel sequences one product launches
 void energy(Handle &h, const void *q, double *E, void *grad, cudaStream_t s);
@@ -358,6 +406,11 @@ void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group, int lag);
 void batch_plan_groups(const BatchPlan &p, int *near_group, int *leaf_group, int *lag);
 int batch_plan_max_ctas_per_sm(const BatchPlan &p);
 void batch_plan_run(BatchPlan &p, const void *const *x, void *const *y, int ctas_per_sm, cudaStream_t s);
+// the caller's queue (false if an item is out of range; NULL items: the queue
+// of the current settings again), the queue in use, the bound of every wait
+bool batch_plan_set_queue(BatchPlan &p, const int *items, int64_t count);
+void batch_plan_get_queue(const BatchPlan &p, int *items, int64_t cap, int64_t *count);
+void batch_plan_set_wait(BatchPlan &p, long long ns);
 void batch_plan_free(BatchPlan *p);
 
 }  // namespace h3d

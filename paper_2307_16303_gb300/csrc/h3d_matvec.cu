@@ -1279,14 +1279,16 @@ void ensure_wide_scratch(Handle &h, cudaStream_t s) {
     if (h.xs_w) return;
     H3D_CUDA(cudaStreamSynchronize(s));
     const size_t es = sizeof(float);
-    h.xs_w = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQW * es);
-    h.nearbuf_w = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQW * es);
-    h.t_w = h.mem.alloc((size_t)std::max<int64_t>(h.sum_rank, 4) * kNQW * es);
-    h.partial_w = h.mem.alloc((size_t)std::max<int64_t>(h.partial_elems_w, 4) * kNQW * es);
+    void *xs = nullptr;   // xs_w last: it marks the scratch as made
+    alloc_all(h.mem, {{&h.nearbuf_w, (size_t)std::max<int64_t>(h.N, 4) * kNQW * es},
+                      {&h.t_w, (size_t)std::max<int64_t>(h.sum_rank, 4) * kNQW * es},
+                      {&h.partial_w, (size_t)std::max<int64_t>(h.partial_elems_w, 4) * kNQW * es},
+                      {&xs, (size_t)std::max<int64_t>(h.N, 4) * kNQW * es}});
+    h.xs_w = xs;
 }
 
 bool use_wide(const Handle &h, int nrhs, bool transpose) {
-    return nrhs > kNQ && !transpose && h.prec == H3D_FP32 && h.leaf_size <= kMaxLeafW &&
+    return nrhs > kNQ && !transpose && h.prec == H3D_FP32 && h.tf32 && h.leaf_size <= kMaxLeafW &&
            h.storage == H3D_STORE_FACTORS;
 }
 
@@ -1964,7 +1966,7 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
         std::vector<int64_t> vc0(nboxes);
         H3D_CUDA(cudaMemcpyAsync(vc0.data(), h.vcol0, nboxes * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         H3D_CUDA(cudaStreamSynchronize(s));
-        const bool wide = h.prec == H3D_FP32 && h.leaf_size <= kMaxLeafW && h.storage == H3D_STORE_FACTORS;
+        const bool wide = h.prec == H3D_FP32 && h.tf32 && h.leaf_size <= kMaxLeafW && h.storage == H3D_STORE_FACTORS;
         std::vector<int> tmap_of(nboxes, -1);
         std::vector<CUtensorMap> tmaps;
         if (wide) {
@@ -2146,14 +2148,18 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
         H3D_CUDA(cudaMemcpyAsync(h.skel_src_order, order.data(), order.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                                  s));
     }
-    if (nblk > 0) {
+    refactor_skeleton(h, s);
+    H3D_CUDA(cudaStreamSynchronize(s));
+    (void)tmp;
+}
+
+void refactor_skeleton(Handle &h, cudaStream_t s) {
+    if (h.nblk > 0) {
         SkelArgs S = skel_args(h);
-        const int grid = (int)std::min<int64_t>(nblk, 4LL * num_sms());
+        const int grid = (int)std::min<int64_t>(h.nblk, 4LL * num_sms());
         k_skel_factor<<<grid, kSkThreads, 0, s>>>(S);
         H3D_LAUNCH_CHECK();
     }
-    H3D_CUDA(cudaStreamSynchronize(s));
-    (void)tmp;
 }
 
 void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s) {

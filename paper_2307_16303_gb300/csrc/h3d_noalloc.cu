@@ -170,12 +170,25 @@ h3d_status scratch_address(void **out) {
     return H3D_OK;
 }
 
+// true for memory the GPU reaches as device memory (cudaMalloc'ed or managed);
+// asks the runtime only, allocates nothing
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" h3d_status h3d_morton_order_noalloc(const double *points, int64_t N, const double *lo, double side,
                                                uint64_t *keys_out, int *perm_out, void *stream) {
     if (!points || !lo || !keys_out || !perm_out || N < 1) return H3D_ERR_ARG;
     if (N > kMaxPoints) return H3D_ERR_ARG;  // beyond the fixed scratch: rejected, never truncated
+    // host buffers would fault the kernels: rejected before any launch
+    if (!is_device_ptr(points) || !is_device_ptr(keys_out) || !is_device_ptr(perm_out)) return H3D_ERR_ARG;
     if (!(side > 0.0) || !std::isfinite(side)) return H3D_ERR_ARG;
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(lo[d])) return H3D_ERR_ARG;

@@ -172,6 +172,36 @@ __global__ void k_local_coords(const double *__restrict__ px, const double *__re
     ploc_lo[i] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.0f);
 }
 
+// new coordinates for the sorted points: flags[0] |= 1 if any differs from the
+// current ones, flags[0] |= 2 if any is not finite
+__global__ void k_points_differ(const double *__restrict__ pts, const int *__restrict__ perm, int64_t n,
+                                const double *__restrict__ px, const double *__restrict__ py,
+                                const double *__restrict__ pz, int *__restrict__ flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = perm[i];
+    const double x = pts[3 * o], y = pts[3 * o + 1], z = pts[3 * o + 2];
+    int f = 0;
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) f |= 2;
+    // bit patterns, so that -0.0 and 0.0 count as different and NaN is caught above
+    if (__double_as_longlong(x) != __double_as_longlong(px[i]) ||
+        __double_as_longlong(y) != __double_as_longlong(py[i]) ||
+        __double_as_longlong(z) != __double_as_longlong(pz[i]))
+        f |= 1;
+    if (f) atomicOr(flags, f);
+}
+
+__global__ void k_scatter_points(const double *__restrict__ px, const double *__restrict__ py,
+                                 const double *__restrict__ pz, const int *__restrict__ perm, int64_t n,
+                                 double *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t o = perm[i];
+    out[3 * o] = px[i];
+    out[3 * o + 1] = py[i];
+    out[3 * o + 2] = pz[i];
+}
+
 // ---------------------------------------------------------------------------
 // lists
 
@@ -513,6 +543,30 @@ void build_lists(Handle &h, cudaStream_t s, Arena &tmp) {
     k_near_sizes<<<grid_for(nleaf), kT, 0, s>>>(h.near_ptr, h.near_src, h.box_start, h.box_end, offL, nleaf, nsz);
     H3D_LAUNCH_CHECK();
     h.near_interactions = scan_exclusive(nsz, nszp, nleaf + 1, s, tmp);
+}
+
+bool update_points(Handle &h, const double *points, cudaStream_t s, Arena &tmp) {
+    const int64_t n = h.N;
+    int *flags = tmp.get<int>(1);
+    H3D_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));
+    k_points_differ<<<grid_for(n), kT, 0, s>>>(points, h.perm, n, h.px, h.py, h.pz, flags);
+    H3D_LAUNCH_CHECK();
+    const int f = read_scalar(flags, s);
+    tmp.free_one(flags);
+    if (f & 2) fail(H3D_ERR_DOMAIN);
+    if (!(f & 1)) return false;
+    k_gather_points<<<grid_for(n), kT, 0, s>>>(points, h.perm, n, h.px, h.py, h.pz);
+    H3D_LAUNCH_CHECK();
+    const double hL = h.side / (double)(1 << h.L);
+    k_local_coords<<<grid_for(n), kT, 0, s>>>(h.px, h.py, h.pz, h.point_leaf, h.box_key, h.box_off[h.L], h.L,
+                                                h.lo[0], h.lo[1], h.lo[2], hL, n, h.ploc, h.ploc_lo);
+    H3D_LAUNCH_CHECK();
+    return true;
+}
+
+void unsorted_points(const Handle &h, double *out, cudaStream_t s) {
+    k_scatter_points<<<grid_for(h.N), kT, 0, s>>>(h.px, h.py, h.pz, h.perm, h.N, out);
+    H3D_LAUNCH_CHECK();
 }
 
 }  // namespace h3d

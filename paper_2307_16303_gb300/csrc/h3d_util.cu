@@ -4,6 +4,11 @@
 
 namespace h3d {
 
+int64_t &fail_alloc_countdown() {
+    static int64_t countdown = -1;
+    return countdown;
+}
+
 int num_sms() {
     static int n = 0;
     if (n == 0) {

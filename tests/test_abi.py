@@ -32,7 +32,7 @@ def test_status_strings_and_defaults_without_gpu():
     assert b"domain" in L.h3d_status_string(2)
     opt = api.Options()
     L.h3d_default_options(ctypes.byref(opt))
-    assert opt.precision == 1 and opt.rank_cap == 512 and opt.side == 2.0 and list(opt.lo) == [-1.0] * 3
+    assert opt.precision == 2 and opt.rank_cap == 512 and opt.side == 2.0 and list(opt.lo) == [-1.0] * 3
     # argument validation happens before any device work
     h = ctypes.c_void_p()
     assert L.h3d_build(None, 10, 0, 64, 1e-7, None, None, ctypes.byref(h)) == 1
@@ -68,3 +68,10 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu():
     assert L.h3d_batch_configure(None, 1, 0, 0, 0, -1) == 1
     assert L.h3d_batch_info(None, None, None, None) == 1
     assert L.h3d_batch_free(None) == 0                                  # freeing nothing is fine
+    assert L.h3d_import_pivots(None, None, None, None, None) == 1
+    assert L.h3d_set_points(None, None, None) == 1
+    assert L.h3d_batch_set_wait_limit(None, 10 ** 6) == 1
+    n = C.c_int64()
+    assert L.h3d_batch_get_queue(None, None, 0, C.byref(n)) == 1
+    assert L.h3d_batch_set_queue(None, None, 0) == 1
+    L.h3d_debug_fail_alloc(-1)                                          # switching the hook off is a no-op

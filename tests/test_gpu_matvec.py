@@ -234,7 +234,7 @@ def test_wide_blocks_of_32_columns():
     # more than 8 columns on an FP32 handle: passes of 32 right-hand sides (the
     # last one partial), checked column by column against the one-column product
     pts = I.uniform(25000, 99)
-    A = H(pts, leaf_size=64, tol=1e-7, precision="fp32")
+    A = H(pts, leaf_size=64, tol=1e-7, precision="fp32_3xtf32")
     x = I.rhs_normal(25000, 40, 100).astype(np.float32)
     Y = gpu_apply(A, x)
     ref = O.direct(pts, x[:, :3].astype(np.float64))
@@ -251,7 +251,7 @@ def test_wide_blocks_of_32_columns():
 ])
 def test_wide_edge_cases(case, pts, leaf, mode):
     n = pts.shape[0]
-    A = H(pts, leaf_size=leaf, tol=1e-7, precision="fp32", admissibility=mode)
+    A = H(pts, leaf_size=leaf, tol=1e-7, precision="fp32_3xtf32", admissibility=mode)
     x = I.rhs_normal(n, 33, 105).astype(np.float32)
     Y = gpu_apply(A, x)
     cols = [0, 13, 31, 32]

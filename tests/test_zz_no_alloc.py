@@ -34,6 +34,27 @@ def _noalloc(api, pts_dev, n, lo=(-1.0, -1.0, -1.0), side=2.0):
     return st, keys.cpu().numpy().view(np.uint64), perm.cpu().numpy().astype(np.int64)
 
 
+def _oracle_order(pts, lo=(-1.0, -1.0, -1.0), side=2.0):
+    """The oracle's Morton keys and the stable order by (key, original index)."""
+    from oracle import oracle as O
+    keys = O.morton(pts, lo=lo, side=side)
+    perm = np.argsort(keys, kind="stable")
+    return keys[perm], perm
+
+
+def test_noalloc_order_matches_oracle_twice_in_a_row():
+    import torch
+    api = _lib()
+    # two clouds, one call each, back to back, against the oracle's keys and a
+    # stable sort of them; a second call must not see the first call's scratch
+    for pts in (I.uniform(300_000, 84), I.jittered_grid(40, 85)):
+        st, keys, perm = _noalloc(api, torch.from_numpy(pts).cuda(), pts.shape[0])
+        assert st == 0
+        ok, op = _oracle_order(pts)
+        assert np.array_equal(keys, ok)
+        assert np.array_equal(perm, op)
+
+
 def test_noalloc_order_matches_build_twice_in_a_row():
     import torch
     api = _lib()
@@ -62,9 +83,23 @@ def test_noalloc_rejects_bad_sizes_and_points():
     bad = torch.from_numpy(np.array([[0.0, 0.0, 0.0], [0.0, 2.5, 0.0]])).cuda()
     st, _, _ = _noalloc(api, bad, 2)
     assert st == 2                       # H3D_ERR_DOMAIN
-    # the largest accepted size works and agrees with a direct lexicographic sort
+    # host buffers are refused before any launch (H3D_ERR_ARG)
+    host_pts = np.ascontiguousarray(I.uniform(100, 86))
+    keys = torch.empty(100, dtype=torch.int64, device="cuda")
+    perm = torch.empty(100, dtype=torch.int32, device="cuda")
+    lo_a = (ctypes.c_double * 3)(-1.0, -1.0, -1.0)
+    s = torch.cuda.current_stream().cuda_stream
+    st = api.lib().h3d_morton_order_noalloc(host_pts.ctypes.data, 100, lo_a, 2.0, keys.data_ptr(), perm.data_ptr(), s)
+    assert st == 1
+    hkeys = np.zeros(100, np.uint64)
+    dpts = torch.from_numpy(host_pts).cuda()
+    st = api.lib().h3d_morton_order_noalloc(dpts.data_ptr(), 100, lo_a, 2.0, hkeys.ctypes.data, perm.data_ptr(), s)
+    assert st == 1
+    # the largest accepted size works and agrees with the oracle's keys and a
+    # stable sort of them
     pts = I.uniform(maxn, 83)
     st, keys, perm = _noalloc(api, torch.from_numpy(pts).cuda(), maxn)
     assert st == 0
-    assert np.all(keys[1:] >= keys[:-1])
-    assert np.array_equal(np.sort(perm), np.arange(maxn))
+    ok, op = _oracle_order(pts)
+    assert np.array_equal(keys, ok)
+    assert np.array_equal(perm, op)
