@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     p.add_argument("--rows", type=int, default=10_000, help="sampled rows for the error / CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the baseline leg")
+    p.add_argument("--o2-N", type=int, default=262_144,
+                   help="points of the oracle's HODLR3D (Alg. 1 + Alg. 2 on the host cores) timed beside the "
+                        "dense sum; 0 skips it")
     p.add_argument("--batched", action="store_true",
                    help="time --batch-count independent clouds (N log-uniform in [8192, --batch-nmax], half cube / "
                         "half sphere, Laplace / Yukawa alternating, FP32) as one persistent launch or one graph "
@@ -186,6 +189,26 @@ def cpu_baseline(pts, x64, y_ours, a, budget_s):
     return {"value": round(full_ms, 3), "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
             "sample": f"O1 FP64 direct sum on {S} seeded rows of the N={a.N} workload "
                       f"({t:.1f} s), scaled by N/rows to one full dense product"}, err, S, (rows, ref)
+
+
+def cpu_hodlr3d(a):
+    """The oracle's HODLR3D on the host cores: Alg. 1 (tree, lists, ACA pivots) and
+    one Alg. 2 product (factors re-formed from the pivots, as the paper does), FP64,
+    on uniform points with the workload's leaf size and tolerance."""
+    from oracle import oracle as O
+    n = a.o2_N
+    pts = I.uniform(n, 1)
+    x = I.rhs_normal(n, 1, 2)[:, 0]
+    t0 = time.perf_counter()
+    o = O.Oracle(pts, leaf_size=a.leaf, tol=a.tol).compress()
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.matvec(x)
+    tm = time.perf_counter() - t0
+    return {"N": n, "leaf_size": a.leaf, "tol": a.tol, "depth": o.L, "build_s": round(tb, 2),
+            "matvec_ms": round(tm * 1e3, 1), "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"O2: the oracle's HODLR3D build (Alg. 1) and one product (Alg. 2, factors re-formed from "
+                      f"the pivots in the product) on N={n} uniform points, FP64, timed whole (not scaled)"}
 
 
 def run_reference(a):
@@ -482,6 +505,8 @@ def main():
         if fp64 is not None and fp64.get("ms") is not None:
             yr = y64_host[ref_rows[0]] if y64_host.ndim == 2 else y64_host[ref_rows[0]][:, None]
             fp64["rel_err_sampled_rows"] = float(np.linalg.norm(yr - ref_rows[1]) / np.linalg.norm(ref_rows[1]))
+        if a.o2_N > 0:
+            out_cpu["o2"] = cpu_hodlr3d(a)
 
     launches = 5 * passes * a.steps   # permute, near field, gather, partial reduce, leaf
     if rank != 0:

@@ -182,6 +182,7 @@ struct Handle {
     struct TcGatherItem *tc_items = nullptr;
     int nsplit_w = 0;                             // gather: boxes split into row tasks (32-column path)
     int *split_box_w = nullptr, *split_ntask_w = nullptr;
+    int max_rv_split_w = 0;                       // widest split box (columns)
     int64_t *split_pbase_w = nullptr;
     int64_t partial_elems_w = 0;
     void *tc_tmaps = nullptr;                     // gather: one 2-D tensor map (CUtensorMap) per source box

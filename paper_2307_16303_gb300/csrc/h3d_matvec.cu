@@ -568,16 +568,28 @@ __global__ void k_permute_in_w(const float *__restrict__ x, int64_t n, int q0, i
     xs[e] = q < nq ? x[(int64_t)(q0 + q) * n + perm[i]] : 0.f;
 }
 
-__global__ void k_reduce_partials_w(SplitArgs S, const float *__restrict__ partial, float *__restrict__ t) {
-    const int q = blockIdx.x;
-    const int Y = S.box[q], nt = S.ntask[q], ld = S.ldv[Y], R = S.Rv[Y];
+// sum of the row-task partials of split box blockIdx.y, columns
+// [8 blockIdx.x, 8 blockIdx.x + 8): one thread per (column, right-hand side),
+// so that every split box spreads over many CTAs
+constexpr int kRedColsW = 8;
+__global__ void __launch_bounds__(kRedColsW * kNQW) k_reduce_partials_w(SplitArgs S, const float *__restrict__ partial,
+                                                                        float *__restrict__ t) {
+    const int q = blockIdx.y;
+    const int Y = S.box[q], R = S.Rv[Y];
+    const int c = blockIdx.x * kRedColsW + (threadIdx.x >> 5), j = threadIdx.x & 31;
+    if (c >= R) return;
+    const int nt = S.ntask[q], ld = S.ldv[Y];
     const int64_t pb = S.pbase[q], vc0 = S.vcol0[Y];
-    for (int e = threadIdx.x; e < R * kNQW; e += blockDim.x) {
-        const int c = e / kNQW, j = e - c * kNQW;
-        float v = 0.f;
-        for (int k = 0; k < nt; ++k) v += partial[(pb + (int64_t)k * ld + c) * kNQW + j];
-        t[S.map_v[vc0 + c] * kNQW + j] = v;
+    const float *p = partial + (pb + c) * kNQW + j;
+    const int64_t step = (int64_t)ld * kNQW;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    int k = 0;
+    for (; k + 4 <= nt; k += 4) {   // four loads in flight
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] += p[(k + u) * step];
     }
+    for (; k < nt; ++k) v[0] += p[k * step];
+    t[S.map_v[vc0 + c] * kNQW + j] = (v[0] + v[1]) + (v[2] + v[3]);
 }
 
 // near field for 32 right-hand sides: one thread per (target, source group)
@@ -1264,7 +1276,8 @@ void matvec_wide(Handle &h, const float *x, float *y, int q0, int nq, cudaStream
     if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
     if (h.nsplit_w > 0) {
         SplitArgs S{h.split_box_w, h.split_ntask_w, h.split_pbase_w, h.Rv, h.ldv, h.vcol0, h.map_v};
-        k_reduce_partials_w<<<h.nsplit_w, 256, 0, s>>>(S, (const float *)h.partial_w, t);
+        const dim3 grid((unsigned)((h.max_rv_split_w + kRedColsW - 1) / kRedColsW), (unsigned)h.nsplit_w);
+        k_reduce_partials_w<<<grid, kRedColsW * kNQW, 0, s>>>(S, (const float *)h.partial_w, t);
     }
     H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
     if (ev) H3D_CUDA(cudaEventRecord(ev[3], s));
@@ -1944,6 +1957,7 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
                 wpbase.push_back(pelw + (int64_t)k * ldv[g]);
             }
             pelw += (int64_t)nt * ldv[g];
+            h.max_rv_split_w = std::max(h.max_rv_split_w, Rv[g]);
         }
     }
     h.nsplit_w = (int)wsbox.size();
