@@ -63,6 +63,9 @@ def parse():
                         "(whichever the tuner picks; both reported) against separate products")
     p.add_argument("--batch-nmax", type=int, default=131072)
     p.add_argument("--batch-count", type=int, default=64, help="clouds in the batch (64: the batched workload)")
+    p.add_argument("--batch-reserve-gb", type=float, default=24.0,
+                   help="device memory kept free while clouds are built with stored factors; larger clouds then "
+                        "take the skeleton storage")
     p.add_argument("--skeleton", action="store_true",
                    help="time the skeleton storage (pivots + LU of K(sigma,tau), entries recomputed in FP64) "
                         "on the same workload")
@@ -240,77 +243,131 @@ def run_reference(a):
 
 
 def run_batched(a):
+    """Independent clouds: one batched product (persistent kernel or graph) against
+    separate products.  Clouds are built smallest first with stored FP32 factors
+    while they fit in device memory (keeping --batch-reserve-gb free); larger
+    clouds then take the skeleton storage (pivots and LU of K(sigma,tau), FP64
+    entries recomputed), which only the graph form runs.  The factor members are
+    also timed as a batch of their own (persistent and graph)."""
     import torch
-    from paper_2307_16303_gb300.api import H3DMatrix, H3DBatch
+    from paper_2307_16303_gb300.api import H3DMatrix, H3DBatch, H3DError
     from oracle import oracle as O
     rng = np.random.default_rng(5)
     sizes = np.round(np.exp(rng.uniform(np.log(8192), np.log(a.batch_nmax), a.batch_count))).astype(int)
-    mats, pts, kerns, xs = [], [], [], []
+    nc = len(sizes)
+    mats, pts, kerns, xs, store = [None] * nc, [None] * nc, [None] * nc, [None] * nc, [None] * nc
+    reserve = a.batch_reserve_gb * 1e9
+    per_point = 0.0          # largest device bytes per point of a factor member so far
+    skeleton_from = None
     t0 = time.perf_counter()
-    for c, n in enumerate(sizes):
-        p = I.uniform(int(n), 500 + c) if c % 2 == 0 else I.sphere(int(n), 500 + c)
+    for c in np.argsort(sizes, kind="stable"):
+        n = int(sizes[c])
+        p = I.uniform(n, 500 + c) if c % 2 == 0 else I.sphere(n, 500 + c)
         kern = "laplace" if (c // 2) % 2 == 0 else "yukawa"
-        mats.append(H3DMatrix(torch.from_numpy(p).cuda(), leaf_size=a.leaf, tol=a.tol, precision="fp32", kernel=kern))
-        pts.append(p)
-        kerns.append(kern)
-        xs.append(torch.from_numpy(I.rhs_normal(int(n), 1, 600 + c)[:, 0].astype(np.float32)).cuda())
+        dev = torch.from_numpy(p).cuda()
+        kind = "factors"
+        if skeleton_from is not None or torch.cuda.mem_get_info()[0] - 1.3 * per_point * n < reserve:
+            kind = "skeleton"
+        try:
+            m = H3DMatrix(dev, leaf_size=a.leaf, tol=a.tol, precision="fp32", kernel=kern, storage=kind)
+        except H3DError as e:
+            if e.status != 3 or kind != "factors":
+                raise
+            kind = "skeleton"
+            m = H3DMatrix(dev, leaf_size=a.leaf, tol=a.tol, precision="fp32", kernel=kern, storage=kind)
+        if kind == "factors":
+            per_point = max(per_point, m.stats()["device_bytes"] / n)
+        elif skeleton_from is None:
+            skeleton_from = n
+        mats[c], pts[c], kerns[c], store[c] = m, p, kern, kind
+        xs[c] = torch.from_numpy(I.rhs_normal(n, 1, 600 + c)[:, 0].astype(np.float32)).cuda()
+        del dev
     build_s = time.perf_counter() - t0
     ys = [torch.empty_like(x) for x in xs]
-    # separate products, one after another on one stream
-    seq = sum(time_steps(lambda m=m, x=x, y=y: m.matvec(x, out=y), a.steps, a.warmup, torch) for m, x, y in
-              zip(mats, xs, ys))
-    B = H3DBatch(mats)
-    forms = {}
-    if B.info()["persistent"] == 1:
-        B.set_mode(True)
-        forms["persistent_untuned_ms"] = round(time_steps(lambda: B.matvec(xs, ys), a.steps, a.warmup, torch), 4)
-    branches = B.tune(xs, ys)
-    info = B.info()
-    with Clocks(torch.cuda.current_device()) as clk:
-        ms = time_steps(lambda: B.matvec(xs, ys), a.steps, a.warmup, torch)
-    # the other form, for comparison (then back to the tuned choice)
-    if info["persistent"] == 1:
-        B.set_mode(False)
-        forms["graph_ms"] = round(time_steps(lambda: B.matvec(xs, ys), a.steps, a.warmup, torch), 4)
-        forms["persistent_ms"] = round(ms, 4)
-    else:
-        forms["graph_ms"] = round(ms, 4)
-        if info["persistent"] == 0:
+    fac = [c for c in range(nc) if store[c] == "factors"]
+    skel = [c for c in range(nc) if store[c] == "skeleton"]
+    peak, src = peaks()
+
+    def batch_forms(idx):
+        """Tuned batch of the members idx: (chosen ms, info, forms, branches, groups)."""
+        bx, by = [xs[c] for c in idx], [ys[c] for c in idx]
+        B = H3DBatch([mats[c] for c in idx])
+        forms = {}
+        if B.info()["persistent"] == 1:
             B.set_mode(True)
-            forms["persistent_ms"] = round(time_steps(lambda: B.matvec(xs, ys), a.steps, a.warmup, torch), 4)
-    B.set_mode(info["persistent"] == 1)
-    B.matvec(xs, ys)
-    torch.cuda.synchronize()
-    errs = []
-    for c in range(min(4, len(sizes))):
+            forms["persistent_untuned_ms"] = round(time_steps(lambda: B.matvec(bx, by), a.steps, a.warmup, torch), 4)
+        branches = B.tune(bx, by)
+        info = B.info()
+        with Clocks(torch.cuda.current_device()) as clk:
+            ms = time_steps(lambda: B.matvec(bx, by), a.steps, a.warmup, torch)
+        if info["persistent"] == 1:
+            B.set_mode(False)
+            forms["graph_ms"] = round(time_steps(lambda: B.matvec(bx, by), a.steps, a.warmup, torch), 4)
+            forms["persistent_ms"] = round(ms, 4)
+        else:
+            forms["graph_ms"] = round(ms, 4)
+            if info["persistent"] == 0:
+                B.set_mode(True)
+                forms["persistent_ms"] = round(time_steps(lambda: B.matvec(bx, by), a.steps, a.warmup, torch), 4)
+        groups = None
+        if info["persistent"] >= 0:
+            ng, lg = B.groups()
+            groups = sorted({(int(u), int(v)) for u, v in zip(ng, lg)})
+        B.set_mode(info["persistent"] == 1)
+        B.matvec(bx, by)
+        torch.cuda.synchronize()
+        B.free()
+        return ms, info, forms, branches, groups, clk.summary()
+
+    # separate products, one after another on one stream
+    seq = sum(time_steps(lambda m=mats[c], x=xs[c], y=ys[c]: m.matvec(x, out=y), a.steps, a.warmup, torch)
+              for c in range(nc))
+    ms, info, forms, branches, groups, clk = batch_forms(list(range(nc)))
+    errs = {}
+    check = sorted(set([0, 1, 2, 3] + ([skel[-1]] if skel else [])))
+    for c in check:
+        if c >= nc:
+            continue
         rows = I.sample_rows(int(sizes[c]), 256, 8 + c)
         ref = O.direct_rows(pts[c], xs[c].double().cpu().numpy(), rows, kernel=kerns[c])
         got = ys[c].double().cpu().numpy()[rows]
-        errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
-    # algorithmic bytes: every factor once, x read and y written once
-    fbytes = sum(m.stats()["factor_bytes"] for m in mats)
-    alg = fbytes + 8 * int(sizes.sum())
-    gbs = alg / (ms * 1e-3) / 1e9
-    peak, src = peaks()
+        errs[f"cloud{c}_{store[c]}_N{int(sizes[c])}"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    fbytes = sum(mats[c].stats()["factor_bytes"] for c in fac)
     persistent = info["persistent"] == 1
-    out = {"metric": f"HODLR3D batched matvec ms, {a.batch_count} clouds (one persistent launch)" if persistent else
-                     f"HODLR3D batched matvec ms, {a.batch_count} clouds (one graph launch)",
+    out = {"metric": f"HODLR3D batched matvec ms, {nc} clouds (one persistent launch)" if persistent else
+                     f"HODLR3D batched matvec ms, {nc} clouds (one graph launch)",
            "value": round(ms, 4), "unit": "ms",
            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"{a.batch_count} clouds, N log-uniform in [8192, {a.batch_nmax}] seed 5, even: uniform cube, "
+           "config": {"workload": f"{nc} clouds, N log-uniform in [8192, {a.batch_nmax}] seed 5, even: uniform cube, "
                                   f"odd: unit sphere; Laplace / Yukawa by pairs; leaf {a.leaf}, tol {a.tol}",
                       "total_points": int(sizes.sum()), "n_min": int(sizes.min()), "n_max": int(sizes.max()),
                       "l2": "inputs larger than L2 (factors >> 129 MB)"},
            "form": "persistent" if persistent else "graph", "ctas_per_sm": info["ctas_per_sm"],
-           "graph_branches": branches if branches else info["branches"],
+           "graph_branches": branches if branches else info["branches"], "item_shapes": groups,
            "separate_products_ms": round(seq, 4), "speedup_vs_separate": round(seq / ms, 3), "forms": forms,
-           "roofline": {"bound": "hbm", "kernel": "k_batch" if persistent else "graph", "achieved": round(gbs, 1),
-                        "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": src,
-                        "traffic": None, "alg_bytes_per_launch": alg},
-           "factor_bytes": fbytes, "build_s": round(build_s, 1),
-           "rel_err_sampled_rows": errs, "clocks": clk.summary(),
-           "gpu_launches": (1 if persistent else 5 * a.batch_count) * a.steps}
+           "storage": {"factor_members": len(fac), "factor_points": int(sum(sizes[c] for c in fac)),
+                       "skeleton_members": len(skel), "skeleton_points": int(sum(sizes[c] for c in skel)),
+                       "skeleton_from_N": skeleton_from, "factor_bytes": fbytes},
+           "build_s": round(build_s, 1), "rel_err_sampled_rows": errs, "clocks": clk,
+           "gpu_launches": (1 if persistent else 5 * nc) * a.steps}
+    if not skel:
+        alg = fbytes + 8 * int(sizes.sum())
+        gbs = alg / (ms * 1e-3) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": "k_batch" if persistent else "graph", "achieved": round(gbs, 1),
+                           "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": src,
+                           "traffic": None, "alg_bytes_per_launch": alg}
+    else:
+        # the factor members alone: the persistent kernel's share of the workload
+        fms, finfo, fforms, _, fgroups, _ = batch_forms(fac)
+        alg = fbytes + 8 * int(sum(sizes[c] for c in fac))
+        gbs = alg / (fms * 1e-3) / 1e9
+        out["factor_members_batch"] = {"ms": round(fms, 4), "form": "persistent" if finfo["persistent"] == 1 else "graph",
+                                       "forms": fforms, "item_shapes": fgroups}
+        out["roofline"] = {"bound": "hbm", "kernel": "k_batch (factor members)" if finfo["persistent"] == 1 else
+                           "graph (factor members)", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                           "frac": round(gbs / peak, 4), "peak_source": src, "traffic": None,
+                           "alg_bytes_per_launch": alg}
     print(json.dumps(out), flush=True)
 
 

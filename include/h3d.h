@@ -208,12 +208,18 @@ h3d_status h3d_forces(h3d_handle h, const void *q, double *E, double *F, void *s
  *            order, by the call that first uses them.
  * h3d_batch_tune times (three runs after a warm-up, CUDA events on `stream`)
  * the graph form with 1, 2, 4, ... branches (up to 32 and the number of
- * handles) and, when available, the persistent form for leaves per item
- * (near, leaf) in {(4,1), (4,2), (8,4)}, queue orders phase-major or pipelined
- * over operators (lag 2 or 8), and the most resident CTAs per SM or one fewer
- * (default: (4,2), lag 0, the most); it keeps the fastest and reports in
- * *branches_out (may be NULL) the branch count, or 0 for the persistent form.
- * It synchronises `stream`.
+ * handles) and, when available, the persistent form: first one item shape for
+ * every operator -- leaves per item (near, leaf) in {(4,1), (4,2), (8,4)} --
+ * with queue orders phase-major or pipelined over operators (lag 2 or 8) and
+ * the most resident CTAs per SM or one fewer (default: (4,2), lag 0, the
+ * most); then, from the best of those, the item shape of each (size, rank)
+ * bucket of operators in turn (N < 2^15, < 2^17 or larger; largest rank <= 96
+ * or larger) among (2,1), (4,1), (4,2), (8,2), (8,4), (16,4).  It keeps the
+ * fastest form and reports in *branches_out (may be NULL) the branch count, or
+ * 0 for the persistent form.  It synchronises `stream`.
+ * h3d_batch_groups writes the persistent form's leaves per near-field item and
+ * per leaf item of every operator (host arrays of `count` ints, either may be
+ * NULL); H3D_ERR_ARG without a persistent form.
  * h3d_batch_configure selects the form (persistent != 0: the persistent kernel;
  * H3D_ERR_ARG if it is not available) and the persistent form's settings: CTAs
  * per SM of its grid (capped at the occupancy limit), leaves per near-field
@@ -232,6 +238,7 @@ h3d_status h3d_batch_tune(h3d_batch b, const void *const *x, void *const *y, voi
 h3d_status h3d_batch_configure(h3d_batch b, int persistent, int ctas_per_sm, int near_group, int leaf_group,
                                int lag);
 h3d_status h3d_batch_info(h3d_batch b, int *persistent, int *ctas_per_sm, int *branches);
+h3d_status h3d_batch_groups(h3d_batch b, int *near_groups, int *leaf_groups);
 
 /* Bound of every wait of the persistent kernel on the completion counters of
  * the items it depends on, in nanoseconds of the GPU's global timer

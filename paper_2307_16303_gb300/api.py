@@ -27,7 +27,7 @@ EXPORTS = ("h3d_default_options", "h3d_build", "h3d_matvec", "h3d_matvec_T", "h3
            "h3d_export_pivots", "h3d_import_pivots", "h3d_set_points", "h3d_debug_fail_alloc",
            "h3d_morton_order_noalloc", "h3d_energy", "h3d_forces",
            "h3d_batch_create", "h3d_batch_matvec", "h3d_batch_tune", "h3d_batch_configure", "h3d_batch_info",
-           "h3d_batch_queue", "h3d_batch_set_wait_limit", "h3d_batch_get_queue", "h3d_batch_set_queue",
+           "h3d_batch_queue", "h3d_batch_groups", "h3d_batch_set_wait_limit", "h3d_batch_get_queue", "h3d_batch_set_queue",
            "h3d_batch_free")
 
 
@@ -94,6 +94,7 @@ def lib():
             "h3d_batch_info": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
             "h3d_batch_queue": (i32, [i32, P, P, P, P, i32, i32, i32, P, C.c_int64, C.POINTER(C.c_int64)]),
             "h3d_batch_set_wait_limit": (i32, [P, i64]),
+            "h3d_batch_groups": (i32, [P, P, P]),
             "h3d_batch_get_queue": (i32, [P, P, i64, C.POINTER(i64)]),
             "h3d_batch_set_queue": (i32, [P, P, i64]),
             "h3d_batch_free": (i32, [P]),
@@ -410,6 +411,15 @@ class H3DBatch:
         if st != 0:
             raise H3DError(st, "h3d_batch_info")
         return {"persistent": p.value, "ctas_per_sm": c.value, "branches": b.value}
+
+    def groups(self) -> tuple[np.ndarray, np.ndarray]:
+        """The persistent form's leaves per near-field item and per leaf item, per matrix."""
+        n = len(self.mats)
+        ng, lg = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        st = lib().h3d_batch_groups(self._b, _np(ng), _np(lg))
+        if st != 0:
+            raise H3DError(st, "h3d_batch_groups")
+        return ng, lg
 
     def set_wait_limit(self, ns: int):
         """Bound of every wait of the persistent kernel, in nanoseconds."""

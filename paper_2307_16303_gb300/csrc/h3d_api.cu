@@ -542,6 +542,14 @@ bool same_vectors(const h3d_batch_s &B, const void *const *x, void *const *y) {
     return true;
 }
 
+// (size, rank) bucket of a handle for the per-bucket item shapes of the tuner:
+// N below 2^15, below 2^17, or larger; largest rank up to 96 or above
+int tune_bucket(const Handle &h) {
+    const int sc = h.N < (1 << 15) ? 0 : h.N < (1 << 17) ? 1 : 2;
+    const int rc = h.max_rank <= 96 ? 0 : 1;
+    return 3 * rc + sc;
+}
+
 // persistent form: leaves per near-field / leaf item
 constexpr int kDefaultNearGroup = 4, kDefaultLeafGroup = 2;   // (a near item gives each of 4 warps a leaf)
 constexpr int kDefaultLag = 0;                                 // phase-major queue
@@ -618,27 +626,28 @@ h3d_status h3d_batch_tune(h3d_batch B, const void *const *x, void *const *y, voi
         cudaEvent_t e0, e1;
         H3D_CUDA(cudaEventCreate(&e0));
         H3D_CUDA(cudaEventCreate(&e1));
-        float best = -1.f;
         // graph form: 1, 2, 4, ... branches
+        float best_graph = -1.f;
         int best_nb = 1;
         const int n = (int)B->hs.size();
         B->persistent = false;
         for (int nb = 1; nb <= std::min(n, 32); nb *= 2) {
             B->branches = nb;
             const float ms = batch_time(*B, x, y, s, e0, e1);
-            if (best < 0.f || ms < best) {
-                best = ms;
+            if (best_graph < 0.f || ms < best_graph) {
+                best_graph = ms;
                 best_nb = nb;
             }
         }
         B->branches = best_nb;
-        // persistent form: leaves per item x CTAs per SM
         bool use_persistent = false;
-        int best_cps = 0, best_ng = kDefaultNearGroup, best_lg = kDefaultLeafGroup;
         if (B->plan) {
+            // persistent form, one item shape for every operator: leaves per item
+            // x queue order x CTAs per SM
             const int cmax = h3d::batch_plan_max_ctas_per_sm(*B->plan);
             static const int groups[][2] = {{4, 1}, {4, 2}, {8, 4}};
-            int best_lag = kDefaultLag;
+            float best = -1.f;
+            int best_cps = cmax, best_ng = kDefaultNearGroup, best_lg = kDefaultLeafGroup, best_lag = kDefaultLag;
             B->persistent = true;
             for (int lag : {0, 2, 8})
                 for (const auto &g : groups) {
@@ -647,9 +656,8 @@ h3d_status h3d_batch_tune(h3d_batch B, const void *const *x, void *const *y, voi
                         if (cps < 1) continue;
                         B->ctas_per_sm = cps;
                         const float ms = batch_time(*B, x, y, s, e0, e1);
-                        if (ms < best) {
+                        if (best < 0.f || ms < best) {
                             best = ms;
-                            use_persistent = true;
                             best_cps = cps;
                             best_ng = g[0];
                             best_lg = g[1];
@@ -657,8 +665,34 @@ h3d_status h3d_batch_tune(h3d_batch B, const void *const *x, void *const *y, voi
                         }
                     }
                 }
-            h3d::batch_plan_regroup(*B->plan, best_ng, best_lg, best_lag);
-            B->ctas_per_sm = use_persistent ? best_cps : cmax;
+            // then the item shape per (size, rank) bucket of operators, one
+            // bucket at a time (coordinate descent from the common best)
+            B->ctas_per_sm = best_cps;
+            std::vector<int> ngv(n, best_ng), lgv(n, best_lg), bucket(n);
+            for (int i = 0; i < n; ++i) bucket[i] = tune_bucket(*B->hs[i]->p);
+            static const int cand[][2] = {{2, 1}, {4, 1}, {4, 2}, {8, 2}, {8, 4}, {16, 4}};
+            for (int k = 0; k < 6; ++k) {
+                if (std::find(bucket.begin(), bucket.end(), k) == bucket.end()) continue;
+                int bng = best_ng, blg = best_lg;
+                for (int i = 0; i < n; ++i)
+                    if (bucket[i] == k) { bng = ngv[i]; blg = lgv[i]; break; }
+                for (const auto &c : cand) {
+                    if (c[0] == bng && c[1] == blg) continue;
+                    for (int i = 0; i < n; ++i)
+                        if (bucket[i] == k) { ngv[i] = c[0]; lgv[i] = c[1]; }
+                    h3d::batch_plan_set_groups(*B->plan, ngv.data(), lgv.data(), best_lag);
+                    const float ms = batch_time(*B, x, y, s, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        bng = c[0];
+                        blg = c[1];
+                    }
+                }
+                for (int i = 0; i < n; ++i)
+                    if (bucket[i] == k) { ngv[i] = bng; lgv[i] = blg; }
+            }
+            h3d::batch_plan_set_groups(*B->plan, ngv.data(), lgv.data(), best_lag);
+            use_persistent = best < best_graph;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -666,6 +700,12 @@ h3d_status h3d_batch_tune(h3d_batch B, const void *const *x, void *const *y, voi
         if (!use_persistent) batch_capture(*B, x, y, best_nb);
         if (branches_out) *branches_out = use_persistent ? 0 : best_nb;
     });
+}
+
+h3d_status h3d_batch_groups(h3d_batch B, int *near_groups, int *leaf_groups) {
+    if (!B || !B->plan) return H3D_ERR_ARG;
+    h3d::batch_plan_op_groups(*B->plan, near_groups, leaf_groups);
+    return H3D_OK;
 }
 
 h3d_status h3d_batch_configure(h3d_batch B, int persistent, int ctas_per_sm, int near_group, int leaf_group, int lag) {

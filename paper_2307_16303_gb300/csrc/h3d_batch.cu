@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchCtasPerSm) k_batch(BatchA
 struct BatchPlan {
     int elem = 4;                            // 4: FP32 operators, 8: FP64
     int nops = 0;
-    int near_group = 0, leaf_group = 0, lag = 0;
+    int near_group = 0, leaf_group = 0, lag = 0;   // the last groups set for every operator
+    std::vector<int> ng, lg;                 // per operator: leaves per near-field item and per leaf item
     std::vector<BatchOp> ops;
     std::vector<Handle *> hs;
     Arena mem;
@@ -272,7 +273,8 @@ struct QueueCounts {
     int ngtask, nsplit, nleaf;
 };
 
-std::vector<int4> batch_queue(const std::vector<QueueCounts> &c, int near_group, int leaf_group, int lag) {
+std::vector<int4> batch_queue(const std::vector<QueueCounts> &c, const std::vector<int> &ng,
+                              const std::vector<int> &lg, int lag) {
     const int nops = (int)c.size();
     std::vector<int4> items;
     for (int o = 0; o < nops; ++o)
@@ -280,8 +282,8 @@ std::vector<int4> batch_queue(const std::vector<QueueCounts> &c, int near_group,
     auto stream_items = [&](int o) {   // G and N of operator o
         std::vector<int4> g, n, out;
         for (int k = 0; k < c[o].ngtask; ++k) g.push_back(make_int4(o, kItemGather, k, 1));
-        for (int z0 = 0; z0 < c[o].nleaf; z0 += near_group)
-            n.push_back(make_int4(o, kItemNear, z0, std::min(near_group, c[o].nleaf - z0)));
+        for (int z0 = 0; z0 < c[o].nleaf; z0 += ng[o])
+            n.push_back(make_int4(o, kItemNear, z0, std::min(ng[o], c[o].nleaf - z0)));
         merge_even(out, g, n);
         return out;
     };
@@ -290,8 +292,8 @@ std::vector<int4> batch_queue(const std::vector<QueueCounts> &c, int near_group,
         if (reduce)
             for (int q = 0; q < c[o].nsplit; ++q) out.push_back(make_int4(o, kItemReduce, q, 1));
         if (leaf)
-            for (int z0 = 0; z0 < c[o].nleaf; z0 += leaf_group)
-                out.push_back(make_int4(o, kItemLeaf, z0, std::min(leaf_group, c[o].nleaf - z0)));
+            for (int z0 = 0; z0 < c[o].nleaf; z0 += lg[o])
+                out.push_back(make_int4(o, kItemLeaf, z0, std::min(lg[o], c[o].nleaf - z0)));
         return out;
     };
     if (lag <= 0) {
@@ -334,7 +336,7 @@ void set_items(BatchPlan &p, const std::vector<int4> &items) {
 void build_items(BatchPlan &p) {
     std::vector<QueueCounts> c;
     for (const Handle *h : p.hs) c.push_back(QueueCounts{h->N, h->ngtask, h->nsplit, h->nleaf});
-    set_items(p, batch_queue(c, p.near_group, p.leaf_group, p.lag));
+    set_items(p, batch_queue(c, p.ng, p.lg, p.lag));
     p.custom = false;
 }
 
@@ -383,10 +385,29 @@ BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, in
 void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group, int lag) {
     p.near_group = std::max(1, near_group);
     p.leaf_group = std::max(1, leaf_group);
+    p.ng.assign(p.nops, p.near_group);
+    p.lg.assign(p.nops, p.leaf_group);
+    batch_plan_set_groups(p, p.ng.data(), p.lg.data(), lag);
+}
+
+void batch_plan_set_groups(BatchPlan &p, const int *near_groups, const int *leaf_groups, int lag) {
     p.lag = std::max(0, lag);
-    for (int o = 0; o < p.nops; ++o) p.ops[o].nnear = (p.hs[o]->nleaf + p.near_group - 1) / p.near_group;
+    p.ng.resize(p.nops);
+    p.lg.resize(p.nops);
+    for (int o = 0; o < p.nops; ++o) {
+        p.ng[o] = std::max(1, near_groups[o]);
+        p.lg[o] = std::max(1, leaf_groups[o]);
+        p.ops[o].nnear = (p.hs[o]->nleaf + p.ng[o] - 1) / p.ng[o];
+    }
     p.d_ops = upload(p, p.d_ops, p.ops);
     build_items(p);
+}
+
+void batch_plan_op_groups(const BatchPlan &p, int *near_groups, int *leaf_groups) {
+    for (int o = 0; o < p.nops; ++o) {
+        if (near_groups) near_groups[o] = p.ng[o];
+        if (leaf_groups) leaf_groups[o] = p.lg[o];
+    }
 }
 
 bool batch_plan_set_queue(BatchPlan &p, const int *items, int64_t count) {
@@ -505,7 +526,8 @@ extern "C" h3d_status h3d_batch_queue(int nops, const int64_t *n_points, const i
         c.push_back(h3d::QueueCounts{n_points[o], n_gather[o], n_split[o], n_leaves[o]});
     }
     try {
-        const std::vector<int4> q = h3d::batch_queue(c, near_group, leaf_group, lag);
+        const std::vector<int4> q = h3d::batch_queue(c, std::vector<int>(nops, near_group),
+                                                     std::vector<int>(nops, leaf_group), lag);
         *count = (int64_t)q.size();
         if (!items) return H3D_OK;
         if (cap < (int64_t)q.size()) return H3D_ERR_ARG;

@@ -404,6 +404,9 @@ void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cud
 struct BatchPlan;
 BatchPlan *batch_plan_create(const std::vector<Handle *> &hs, int near_group, int leaf_group, int lag);
 void batch_plan_regroup(BatchPlan &p, int near_group, int leaf_group, int lag);
+// leaves per near-field item and per leaf item chosen per operator
+void batch_plan_set_groups(BatchPlan &p, const int *near_groups, const int *leaf_groups, int lag);
+void batch_plan_op_groups(const BatchPlan &p, int *near_groups, int *leaf_groups);
 void batch_plan_groups(const BatchPlan &p, int *near_group, int *leaf_group, int *lag);
 int batch_plan_max_ctas_per_sm(const BatchPlan &p);
 void batch_plan_run(BatchPlan &p, const void *const *x, void *const *y, int ctas_per_sm, cudaStream_t s);

@@ -166,3 +166,35 @@ def test_mixed_precision_batch_uses_the_graph_form():
     for m, x, y in zip(mats, xs, run(B, xs, ys)):
         assert torch.equal(y, m.matvec(x))
     B.free()
+
+
+def test_tuner_item_shapes_per_size_and_rank_bucket():
+    import torch
+    from paper_2307_16303_gb300.api import H3DBatch
+    sizes = [4000, 40000, 6000, 150000]        # three size buckets
+    mats, pts = clouds(sizes=sizes, leaf=64)
+    xs = vectors(sizes, np.float32, 600)
+    ys = [torch.empty_like(x) for x in xs]
+    B = H3DBatch(mats)
+    B.set_mode(True)
+    first = run(B, xs, ys)
+    ng0, lg0 = B.groups()
+    assert set(ng0) == {4} and set(lg0) == {2}      # the default shape for every operator
+    B.tune(xs, ys)
+    ng, lg = B.groups()
+    shapes = {(2, 1), (4, 1), (4, 2), (8, 2), (8, 4), (16, 4)}
+    assert all((int(a), int(b)) in shapes for a, b in zip(ng, lg))
+    # operators of one bucket share a shape (clouds 0 and 2 are both below 2^15 points)
+    if mats[0].stats()["max_rank"] <= 96 and mats[2].stats()["max_rank"] <= 96:
+        assert (ng[0], lg[0]) == (ng[2], lg[2])
+    B.set_mode(True)                                  # the tuned shapes: the same bits
+    for y, f in zip(run(B, xs, ys), first):
+        assert torch.equal(y, f)
+    q = B.queue()
+    for o in range(len(sizes)):                       # the queue follows each operator's shape
+        near = q[(q[:, 0] == o) & (q[:, 1] == 1)]
+        leaf = q[(q[:, 0] == o) & (q[:, 1] == 3)]
+        assert near[:, 3].max() == min(int(ng[o]), mats[o].stats()["n_leaves"])
+        assert leaf[:, 3].max() == min(int(lg[o]), mats[o].stats()["n_leaves"])
+        assert near[:, 3].sum() == mats[o].stats()["n_leaves"] == leaf[:, 3].sum()
+    B.free()
