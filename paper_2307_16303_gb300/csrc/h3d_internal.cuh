@@ -161,6 +161,9 @@ struct Handle {
     int skel_nq = 16;                             // columns per skeleton pass (memory-bound choice)
     int64_t *skel_src_ptr = nullptr, *skel_src_order = nullptr;   // blocks by source box (transpose)
     int *skel_next = nullptr;                     // next block of the source-side pass (work queue head)
+    // FP32 skeleton handles of a kernel that float-float evaluates (Laplace,
+    // 1/r^4): coordinates as float-float offsets from the domain centre
+    float4 *sffh = nullptr, *sffl = nullptr;
     double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
     int L = 0;
 

@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include "h3d_async.cuh"
+#include "h3d_ff.cuh"
 #include "h3d_internal.cuh"
 #include "h3d_stream.cuh"
 
@@ -641,6 +642,11 @@ __global__ void __launch_bounds__(kLeafThreads) k_near_w(LeafArgs A, const float
             }
             __syncthreads();
             if (active) {
+                // plain FMAs over the staged sources (at most CAP / S per thread),
+                // then one compensated addition per right-hand side
+                float bs[kNQW];
+#pragma unroll
+                for (int q = 0; q < kNQW; ++q) bs[q] = 0.f;
                 for (int j = s; j < cnt; j += S) {
                     const float4 sh = srcf[2 * j], sl = srcf[2 * j + 1];
                     const float dx = (th.x - sh.x) + (tl.x - sl.x);
@@ -651,12 +657,14 @@ __global__ void __launch_bounds__(kLeafThreads) k_near_w(LeafArgs A, const float
 #pragma unroll
                     for (int u = 0; u < kNQW / 4; ++u) {
                         const float4 b = xj[u];
-                        acc[4 * u].add(kij * b.x);
-                        acc[4 * u + 1].add(kij * b.y);
-                        acc[4 * u + 2].add(kij * b.z);
-                        acc[4 * u + 3].add(kij * b.w);
+                        bs[4 * u] = fmaf(kij, b.x, bs[4 * u]);
+                        bs[4 * u + 1] = fmaf(kij, b.y, bs[4 * u + 1]);
+                        bs[4 * u + 2] = fmaf(kij, b.z, bs[4 * u + 2]);
+                        bs[4 * u + 3] = fmaf(kij, b.w, bs[4 * u + 3]);
                     }
                 }
+#pragma unroll
+                for (int q = 0; q < kNQW; ++q) acc[q].add(bs[q]);
             }
             p = pe;
         }
@@ -1381,6 +1389,7 @@ struct SkelArgs {
     int kind;
     double kappa;
     const double *px, *py, *pz;
+    const float4 *fh, *fl;    // float-float coordinates (FP32 handles, Laplace and 1/r^4)
     int64_t nblk;
     const int *blk_tgt, *blk_src, *box_start, *box_end, *rank, *sigma, *tau;
     const int64_t *piv_off, *lu_off;
@@ -1483,7 +1492,21 @@ __global__ void k_skel_permute(const T *__restrict__ x, int64_t n, int q0, int n
 // per block (one warp): s = K(sigma,Y) X_Y for the pass's nq <= NQ columns (each
 // entry evaluated once), then C = U^{-1} L^{-1} P s with lane q solving column q.
 // cbuf: kSkNQ values per pivot; sbuf: a scratch of max_rank x kSkNQ per warp.
-template <class T, int NQ>
+// The r x nq solved coefficients of one block (stride cst per pivot) rewritten
+// in place as float-float pairs (8 bytes each, like the doubles they replace),
+// each value by the lane that reads it
+__device__ __forceinline__ void skel_coef_to_ff(double *cv, int r, int nq, int cst, int lane) {
+    for (int e = lane; e < r * nq; e += 32) {
+        const int k = e / nq, q = e - k * nq;
+        double *p = cv + (int64_t)k * cst + q;
+        const FF f = ff_from_double(*p);
+        *reinterpret_cast<float2 *>(p) = make_float2(f.h, f.l);
+    }
+}
+
+// FF: entries and sums in float-float (FP32 handles, Laplace and 1/r^4); the
+// solved coefficients are then stored as float-float pairs in place of doubles.
+template <class T, int NQ, bool FF_>
 __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__restrict__ xs, int nq) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * kSkThreads + threadIdx.x) >> 5;
@@ -1500,7 +1523,31 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
         const double *M = S.lu + S.lu_off[b];
         const int *pv = S.lu_piv + po;
         int kb = 0;
-        if (NQ == 1)   // four pivots at a time: each source point is loaded once per four entries
+        if (NQ == 1 && FF_)   // as below, entries and sums in float-float
+            for (; kb + 4 <= r; kb += 4) {
+                float4 ph[4], pl[4];
+                FF a4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int ps = x0 + sg[kb + u];
+                    ph[u] = S.fh[ps];
+                    pl[u] = S.fl[ps];
+                    a4[u] = FF{0.f, 0.f};
+                }
+                for (int j = y0 + lane; j < y1; j += 32) {
+                    const float4 jh = S.fh[j], jl = S.fl[j];
+                    const float xv = (float)xs[j];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) a4[u] = ff_fma_acc(a4[u], ff_kernel(S.kind, ph[u], pl[u], jh, jl), xv);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    double v = ff_to_double(a4[u]);
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) sv[(int64_t)(kb + u) * kSkNQ] = v;
+                }
+            }
+        if (NQ == 1 && !FF_)   // four pivots at a time: each source point is loaded once per four entries
             for (; kb + 4 <= r; kb += 4) {
                 double sx[4], sy[4], sz[4], a4[4];
 #pragma unroll
@@ -1527,13 +1574,28 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
         for (int k = kb; k < r; ++k) {
             const int ps = x0 + sg[k];
             double acc[NQ];
+            if constexpr (FF_) {
+                const float4 ph = S.fh[ps], pl = S.fl[ps];
+                FF fa[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-            for (int j = y0 + lane; j < y1; j += 32) {
-                const double kv = skel_k(S.kind, S.kappa, S.px, S.py, S.pz, ps, j);
+                for (int q = 0; q < NQ; ++q) fa[q] = FF{0.f, 0.f};
+                for (int j = y0 + lane; j < y1; j += 32) {
+                    const FF kv = ff_kernel(S.kind, ph, pl, S.fh[j], S.fl[j]);
 #pragma unroll
-                for (int q = 0; q < NQ; ++q)
-                    if (q < nq) acc[q] += kv * (double)xs[(int64_t)j * nq + q];
+                    for (int q = 0; q < NQ; ++q)
+                        if (q < nq) fa[q] = ff_fma_acc(fa[q], kv, (float)xs[(int64_t)j * nq + q]);
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) acc[q] = ff_to_double(fa[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+                for (int j = y0 + lane; j < y1; j += 32) {
+                    const double kv = skel_k(S.kind, S.kappa, S.px, S.py, S.pz, ps, j);
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+                        if (q < nq) acc[q] += kv * (double)xs[(int64_t)j * nq + q];
+                }
             }
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
@@ -1596,18 +1658,26 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
             }
         }
         __syncwarp();
+        if constexpr (FF_) skel_coef_to_ff(cv, r, nq, S.cst, lane);
     }
 }
 
 // per leaf: Y = near + sum over its ancestors' blocks of K(rows, tau) C.  The
 // four warps split the blocks, lanes take rows (32 at a time); the partial sums
 // are added in shared memory in warp order.  nearbuf is column-major (N x nq).
-template <class T, int NQ>
+struct FFPivot {   // a staged pivot of the float-float path: coordinates, coefficient
+    float4 h, l;
+    float ch, cl;
+};
+
+template <class T, int NQ, bool FF_>
 __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A, const int64_t *__restrict__ tgt_ptr,
                                                           const T *__restrict__ nearbuf, T *__restrict__ y, int64_t n,
                                                           int nq) {
     __shared__ double red[kSkThreads / 32][32][NQ];
-    __shared__ Pt4d piv[kSkThreads / 32][NQ == 1 ? kSkLeafStage : 1];   // one column: a warp's staged pivots
+    __shared__ Pt4d piv[kSkThreads / 32][NQ == 1 && !FF_ ? kSkLeafStage : 1];   // one column: a warp's staged pivots
+    __shared__ FFPivot fpiv[kSkThreads / 32][NQ == 1 && FF_ ? kSkLeafStage : 1];
+    const float2 *cff = reinterpret_cast<const float2 *>(S.cbuf);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int z = blockIdx.x;
     const int Zg = (int)(A.offL + z);
@@ -1618,7 +1688,13 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A
         double acc[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-        const double ix = row ? S.px[i] : 0.0, iy = row ? S.py[i] : 0.0, iz = row ? S.pz[i] : 0.0;
+        const double ix = row && !FF_ ? S.px[i] : 0.0, iy = row && !FF_ ? S.py[i] : 0.0,
+                     iz = row && !FF_ ? S.pz[i] : 0.0;
+        FF fa[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) fa[q] = FF{0.f, 0.f};
+        const float4 fih = FF_ && row ? S.fh[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 fil = FF_ && row ? S.fl[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         int cnt = 0;
         for (int l = 1; l <= A.L; ++l) {
             const int Ag = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
@@ -1627,6 +1703,38 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A
                 const int r = S.rank[b];
                 const int y0 = S.box_start[S.blk_src[b]];
                 const int64_t po = S.piv_off[b];
+                if constexpr (FF_) {
+                    if (NQ == 1) {   // staged pivots, float-float entries and sums
+                        for (int k0 = 0; k0 < r; k0 += kSkLeafStage) {
+                            const int kn = min(kSkLeafStage, r - k0);
+                            __syncwarp();
+                            for (int k = lane; k < kn; k += 32) {
+                                const int pt = y0 + S.tau[po + k0 + k];
+                                const float2 c = cff[(po + k0 + k) * S.cst];
+                                fpiv[warp][k] = FFPivot{S.fh[pt], S.fl[pt], c.x, c.y};
+                            }
+                            __syncwarp();
+                            if (row)
+                                for (int k = 0; k < kn; ++k) {
+                                    const FFPivot p = fpiv[warp][k];
+                                    fa[0] = ff_fma_acc(fa[0], ff_kernel(S.kind, fih, fil, p.h, p.l), FF{p.ch, p.cl});
+                                }
+                        }
+                    } else {
+                        for (int k = 0; k < r; ++k) {
+                            const int pt = y0 + S.tau[po + k];
+                            const FF kv = row ? ff_kernel(S.kind, fih, fil, S.fh[pt], S.fl[pt]) : FF{0.f, 0.f};
+                            const float2 *cv = cff + (po + k) * S.cst;
+#pragma unroll
+                            for (int q = 0; q < NQ; ++q)
+                                if (q < nq) {
+                                    const float2 c = cv[q];
+                                    fa[q] = ff_fma_acc(fa[q], kv, FF{c.x, c.y});
+                                }
+                        }
+                    }
+                    continue;
+                }
                 if (NQ == 1) {   // pivots (coordinates and coefficient) staged in shared memory
                     for (int k0 = 0; k0 < r; k0 += kSkLeafStage) {
                         const int kn = min(kSkLeafStage, r - k0);
@@ -1654,7 +1762,7 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A
             }
         }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) red[warp][lane][q] = acc[q];
+        for (int q = 0; q < NQ; ++q) red[warp][lane][q] = FF_ ? ff_to_double(fa[q]) : acc[q];
         __syncthreads();
         if (warp == 0 && row) {
             const int64_t o = A.perm[i];
@@ -1669,7 +1777,7 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_leaf(SkelArgs S, LeafArgs A
 
 // transpose, per block (one warp): u = K(X,tau)^T X_X for the pass's columns,
 // then a = M^{-T} u from P M = L U: U^T z = u, L^T w = z, a = P^T w.
-template <class T, int NQ>
+template <class T, int NQ, bool FF_>
 __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *__restrict__ xs, int nq) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * kSkThreads + threadIdx.x) >> 5;
@@ -1688,13 +1796,28 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *_
         for (int k = 0; k < r; ++k) {
             const int pt = y0 + ta[k];
             double acc[NQ];
+            if constexpr (FF_) {
+                const float4 ph = S.fh[pt], pl = S.fl[pt];
+                FF fa[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-            for (int i = x0 + lane; i < x1; i += 32) {
-                const double kv = skel_k(S.kind, S.kappa, S.px, S.py, S.pz, i, pt);
+                for (int q = 0; q < NQ; ++q) fa[q] = FF{0.f, 0.f};
+                for (int i = x0 + lane; i < x1; i += 32) {
+                    const FF kv = ff_kernel(S.kind, S.fh[i], S.fl[i], ph, pl);
 #pragma unroll
-                for (int q = 0; q < NQ; ++q)
-                    if (q < nq) acc[q] += kv * (double)xs[(int64_t)i * nq + q];
+                    for (int q = 0; q < NQ; ++q)
+                        if (q < nq) fa[q] = ff_fma_acc(fa[q], kv, (float)xs[(int64_t)i * nq + q]);
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) acc[q] = ff_to_double(fa[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+                for (int i = x0 + lane; i < x1; i += 32) {
+                    const double kv = skel_k(S.kind, S.kappa, S.px, S.py, S.pz, i, pt);
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+                        if (q < nq) acc[q] += kv * (double)xs[(int64_t)i * nq + q];
+                }
             }
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
@@ -1758,12 +1881,13 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *_
             for (int k = 0; k < r; ++k) cv[(int64_t)pv[k] * S.cst + q] = sv[(int64_t)k * kSkNQ + q];
         }
         __syncwarp();
+        if constexpr (FF_) skel_coef_to_ff(cv, r, nq, S.cst, lane);
     }
 }
 
 // transpose, per leaf: Y = near + sum over blocks whose source is an ancestor of
 // the leaf of K(sigma, rows)^T a, blocks taken from the source-major index
-template <class T, int NQ>
+template <class T, int NQ, bool FF_>
 __global__ void __launch_bounds__(kSkThreads) k_skelT_leaf(SkelArgs S, LeafArgs A, const int64_t *__restrict__ src_ptr,
                                                            const int64_t *__restrict__ src_order,
                                                            const T *__restrict__ nearbuf, T *__restrict__ y,
@@ -1779,6 +1903,12 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_leaf(SkelArgs S, LeafArgs 
         double acc[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+        FF fa[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) fa[q] = FF{0.f, 0.f};
+        const float4 fih = FF_ && row ? S.fh[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 fil = FF_ && row ? S.fl[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 *cff = reinterpret_cast<const float2 *>(S.cbuf);
         int cnt = 0;
         for (int l = 1; l <= A.L; ++l) {
             const int Bg = A.leaf_anc[(int64_t)(l - 1) * A.nleaf + z];
@@ -1788,6 +1918,20 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_leaf(SkelArgs S, LeafArgs 
                 const int r = S.rank[b];
                 const int x0 = S.box_start[S.blk_tgt[b]];
                 const int64_t po = S.piv_off[b];
+                if constexpr (FF_) {
+                    for (int k = 0; k < r; ++k) {
+                        const int pt = x0 + S.sigma[po + k];
+                        const FF kv = row ? ff_kernel(S.kind, S.fh[pt], S.fl[pt], fih, fil) : FF{0.f, 0.f};
+                        const float2 *cv = cff + (po + k) * S.cst;
+#pragma unroll
+                        for (int q = 0; q < NQ; ++q)
+                            if (q < nq) {
+                                const float2 c = cv[q];
+                                fa[q] = ff_fma_acc(fa[q], kv, FF{c.x, c.y});
+                            }
+                    }
+                    continue;
+                }
                 for (int k = 0; k < r; ++k) {
                     const double kv = row ? skel_k(S.kind, S.kappa, S.px, S.py, S.pz, x0 + S.sigma[po + k], i) : 0.0;
                     const double *cv = S.cbuf + (po + k) * S.cst;
@@ -1798,7 +1942,7 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_leaf(SkelArgs S, LeafArgs 
             }
         }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) red[warp][lane][q] = acc[q];
+        for (int q = 0; q < NQ; ++q) red[warp][lane][q] = FF_ ? ff_to_double(fa[q]) : acc[q];
         __syncthreads();
         if (warp == 0 && row) {
             const int64_t o = A.perm[i];
@@ -1811,11 +1955,25 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_leaf(SkelArgs S, LeafArgs 
     }
 }
 
+// float-float offsets of the sorted points from the domain centre c0: the high
+// part is the FP32 rounding of the FP64 offset, the low part the FP32 rounding
+// of the remainder (together within 2^-48 of the offset)
+__global__ void k_ff_coords(const double *__restrict__ px, const double *__restrict__ py,
+                            const double *__restrict__ pz, double c0x, double c0y, double c0z, int64_t n,
+                            float4 *__restrict__ hi, float4 *__restrict__ lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const FF x = ff_from_double(px[i] - c0x), y = ff_from_double(py[i] - c0y), z = ff_from_double(pz[i] - c0z);
+    hi[i] = make_float4(x.h, y.h, z.h, 0.f);
+    lo[i] = make_float4(x.l, y.l, z.l, 0.f);
+}
+
 SkelArgs skel_args(Handle &h) {
     SkelArgs S{};
     S.kind = h.kernel;
     S.kappa = h.kappa;
     S.px = h.px; S.py = h.py; S.pz = h.pz;
+    S.fh = h.sffh; S.fl = h.sffl;
     S.nblk = h.nblk;
     S.blk_tgt = h.blk_tgt; S.blk_src = h.blk_src; S.box_start = h.box_start; S.box_end = h.box_end;
     S.rank = h.rank; S.sigma = h.sigma; S.tau = h.tau;
@@ -1832,8 +1990,38 @@ int skel_src_grid(const Handle &h) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((h.nblk * 32 + kSkThreads - 1) / kSkThreads, 16LL * num_sms()));
 }
 
-// one pass of up to kSkNQ columns: x, y column-major (N x nrhs), from column q0
-template <class T>
+// the source-side and leaf kernels of one pass
+template <class T, bool FF_>
+void skel_launch(Handle &h, const SkelArgs &S, const LeafArgs &A, const T *xs, const T *nearbuf, T *yq, int nq,
+                 bool transpose, cudaStream_t s) {
+    const int64_t n = h.N;
+    if (h.nblk > 0) {
+        const int grid = skel_src_grid(h);
+        H3D_CUDA(cudaMemsetAsync(h.skel_next, 0, sizeof(int), s));
+        if (transpose) {
+            if (nq == 1) k_skelT_src<T, 1, FF_><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+            else k_skelT_src<T, kSkNQ, FF_><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+        } else {
+            if (nq == 1) k_skel_src<T, 1, FF_><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+            else k_skel_src<T, kSkNQ, FF_><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
+        }
+    }
+    if (transpose) {
+        if (nq == 1)
+            k_skelT_leaf<T, 1, FF_><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.skel_src_ptr, h.skel_src_order, nearbuf, yq, n,
+                                                                  nq);
+        else
+            k_skelT_leaf<T, kSkNQ, FF_><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.skel_src_ptr, h.skel_src_order, nearbuf,
+                                                                      yq, n, nq);
+    } else {
+        if (nq == 1) k_skel_leaf<T, 1, FF_><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, yq, n, nq);
+        else k_skel_leaf<T, kSkNQ, FF_><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, yq, n, nq);
+    }
+}
+
+// one pass of up to kSkNQ columns: x, y column-major (N x nrhs), from column q0;
+// FF_: float-float entries (FP32 handles of a kernel float-float evaluates)
+template <class T, bool FF_>
 void matvec_skel_pass(Handle &h, const T *x, T *y, int q0, int nq, bool transpose, cudaStream_t s) {
     const int64_t n = h.N;
     T *xs = (T *)h.skel_xs, *nearbuf = (T *)h.skel_near, *x1 = (T *)h.xs;
@@ -1850,28 +2038,8 @@ void matvec_skel_pass(Handle &h, const T *x, T *y, int q0, int nq, bool transpos
         H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));   // x1 is reused by the next column
     }
     SkelArgs S = skel_args(h);
-    if (h.nblk > 0) {
-        const int grid = skel_src_grid(h);
-        H3D_CUDA(cudaMemsetAsync(h.skel_next, 0, sizeof(int), s));
-        if (transpose) {
-            if (nq == 1) k_skelT_src<T, 1><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
-            else k_skelT_src<T, kSkNQ><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
-        } else {
-            if (nq == 1) k_skel_src<T, 1><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
-            else k_skel_src<T, kSkNQ><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
-        }
-    }
     T *yq = y + (size_t)q0 * n;
-    if (transpose) {
-        if (nq == 1)
-            k_skelT_leaf<T, 1><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.skel_src_ptr, h.skel_src_order, nearbuf, yq, n, nq);
-        else
-            k_skelT_leaf<T, kSkNQ><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.skel_src_ptr, h.skel_src_order, nearbuf, yq, n,
-                                                                 nq);
-    } else {
-        if (nq == 1) k_skel_leaf<T, 1><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, yq, n, nq);
-        else k_skel_leaf<T, kSkNQ><<<h.nleaf, kSkThreads, 0, s>>>(S, A, h.tgt_ptr, nearbuf, yq, n, nq);
-    }
+    skel_launch<T, FF_>(h, S, A, xs, nearbuf, yq, nq, transpose, s);
     H3D_LAUNCH_CHECK();
 }
 
@@ -2144,6 +2312,10 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
     h.skel_s = h.mem.get<double>((size_t)skel_src_grid(h) * (kSkThreads / 32) * std::max(1, h.max_rank) * kSkNQ);
     h.skel_next = h.mem.get<int>(1);
     h.skel_c = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1) * h.skel_nq);
+    if (h.prec == H3D_FP32 && ff_kernel_supported(h.kernel)) {   // float-float entries in the products
+        h.sffh = h.mem.get<float4>((size_t)std::max<int64_t>(h.N, 1));
+        h.sffl = h.mem.get<float4>((size_t)std::max<int64_t>(h.N, 1));
+    }
     h.skel_xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
     h.skel_near = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
     {   // blocks grouped by source box (stable), for the transpose product
@@ -2168,6 +2340,11 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
 }
 
 void refactor_skeleton(Handle &h, cudaStream_t s) {
+    if (h.sffh) {
+        const double c0[3] = {h.lo[0] + 0.5 * h.side, h.lo[1] + 0.5 * h.side, h.lo[2] + 0.5 * h.side};
+        k_ff_coords<<<gridn(h.N, 256), 256, 0, s>>>(h.px, h.py, h.pz, c0[0], c0[1], c0[2], h.N, h.sffh, h.sffl);
+        H3D_LAUNCH_CHECK();
+    }
     if (h.nblk > 0) {
         SkelArgs S = skel_args(h);
         const int grid = (int)std::min<int64_t>(h.nblk, 4LL * num_sms());
@@ -2180,8 +2357,12 @@ void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, bool transpose
     const int width = std::max(1, std::min(kSkNQ, h.skel_nq));
     for (int q0 = 0; q0 < nrhs; q0 += width) {
         const int nq = std::min(width, nrhs - q0);
-        if (h.prec == H3D_FP64) matvec_skel_pass<double>(h, (const double *)x, (double *)y, q0, nq, transpose, s);
-        else matvec_skel_pass<float>(h, (const float *)x, (float *)y, q0, nq, transpose, s);
+        if (h.prec == H3D_FP64)
+            matvec_skel_pass<double, false>(h, (const double *)x, (double *)y, q0, nq, transpose, s);
+        else if (h.sffh)
+            matvec_skel_pass<float, true>(h, (const float *)x, (float *)y, q0, nq, transpose, s);
+        else
+            matvec_skel_pass<float, false>(h, (const float *)x, (float *)y, q0, nq, transpose, s);
     }
 }
 

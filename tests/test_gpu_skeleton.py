@@ -67,3 +67,50 @@ def test_skeleton_fp32_vs_direct_multi_rhs_and_forces():
     rows = np.arange(0, n, 97)
     Fx = O.direct_forces_rows(pts, q.double().cpu().numpy(), rows)
     assert rel(Fo.cpu().numpy()[rows], Fx) <= 1e-5
+
+
+@pytest.mark.parametrize("kern", ["laplace", "inv_r4", "yukawa"])
+def test_skeleton_fp32_float_float_entries_vs_oracle(kern):
+    # FP32 handles evaluate K(sigma,Y) and K(X,tau) of Laplace and 1/r^4 in
+    # float-float on the FP32 pipes (Yukawa keeps FP64 entries); against the
+    # oracle's FP64 skeleton product with the same pivots the difference is the
+    # FP32 output and near field, not the entries
+    import torch
+    n = 12000
+    pts = I.uniform(n, 276)
+    kw = dict(leaf_size=48, tol=1e-7, kernel=kern)
+    S = H(pts, precision="fp32", storage="skeleton", **kw)
+    o = O.Oracle(pts, **kw).set_pivots(*S.export_pivots())
+    x = I.rhs_normal(n, 1, 277)[:, 0].astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    x64 = x.astype(np.float64)
+    assert rel(S.matvec(xt).double().cpu().numpy(), o.matvec_skeleton(x64)) <= 1e-6
+    assert rel(S.matvec_T(xt).double().cpu().numpy(), o.matvec_skeleton(x64, transpose=True)) <= 1e-6
+    X = np.ascontiguousarray(np.stack([x, -2 * x, 0.5 * x], axis=1))   # a 3-column pass
+    Y = S.matvec(torch.from_numpy(X).cuda()).double().cpu().numpy()
+    ref = o.matvec_skeleton(x64)
+    for c, f in enumerate((1.0, -2.0, 0.5)):
+        assert rel(Y[:, c], f * ref) <= 1e-6
+    # moved points: the float-float coordinates follow
+    moved = pts + 1e-7 * np.random.default_rng(278).standard_normal(pts.shape)
+    om = O.Oracle(moved, **kw)
+    assert np.array_equal(om.tree()["perm"], o.tree()["perm"])
+    om.set_pivots(*S.export_pivots())
+    S.set_points(torch.from_numpy(moved).cuda())
+    assert rel(S.matvec(xt).double().cpu().numpy(), om.matvec_skeleton(x64)) <= 1e-6
+
+
+def test_skeleton_fp32_float_float_close_pairs():
+    # vertex-sharing leaf blocks hold point pairs much closer than the box size:
+    # points clustered at box corners of the leaf level
+    import torch
+    rng = np.random.default_rng(279)
+    corners = rng.integers(1, 8, size=(3000, 3)) * 0.25 - 1.0          # vertices of the level-3 grid
+    pts = np.clip(corners + rng.uniform(-1e-3, 1e-3, size=corners.shape), -0.999, 0.999)
+    kw = dict(leaf_size=16, tol=1e-7)
+    S = H(pts, precision="fp32", storage="skeleton", **kw)
+    S64 = H(pts, precision="fp64", storage="skeleton", **kw)
+    x = I.rhs_normal(pts.shape[0], 1, 280)[:, 0].astype(np.float32)
+    y32 = S.matvec(torch.from_numpy(x).cuda()).double().cpu().numpy()
+    y64 = S64.matvec(torch.from_numpy(x.astype(np.float64)).cuda()).cpu().numpy()
+    assert rel(y32, y64) <= 1e-6
