@@ -116,6 +116,20 @@ __device__ __forceinline__ FF ff_fma_acc(FF acc, FF k, FF c) {
 
 __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.h + (double)a.l; }
 
+// sum over the 32 lanes of a warp in float-float (TwoSum of the high parts at
+// each butterfly step): FP64 additions run at 1/64 of the FP32 rate on GB300,
+// so a warp sum of doubles costs more than the float-float entries it sums.
+// Every lane receives a sum (the lanes' roundings may differ in the last bits).
+__device__ __forceinline__ FF ff_warp_sum(FF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, v.h, o), ol = __shfl_xor_sync(0xffffffffu, v.l, o);
+        const FF s = ff_two_sum(v.h, oh);
+        v = FF{s.h, __fadd_rn(__fadd_rn(v.l, ol), s.l)};
+    }
+    return v;
+}
+
 __device__ __forceinline__ FF ff_from_double(double v) {
     const float h = (float)v;
     return FF{h, (float)(v - (double)h)};

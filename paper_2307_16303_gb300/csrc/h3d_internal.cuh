@@ -164,6 +164,10 @@ struct Handle {
     // FP32 skeleton handles of a kernel that float-float evaluates (Laplace,
     // 1/r^4): coordinates as float-float offsets from the domain centre
     float4 *sffh = nullptr, *sffl = nullptr;
+    // large blocks of the skeleton products: (block, pivot) items, per-block slot, pivot sums
+    int2 *skel_big = nullptr;
+    int64_t skel_nbig = 0, *skel_bigpo = nullptr;
+    double *skel_sbig = nullptr;
     double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
     int L = 0;
 

@@ -1399,6 +1399,10 @@ struct SkelArgs {
     int mr;                   // largest rank (per-warp scratch stride)
     int cst;                  // columns per pass (cbuf stride per pivot)
     int *next;                // source-side pass: next block (zero before the launch)
+    int ff;                   // LU factors, pivot sums and coefficients held as float-float pairs
+    // large blocks: their pivot sums come from k_skel_rows (one warp per pivot)
+    const int64_t *bigpo;     // per block: first slot in sbig, or -1
+    double *sbig;             // kSkNQ values per pivot of the large blocks
 };
 
 // next block for a warp of a source-side pass: blocks in list order (largest,
@@ -1411,6 +1415,7 @@ __device__ __forceinline__ int64_t skel_next_block(const SkelArgs &S, int lane) 
 }
 
 constexpr int kSkThreads = 128;
+constexpr int64_t kSkBig = 1 << 14;   // entries r x max(m, n) from which a block's pivot sums are spread over warps
 constexpr int kSkLeafStage = 128;   // pivots staged per warp at a time (single-column leaf pass)
 
 // M = K(sigma,tau) of every block, factored P M = L U in place (partial pivoting)
@@ -1470,6 +1475,12 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_factor(SkelArgs S) {
             }
             __syncthreads();
         }
+        if (S.ff)   // float-float factors for the float-float solves, the diagonal as its reciprocal
+            for (int e = tid; e < r * r; e += kSkThreads) {
+                const double v = (e % (r + 1) == 0) ? 1.0 / M[e] : M[e];
+                const FF f = ff_from_double(v);
+                *reinterpret_cast<float2 *>(M + e) = make_float2(f.h, f.l);
+            }
         for (int k = tid; k < r; k += kSkThreads) S.lu_piv[S.piv_off[b] + k] = piv[k];
         __syncthreads();
     }
@@ -1492,20 +1503,214 @@ __global__ void k_skel_permute(const T *__restrict__ x, int64_t n, int q0, int n
 // per block (one warp): s = K(sigma,Y) X_Y for the pass's nq <= NQ columns (each
 // entry evaluated once), then C = U^{-1} L^{-1} P s with lane q solving column q.
 // cbuf: kSkNQ values per pivot; sbuf: a scratch of max_rank x kSkNQ per warp.
-// The r x nq solved coefficients of one block (stride cst per pivot) rewritten
-// in place as float-float pairs (8 bytes each, like the doubles they replace),
-// each value by the lane that reads it
-__device__ __forceinline__ void skel_coef_to_ff(double *cv, int r, int nq, int cst, int lane) {
-    for (int e = lane; e < r * nq; e += 32) {
-        const int k = e / nq, q = e - k * nq;
-        double *p = cv + (int64_t)k * cst + q;
-        const FF f = ff_from_double(*p);
-        *reinterpret_cast<float2 *>(p) = make_float2(f.h, f.l);
+// float-float values stored in the 8 bytes of a double slot
+__device__ __forceinline__ FF ld_ff(const double *p) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    return FF{v.x, v.y};
+}
+__device__ __forceinline__ void st_ff(double *p, FF v) { *reinterpret_cast<float2 *>(p) = make_float2(v.h, v.l); }
+// a - b c, renormalised (TwoSum of the result's two parts): the triangular
+// solves cancel at nearly every step, and a low part left larger than the high
+// part's last bit would then carry only single precision into the next step
+__device__ __forceinline__ FF ff_fms(FF a, FF b, FF c) {
+    const FF p = ff_mul(b, c);
+    const FF t = ff_two_sum(a.h, -p.h);
+    return ff_two_sum(t.h, __fadd_rn(__fsub_rn(a.l, p.l), t.l));
+}
+__device__ __forceinline__ FF ff_shfl(FF v, int src) {
+    return FF{__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src)};
+}
+
+// Float-float solves with the float-float LU of one block (row-major r x r, L
+// unit lower, the diagonal of U stored as its reciprocal; P M = L U, pv the row
+// order).  s: pivot sums at stride kSkNQ; c: the result at stride cst.  With
+// every intermediate renormalised, the solve's rounding acts like a relative
+// perturbation of ~1e-14 of the factors, which changes the block's product by
+// far less than the ACA tolerance, so the FP64 pipe is not needed here.
+//   c = U^{-1} L^{-1} P s           (forward product)
+template <int NQ>
+__device__ __forceinline__ void ff_solve(const double *M, const int *pv, int r, const double *sv, double *cv, int cst,
+                                         int nq, int lane) {
+    if (NQ == 1 && r <= 64) {   // lane k holds rows k and k + 32
+        const int k0 = lane, k1 = lane + 32;
+        FF z0 = k0 < r ? ld_ff(sv + (int64_t)pv[k0] * kSkNQ) : FF{0.f, 0.f};
+        FF z1 = k1 < r ? ld_ff(sv + (int64_t)pv[k1] * kSkNQ) : FF{0.f, 0.f};
+        for (int l = 0; l < r; ++l) {   // L z = P s
+            const FF zl = ff_shfl(l < 32 ? z0 : z1, l & 31);
+            if (k0 > l && k0 < r) z0 = ff_fms(z0, ld_ff(M + (size_t)k0 * r + l), zl);
+            if (k1 > l && k1 < r) z1 = ff_fms(z1, ld_ff(M + (size_t)k1 * r + l), zl);
+        }
+        for (int l = r - 1; l >= 0; --l) {   // U c = z
+            if (lane == (l & 31)) {
+                if (l < 32) z0 = ff_mul(z0, ld_ff(M + (size_t)l * r + l));
+                else z1 = ff_mul(z1, ld_ff(M + (size_t)l * r + l));
+            }
+            const FF cl = ff_shfl(l < 32 ? z0 : z1, l & 31);
+            if (k0 < l) z0 = ff_fms(z0, ld_ff(M + (size_t)k0 * r + l), cl);
+            if (k1 < l) z1 = ff_fms(z1, ld_ff(M + (size_t)k1 * r + l), cl);
+        }
+        if (k0 < r) st_ff(cv + (int64_t)k0 * cst, z0);
+        if (k1 < r) st_ff(cv + (int64_t)k1 * cst, z1);
+    } else if (NQ == 1) {   // the warp shares each dot product
+        for (int k = 0; k < r; ++k) {
+            FF acc{0.f, 0.f};
+            for (int l = lane; l < k; l += 32) acc = ff_fma_acc(acc, ld_ff(M + (size_t)k * r + l), ld_ff(cv + (int64_t)l * cst));
+            acc = ff_warp_sum(acc);
+            if (lane == 0) st_ff(cv + (int64_t)k * cst, ff_fms(ld_ff(sv + (int64_t)pv[k] * kSkNQ), acc, FF{1.f, 0.f}));
+            __syncwarp();
+        }
+        for (int k = r - 1; k >= 0; --k) {
+            FF acc{0.f, 0.f};
+            for (int l = k + 1 + lane; l < r; l += 32)
+                acc = ff_fma_acc(acc, ld_ff(M + (size_t)k * r + l), ld_ff(cv + (int64_t)l * cst));
+            acc = ff_warp_sum(acc);
+            if (lane == 0)
+                st_ff(cv + (int64_t)k * cst,
+                      ff_mul(ff_fms(ld_ff(cv + (int64_t)k * cst), acc, FF{1.f, 0.f}), ld_ff(M + (size_t)k * r + k)));
+            __syncwarp();
+        }
+    } else if (lane < nq) {   // lane q solves column q
+        const int q = lane;
+        for (int k = 0; k < r; ++k) {
+            FF z = ld_ff(sv + (int64_t)pv[k] * kSkNQ + q);
+            for (int l = 0; l < k; ++l) z = ff_fms(z, ld_ff(M + (size_t)k * r + l), ld_ff(cv + (int64_t)l * cst + q));
+            st_ff(cv + (int64_t)k * cst + q, z);
+        }
+        for (int k = r - 1; k >= 0; --k) {
+            FF z = ld_ff(cv + (int64_t)k * cst + q);
+            for (int l = k + 1; l < r; ++l) z = ff_fms(z, ld_ff(M + (size_t)k * r + l), ld_ff(cv + (int64_t)l * cst + q));
+            st_ff(cv + (int64_t)k * cst + q, ff_mul(z, ld_ff(M + (size_t)k * r + k)));
+        }
     }
 }
 
-// FF: entries and sums in float-float (FP32 handles, Laplace and 1/r^4); the
-// solved coefficients are then stored as float-float pairs in place of doubles.
+//   a = P^T L^{-T} U^{-T} u          (transpose product); sv is overwritten
+template <int NQ>
+__device__ __forceinline__ void ff_solve_T(const double *M, const int *pv, int r, double *sv, double *cv, int cst,
+                                           int nq, int lane) {
+    if (NQ == 1 && r <= 64) {
+        const int k0 = lane, k1 = lane + 32;
+        FF z0 = k0 < r ? ld_ff(sv + (int64_t)k0 * kSkNQ) : FF{0.f, 0.f};
+        FF z1 = k1 < r ? ld_ff(sv + (int64_t)k1 * kSkNQ) : FF{0.f, 0.f};
+        for (int l = 0; l < r; ++l) {   // U^T z = u
+            if (lane == (l & 31)) {
+                if (l < 32) z0 = ff_mul(z0, ld_ff(M + (size_t)l * r + l));
+                else z1 = ff_mul(z1, ld_ff(M + (size_t)l * r + l));
+            }
+            const FF zl = ff_shfl(l < 32 ? z0 : z1, l & 31);
+            if (k0 > l && k0 < r) z0 = ff_fms(z0, ld_ff(M + (size_t)l * r + k0), zl);
+            if (k1 > l && k1 < r) z1 = ff_fms(z1, ld_ff(M + (size_t)l * r + k1), zl);
+        }
+        for (int l = r - 1; l >= 0; --l) {   // L^T w = z
+            const FF wl = ff_shfl(l < 32 ? z0 : z1, l & 31);
+            if (k0 < l) z0 = ff_fms(z0, ld_ff(M + (size_t)l * r + k0), wl);
+            if (k1 < l) z1 = ff_fms(z1, ld_ff(M + (size_t)l * r + k1), wl);
+        }
+        if (k0 < r) st_ff(cv + (int64_t)pv[k0] * cst, z0);
+        if (k1 < r) st_ff(cv + (int64_t)pv[k1] * cst, z1);
+    } else if (NQ == 1) {
+        for (int k = 0; k < r; ++k) {   // U^T z = u
+            FF acc{0.f, 0.f};
+            for (int l = lane; l < k; l += 32) acc = ff_fma_acc(acc, ld_ff(M + (size_t)l * r + k), ld_ff(sv + (int64_t)l * kSkNQ));
+            acc = ff_warp_sum(acc);
+            if (lane == 0)
+                st_ff(sv + (int64_t)k * kSkNQ,
+                      ff_mul(ff_fms(ld_ff(sv + (int64_t)k * kSkNQ), acc, FF{1.f, 0.f}), ld_ff(M + (size_t)k * r + k)));
+            __syncwarp();
+        }
+        for (int k = r - 1; k >= 0; --k) {   // L^T w = z
+            FF acc{0.f, 0.f};
+            for (int l = k + 1 + lane; l < r; l += 32)
+                acc = ff_fma_acc(acc, ld_ff(M + (size_t)l * r + k), ld_ff(sv + (int64_t)l * kSkNQ));
+            acc = ff_warp_sum(acc);
+            if (lane == 0) st_ff(sv + (int64_t)k * kSkNQ, ff_fms(ld_ff(sv + (int64_t)k * kSkNQ), acc, FF{1.f, 0.f}));
+            __syncwarp();
+        }
+        for (int k = lane; k < r; k += 32) st_ff(cv + (int64_t)pv[k] * cst, ld_ff(sv + (int64_t)k * kSkNQ));
+    } else if (lane < nq) {
+        const int q = lane;
+        for (int k = 0; k < r; ++k) {
+            FF z = ld_ff(sv + (int64_t)k * kSkNQ + q);
+            for (int l = 0; l < k; ++l) z = ff_fms(z, ld_ff(M + (size_t)l * r + k), ld_ff(sv + (int64_t)l * kSkNQ + q));
+            st_ff(sv + (int64_t)k * kSkNQ + q, ff_mul(z, ld_ff(M + (size_t)k * r + k)));
+        }
+        for (int k = r - 1; k >= 0; --k) {
+            FF z = ld_ff(sv + (int64_t)k * kSkNQ + q);
+            for (int l = k + 1; l < r; ++l) z = ff_fms(z, ld_ff(M + (size_t)l * r + k), ld_ff(sv + (int64_t)l * kSkNQ + q));
+            st_ff(sv + (int64_t)k * kSkNQ + q, z);
+        }
+        for (int k = 0; k < r; ++k) st_ff(cv + (int64_t)pv[k] * cst + q, ld_ff(sv + (int64_t)k * kSkNQ + q));
+    }
+}
+
+// The pivot sums of the large blocks, one warp per (block, pivot) item, so that
+// a few large blocks (the coarse levels) spread over the whole GPU instead of
+// leaving one warp each running long after the rest:
+//   TR = false: s_k = sum_{j in Y} K(sigma_k, p_j) x_j   (forward product)
+//   TR = true:  u_k = sum_{i in X} K(p_i, tau_k) x_i     (transpose product)
+// written to sbig in the layout the source-side kernels read.
+template <class T, int NQ, bool FF_, bool TR>
+__global__ void __launch_bounds__(kSkThreads) k_skel_rows(SkelArgs S, const int2 *__restrict__ items, int64_t nitems,
+                                                          const T *__restrict__ xs, int nq) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (kSkThreads / 32);
+    for (int64_t it = ((int64_t)blockIdx.x * kSkThreads + threadIdx.x) >> 5; it < nitems; it += nw) {
+        const int2 I = items[it];
+        const int64_t b = I.x, po = S.piv_off[b];
+        const int k = I.y;
+        int p, j0, j1;
+        if (TR) {
+            p = S.box_start[S.blk_src[b]] + S.tau[po + k];
+            j0 = S.box_start[S.blk_tgt[b]];
+            j1 = S.box_end[S.blk_tgt[b]];
+        } else {
+            p = S.box_start[S.blk_tgt[b]] + S.sigma[po + k];
+            j0 = S.box_start[S.blk_src[b]];
+            j1 = S.box_end[S.blk_src[b]];
+        }
+        double *out = S.sbig + (S.bigpo[b] + k) * kSkNQ;
+        if constexpr (FF_) {
+            const float4 ph = S.fh[p], pl = S.fl[p];
+            FF fa[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) fa[q] = FF{0.f, 0.f};
+            for (int j = j0 + lane; j < j1; j += 32) {
+                const FF kv = TR ? ff_kernel(S.kind, S.fh[j], S.fl[j], ph, pl) : ff_kernel(S.kind, ph, pl, S.fh[j], S.fl[j]);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    if (q < nq) fa[q] = ff_fma_acc(fa[q], kv, (float)xs[(int64_t)j * nq + q]);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nq) {
+                    const FF v = ff_warp_sum(fa[q]);
+                    if (lane == 0) st_ff(out + q, v);
+                }
+        } else {
+            double acc[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+            for (int j = j0 + lane; j < j1; j += 32) {
+                const double kv = TR ? skel_k(S.kind, S.kappa, S.px, S.py, S.pz, j, p)
+                                     : skel_k(S.kind, S.kappa, S.px, S.py, S.pz, p, j);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    if (q < nq) acc[q] += kv * (double)xs[(int64_t)j * nq + q];
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < nq) {
+                    double v = acc[q];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) out[q] = v;
+                }
+        }
+    }
+}
+
+// FF_: entries, sums, solves and the solved coefficients in float-float (FP32
+// handles, Laplace and 1/r^4); pivot sums and coefficients then occupy their
+// double slots as float-float pairs.
 template <class T, int NQ, bool FF_>
 __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__restrict__ xs, int nq) {
     const int lane = threadIdx.x & 31;
@@ -1522,7 +1727,9 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
         double *sv = S.sbuf + w0 * (int64_t)S.mr * kSkNQ, *cv = S.cbuf + po * S.cst;
         const double *M = S.lu + S.lu_off[b];
         const int *pv = S.lu_piv + po;
-        int kb = 0;
+        const int64_t bp = S.bigpo[b];
+        if (bp >= 0) sv = S.sbig + bp * kSkNQ;   // a large block: its sums are ready
+        int kb = bp >= 0 ? r : 0;
         if (NQ == 1 && FF_)   // as below, entries and sums in float-float
             for (; kb + 4 <= r; kb += 4) {
                 float4 ph[4], pl[4];
@@ -1542,9 +1749,8 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    double v = ff_to_double(a4[u]);
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0) sv[(int64_t)(kb + u) * kSkNQ] = v;
+                    const FF v = ff_warp_sum(a4[u]);
+                    if (lane == 0) st_ff(sv + (int64_t)(kb + u) * kSkNQ, v);
                 }
             }
         if (NQ == 1 && !FF_)   // four pivots at a time: each source point is loaded once per four entries
@@ -1586,7 +1792,12 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
                         if (q < nq) fa[q] = ff_fma_acc(fa[q], kv, (float)xs[(int64_t)j * nq + q]);
                 }
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) acc[q] = ff_to_double(fa[q]);
+                for (int q = 0; q < NQ; ++q)
+                    if (q < nq) {
+                        const FF v = ff_warp_sum(fa[q]);
+                        if (lane == 0) st_ff(sv + (int64_t)k * kSkNQ + q, v);
+                    }
+                continue;
             } else {
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
@@ -1607,6 +1818,11 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
             }
         }
         __syncwarp();
+        if constexpr (FF_) {
+            ff_solve<NQ>(M, pv, r, sv, cv, S.cst, nq, lane);
+            __syncwarp();
+            continue;
+        }
         if (NQ == 1 && r <= 64) {   // one column, rank <= 64: lane k holds z_k and z_(k+32)
             // column-oriented substitutions: one FMA per lane and column instead of a
             // dot product and a five-step FP64 warp sum per row
@@ -1658,7 +1874,6 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
             }
         }
         __syncwarp();
-        if constexpr (FF_) skel_coef_to_ff(cv, r, nq, S.cst, lane);
     }
 }
 
@@ -1793,7 +2008,9 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *_
         double *sv = S.sbuf + w0 * (int64_t)S.mr * kSkNQ, *cv = S.cbuf + po * S.cst;
         const double *M = S.lu + S.lu_off[b];
         const int *pv = S.lu_piv + po;
-        for (int k = 0; k < r; ++k) {
+        const int64_t bp = S.bigpo[b];
+        if (bp >= 0) sv = S.sbig + bp * kSkNQ;   // a large block: its sums are ready
+        for (int k = bp >= 0 ? r : 0; k < r; ++k) {
             const int pt = y0 + ta[k];
             double acc[NQ];
             if constexpr (FF_) {
@@ -1808,7 +2025,12 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *_
                         if (q < nq) fa[q] = ff_fma_acc(fa[q], kv, (float)xs[(int64_t)i * nq + q]);
                 }
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) acc[q] = ff_to_double(fa[q]);
+                for (int q = 0; q < NQ; ++q)
+                    if (q < nq) {
+                        const FF v = ff_warp_sum(fa[q]);
+                        if (lane == 0) st_ff(sv + (int64_t)k * kSkNQ + q, v);
+                    }
+                continue;
             } else {
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
@@ -1829,6 +2051,11 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *_
             }
         }
         __syncwarp();
+        if constexpr (FF_) {
+            ff_solve_T<NQ>(M, pv, r, sv, cv, S.cst, nq, lane);
+            __syncwarp();
+            continue;
+        }
         // z and w overwrite u in sv; a is scattered into cv by the row order
         if (NQ == 1 && r <= 64) {   // one column, rank <= 64: lane k holds entries k and k + 32
             const int k0 = lane, k1 = lane + 32;
@@ -1881,7 +2108,6 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *_
             for (int k = 0; k < r; ++k) cv[(int64_t)pv[k] * S.cst + q] = sv[(int64_t)k * kSkNQ + q];
         }
         __syncwarp();
-        if constexpr (FF_) skel_coef_to_ff(cv, r, nq, S.cst, lane);
     }
 }
 
@@ -1983,6 +2209,9 @@ SkelArgs skel_args(Handle &h) {
     S.mr = std::max(1, h.max_rank);
     S.cst = std::max(1, h.skel_nq);
     S.next = h.skel_next;
+    S.ff = h.sffh != nullptr;
+    S.bigpo = h.skel_bigpo;
+    S.sbig = h.skel_sbig;
     return S;
 }
 
@@ -1997,6 +2226,16 @@ void skel_launch(Handle &h, const SkelArgs &S, const LeafArgs &A, const T *xs, c
     const int64_t n = h.N;
     if (h.nblk > 0) {
         const int grid = skel_src_grid(h);
+        if (h.skel_nbig > 0) {   // pivot sums of the large blocks first
+            const int rg = (int)std::min<int64_t>((h.skel_nbig * 32 + kSkThreads - 1) / kSkThreads, 16LL * num_sms());
+            if (transpose) {
+                if (nq == 1) k_skel_rows<T, 1, FF_, true><<<rg, kSkThreads, 0, s>>>(S, h.skel_big, h.skel_nbig, xs, nq);
+                else k_skel_rows<T, kSkNQ, FF_, true><<<rg, kSkThreads, 0, s>>>(S, h.skel_big, h.skel_nbig, xs, nq);
+            } else {
+                if (nq == 1) k_skel_rows<T, 1, FF_, false><<<rg, kSkThreads, 0, s>>>(S, h.skel_big, h.skel_nbig, xs, nq);
+                else k_skel_rows<T, kSkNQ, FF_, false><<<rg, kSkThreads, 0, s>>>(S, h.skel_big, h.skel_nbig, xs, nq);
+            }
+        }
         H3D_CUDA(cudaMemsetAsync(h.skel_next, 0, sizeof(int), s));
         if (transpose) {
             if (nq == 1) k_skelT_src<T, 1, FF_><<<grid, kSkThreads, 0, s>>>(S, xs, nq);
@@ -2310,6 +2549,34 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
         while (h.skel_nq > 1 && (double)h.sum_rank * h.skel_nq * 8.0 > avail / 3.0) h.skel_nq /= 2;
     }
     h.skel_s = h.mem.get<double>((size_t)skel_src_grid(h) * (kSkThreads / 32) * std::max(1, h.max_rank) * kSkNQ);
+    {   // large blocks (r x max(m, n) >= kSkBig entries): one item per pivot
+        std::vector<int> tg(nblk), sc(nblk), bs(h.n_boxes), be(h.n_boxes);
+        if (nblk > 0) {
+            H3D_CUDA(cudaMemcpyAsync(tg.data(), h.blk_tgt, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+            H3D_CUDA(cudaMemcpyAsync(sc.data(), h.blk_src, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+        }
+        H3D_CUDA(cudaMemcpyAsync(bs.data(), h.box_start, h.n_boxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+        H3D_CUDA(cudaMemcpyAsync(be.data(), h.box_end, h.n_boxes * sizeof(int), cudaMemcpyDeviceToHost, s));
+        H3D_CUDA(cudaStreamSynchronize(s));
+        std::vector<int64_t> bigpo(std::max<int64_t>(nblk, 1), -1);
+        std::vector<int2> items;
+        int64_t slots = 0;
+        for (int64_t b = 0; b < nblk; ++b) {
+            const int64_t ext = std::max(be[tg[b]] - bs[tg[b]], be[sc[b]] - bs[sc[b]]);
+            if ((int64_t)rk[b] * ext < kSkBig) continue;
+            bigpo[b] = slots;
+            for (int k = 0; k < rk[b]; ++k) items.push_back(make_int2((int)b, k));
+            slots += rk[b];
+        }
+        h.skel_nbig = (int64_t)items.size();
+        h.skel_bigpo = h.mem.get<int64_t>(bigpo.size());
+        H3D_CUDA(cudaMemcpyAsync(h.skel_bigpo, bigpo.data(), bigpo.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        h.skel_big = h.mem.get<int2>(std::max<size_t>(items.size(), 1));
+        if (!items.empty())
+            H3D_CUDA(cudaMemcpyAsync(h.skel_big, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        h.skel_sbig = h.mem.get<double>((size_t)std::max<int64_t>(slots, 1) * kSkNQ);
+        H3D_CUDA(cudaStreamSynchronize(s));
+    }
     h.skel_next = h.mem.get<int>(1);
     h.skel_c = h.mem.get<double>((size_t)std::max<int64_t>(h.sum_rank, 1) * h.skel_nq);
     if (h.prec == H3D_FP32 && ff_kernel_supported(h.kernel)) {   // float-float entries in the products

@@ -1,4 +1,6 @@
-"""Skeleton storage (pivots + LU of K(sigma,tau), entries recomputed in FP64).
+"""Skeleton storage (pivots + LU of K(sigma,tau), entries recomputed in every product:
+FP64 for FP64 handles, float-float on the FP32 pipes for FP32 handles of the
+Laplace and 1/r^4 kernels).
 
 * FP64 handle: the product equals the oracle's skeleton-form product with the
   GPU's pivots to 1e-10 (cond K(sigma,tau) times rounding), and the factor-
@@ -61,7 +63,9 @@ def test_skeleton_fp32_vs_direct_multi_rhs_and_forces():
     ref = O.direct(pts, X[:, [0, 15, 16, 18]].astype(np.float64))
     assert rel(Y[:, [0, 15, 16, 18]], ref) <= 1e-6
     y1 = S.matvec(torch.from_numpy(np.ascontiguousarray(X[:, 16])).cuda()).double().cpu().numpy()
-    assert rel(Y[:, 16], y1) <= 1e-12   # the same FP64 sums in a pass of one column
+    # a pass of one column takes the same entries and sums; only the order of its
+    # triangular solve differs, which moves a few FP32 outputs by their last bit
+    assert rel(Y[:, 16], y1) <= 1e-9
     q = torch.from_numpy(I.rhs_uniform(n, 1, 275)[:, 0].astype(np.float32)).cuda()
     E, Fo = S.forces(q)
     rows = np.arange(0, n, 97)
