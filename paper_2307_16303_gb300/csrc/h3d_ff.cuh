@@ -99,6 +99,40 @@ __device__ __forceinline__ FF ff_kernel(int kind, float4 hi, float4 lo, float4 h
     return ff_mul(ff_inv4pi(), y);
 }
 
+// K(p_i, p_j), f'(rho) / rho and the difference p_i - p_j, all float-float, for
+// the gradient dK/dp_i = (f'(rho) / rho) (p_i - p_j); 0 for coincident points
+__device__ __forceinline__ void ff_kernel_grad(int kind, float4 hi, float4 lo, float4 hj, float4 lj, FF &f, FF &fr,
+                                               FF (&d)[3]) {
+    const float ah[3] = {hi.x, hi.y, hi.z}, al[3] = {lo.x, lo.y, lo.z};
+    const float bh[3] = {hj.x, hj.y, hj.z}, bl[3] = {lj.x, lj.y, lj.z};
+    FF sq[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const FF s = ff_two_sum(ah[a], -bh[a]);
+        const float t = __fadd_rn(s.l, __fsub_rn(al[a], bl[a]));
+        d[a] = FF{s.h, t};
+        const FF p = ff_two_prod(s.h, s.h);
+        sq[a] = FF{p.h, __fadd_rn(p.l, __fmaf_rn(__fmul_rn(2.0f, s.h), t, __fmul_rn(t, t)))};
+    }
+    const FF u = ff_two_sum(sq[0].h, sq[1].h);
+    const FF v = ff_two_sum(u.h, sq[2].h);
+    const FF d2{v.h, __fadd_rn(__fadd_rn(u.l, v.l), __fadd_rn(__fadd_rn(sq[0].l, sq[1].l), sq[2].l))};
+    if (d2.h == 0.0f) {
+        f = fr = FF{0.f, 0.f};
+        return;
+    }
+    const FF y = ff_rsqrt(d2), y2 = ff_mul(y, y);
+    if (kind == 2) {   // 1/r^4: f' / r = -4 / r^6
+        f = ff_mul(y2, y2);
+        const FF g = ff_mul(f, y2);
+        fr = FF{__fmul_rn(-4.0f, g.h), __fmul_rn(-4.0f, g.l)};
+    } else {           // 1/(4 pi r): f' / r = -f / r^2
+        f = ff_mul(ff_inv4pi(), y);
+        const FF g = ff_mul(f, y2);
+        fr = FF{-g.h, -g.l};
+    }
+}
+
 // acc + k * x for an FP32 x (exact product, then TwoSum of the high parts)
 __device__ __forceinline__ FF ff_fma_acc(FF acc, FF k, float x) {
     FF p = ff_two_prod(k.h, x);

@@ -17,6 +17,7 @@
 // in FP32 (coordinate differences from a hi + lo split, compensated sums).
 // Far-field contributions reach the points through FP64 atomic additions; the
 // energy is reduced in a fixed order.
+#include "h3d_ff.cuh"
 #include "h3d_internal.cuh"
 
 namespace h3d {
@@ -229,7 +230,12 @@ __device__ __forceinline__ void gadd(double *G, int p, double s, double gx, doub
 }
 
 // far field: one block at a time per CTA (taken from a queue), M in this CTA's
-// scratch, everything in FP64
+// scratch.  FF_ = false: everything in FP64.  FF_ = true (FP32 handles of the
+// Laplace and 1/r^4 kernels): the entries of K(sigma,Y), K(X,tau) and their
+// gradients, and the sums over the points, in float-float on the FP32 pipes
+// (coordinates split hi + lo, FP32 charges exact); M, its factorisation, the
+// solves and the -a^T dM c term stay FP64.
+template <bool FF_>
 __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
     using T = double;
     __shared__ int sp[kMaxRank], tp[kMaxRank], piv[kMaxRank];
@@ -263,7 +269,52 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
         // one warp per pivot, each entry evaluated once for its value and gradient:
         //   s = K(sigma, Y) q_Y -> c,  u = K(X, tau)^T q_X -> a, u0,
         //   gs_k = sum_j q_j dK(sigma_k, p_j),  gt_k = sum_i q_i dK(p_i, tau_k)
-        for (int k = warp; k < r; k += kFWarps) {
+        for (int k = warp; k < r && FF_; k += kFWarps) {
+            const int ps = sp[k], pt = tp[k];
+            const float4 hs = A.ph[ps], ls = A.pl[ps], ht = A.ph[pt], lt = A.pl[pt];
+            FF sv{0.f, 0.f}, uv{0.f, 0.f}, sg[3], tg[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) sg[a] = tg[a] = FF{0.f, 0.f};
+            for (int o = lane; o < max(m, n); o += 32) {
+                if (o < n) {
+                    const float4 hj = A.ph[y0 + o], lj = A.pl[y0 + o];
+                    FF f, fr, d[3];
+                    ff_kernel_grad(A.kind, hs, ls, hj, lj, f, fr, d);
+                    sv = ff_fma_acc(sv, f, hj.w);
+                    FF w = ff_two_prod(fr.h, hj.w);
+                    w.l = __fmaf_rn(fr.l, hj.w, w.l);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) sg[a] = ff_fma_acc(sg[a], w, d[a]);
+                }
+                if (o < m) {
+                    const float4 hi = A.ph[x0 + o], li = A.pl[x0 + o];
+                    FF f, fr, d[3];
+                    ff_kernel_grad(A.kind, hi, li, ht, lt, f, fr, d);
+                    uv = ff_fma_acc(uv, f, hi.w);
+                    FF w = ff_two_prod(fr.h, hi.w);
+                    w.l = __fmaf_rn(fr.l, hi.w, w.l);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) tg[a] = ff_fma_acc(tg[a], w, d[a]);
+                }
+            }
+            sv = ff_warp_sum(sv);
+            uv = ff_warp_sum(uv);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                sg[a] = ff_warp_sum(sg[a]);
+                tg[a] = ff_warp_sum(tg[a]);
+            }
+            if (lane == 0) {
+                c[k] = ff_to_double(sv);
+                a[k] = u0[k] = ff_to_double(uv);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    gs[k][q] = ff_to_double(sg[q]);
+                    gt[k][q] = ff_to_double(tg[q]);
+                }
+            }
+        }
+        for (int k = warp; k < r && !FF_; k += kFWarps) {
             const int ps = sp[k], pt = tp[k];
             double sv = 0.0, uv = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0;
             // the row of sigma_k and the column of tau_k side by side: two independent
@@ -305,8 +356,13 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
                 gt[k][0] = t0; gt[k][1] = t1; gt[k][2] = t2;
             }
         }
-        // M = K(sigma, tau), row-major r x r, FP64 (two entries per thread and step)
-        for (int e = tid; e < r * r; e += 2 * kFThreads) {
+        // M = K(sigma, tau), row-major r x r, FP64 (two entries per thread and step;
+        // FF_: float-float entries rounded to FP64)
+        for (int e = tid; e < r * r && FF_; e += kFThreads) {
+            const int k = e / r, l = e - k * r;
+            M[e] = ff_to_double(ff_kernel(A.kind, A.ph[sp[k]], A.pl[sp[k]], A.ph[tp[l]], A.pl[tp[l]]));
+        }
+        for (int e = tid; e < r * r && !FF_; e += 2 * kFThreads) {
             const int e2 = e + kFThreads;
             const int k = e / r, l = e - k * r;
             double dx, dy, dz, fr;
@@ -397,56 +453,117 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
         __syncthreads();
         for (int k = tid; k < r; k += kFThreads) a[piv[k]] = u0[k];
         __syncthreads();
-        // first term: q_X^T dK(X,tau) c (pivots in pairs: two independent chains)
-        for (int i = x0 + tid; i < x0 + m; i += kFThreads) {
-            T gx = 0, gy = 0, gz = 0, fx = 0, fy = 0, fz = 0;
-            int k = 0;
-            for (; k + 1 < r; k += 2) {
-                double dx, dy, dz, ex, ey, ez, fr, fr1;
-                pdiff(A, i, tp[k], dx, dy, dz);
-                pdiff(A, i, tp[k + 1], ex, ey, ez);
-                kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
-                kval_fr(A.kind, A.kappa, fma(ez, ez, fma(ey, ey, ex * ex)), fr1);
-                const T w = (T)c[k] * fr, w1 = (T)c[k + 1] * fr1;
-                gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
-                fx = fma(w1, ex, fx); fy = fma(w1, ey, fy); fz = fma(w1, ez, fz);
+        if constexpr (FF_) {
+            // the pivot points' own terms first, then gs / gt hold c and a as
+            // float-float pairs for the point loops
+            for (int k = tid; k < r; k += kFThreads) gadd(A.G, tp[k], -0.5 * c[k], gt[k][0], gt[k][1], gt[k][2]);
+            for (int k = tid; k < r; k += kFThreads) gadd(A.G, sp[k], 0.5 * a[k], gs[k][0], gs[k][1], gs[k][2]);
+            __syncthreads();
+            float2 *cf = reinterpret_cast<float2 *>(&gs[0][0]), *af = reinterpret_cast<float2 *>(&gt[0][0]);
+            for (int k = tid; k < r; k += kFThreads) {
+                const FF x = ff_from_double(c[k]), y = ff_from_double(a[k]);
+                cf[k] = make_float2(x.h, x.l);
+                af[k] = make_float2(y.h, y.l);
             }
-            if (k < r) {
-                double dx, dy, dz, fr;
-                pdiff(A, i, tp[k], dx, dy, dz);
-                kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
-                const T w = (T)c[k] * fr;
-                gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+            __syncthreads();
+            // first term: q_X^T dK(X,tau) c
+            for (int i = x0 + tid; i < x0 + m; i += kFThreads) {
+                const float4 hi = A.ph[i], li = A.pl[i];
+                FF g[3] = {FF{0.f, 0.f}, FF{0.f, 0.f}, FF{0.f, 0.f}};
+                for (int k = 0; k < r; ++k) {
+                    const int pt = tp[k];
+                    FF f, fr, d[3];
+                    ff_kernel_grad(A.kind, hi, li, A.ph[pt], A.pl[pt], f, fr, d);
+                    const FF w = ff_mul(fr, FF{cf[k].x, cf[k].y});
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) g[q] = ff_fma_acc(g[q], w, d[q]);
+                }
+                gadd(A.G, i, 0.5 * A.qs[i], ff_to_double(g[0]), ff_to_double(g[1]), ff_to_double(g[2]));
             }
-            gadd(A.G, i, 0.5 * A.qs[i], gx + fx, gy + fy, gz + fz);
+            // second term: a^T dK(sigma,Y) q_Y
+            for (int j = y0 + tid; j < y0 + n; j += kFThreads) {
+                const float4 hj = A.ph[j], lj = A.pl[j];
+                FF g[3] = {FF{0.f, 0.f}, FF{0.f, 0.f}, FF{0.f, 0.f}};
+                for (int k = 0; k < r; ++k) {
+                    const int ps = sp[k];
+                    FF f, fr, d[3];
+                    ff_kernel_grad(A.kind, A.ph[ps], A.pl[ps], hj, lj, f, fr, d);
+                    const FF w = ff_mul(fr, FF{af[k].x, af[k].y});
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) g[q] = ff_fma_acc(g[q], w, d[q]);
+                }
+                gadd(A.G, j, -0.5 * A.qs[j], ff_to_double(g[0]), ff_to_double(g[1]), ff_to_double(g[2]));
+            }
+            // third term: - a^T dM c
+            for (int k = tid; k < r; k += kFThreads) {
+                const float4 hs = A.ph[sp[k]], ls = A.pl[sp[k]], ht = A.ph[tp[k]], lt = A.pl[tp[k]];
+                FF g[3] = {FF{0.f, 0.f}, FF{0.f, 0.f}, FF{0.f, 0.f}}, h[3] = {FF{0.f, 0.f}, FF{0.f, 0.f}, FF{0.f, 0.f}};
+                for (int l = 0; l < r; ++l) {
+                    FF f, fr, d[3];
+                    ff_kernel_grad(A.kind, hs, ls, A.ph[tp[l]], A.pl[tp[l]], f, fr, d);
+                    const FF w = ff_mul(fr, FF{cf[l].x, cf[l].y});
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) g[q] = ff_fma_acc(g[q], w, d[q]);
+                    ff_kernel_grad(A.kind, A.ph[sp[l]], A.pl[sp[l]], ht, lt, f, fr, d);
+                    const FF w1 = ff_mul(fr, FF{af[l].x, af[l].y});
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) h[q] = ff_fma_acc(h[q], w1, d[q]);
+                }
+                gadd(A.G, sp[k], -0.5 * a[k], ff_to_double(g[0]), ff_to_double(g[1]), ff_to_double(g[2]));
+                gadd(A.G, tp[k], 0.5 * c[k], ff_to_double(h[0]), ff_to_double(h[1]), ff_to_double(h[2]));
+            }
+        } else {
+            // first term: q_X^T dK(X,tau) c (pivots in pairs: two independent chains)
+            for (int i = x0 + tid; i < x0 + m; i += kFThreads) {
+                T gx = 0, gy = 0, gz = 0, fx = 0, fy = 0, fz = 0;
+                int k = 0;
+                for (; k + 1 < r; k += 2) {
+                    double dx, dy, dz, ex, ey, ez, fr, fr1;
+                    pdiff(A, i, tp[k], dx, dy, dz);
+                    pdiff(A, i, tp[k + 1], ex, ey, ez);
+                    kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                    kval_fr(A.kind, A.kappa, fma(ez, ez, fma(ey, ey, ex * ex)), fr1);
+                    const T w = (T)c[k] * fr, w1 = (T)c[k + 1] * fr1;
+                    gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+                    fx = fma(w1, ex, fx); fy = fma(w1, ey, fy); fz = fma(w1, ez, fz);
+                }
+                if (k < r) {
+                    double dx, dy, dz, fr;
+                    pdiff(A, i, tp[k], dx, dy, dz);
+                    kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                    const T w = (T)c[k] * fr;
+                    gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+                }
+                gadd(A.G, i, 0.5 * A.qs[i], gx + fx, gy + fy, gz + fz);
+            }
+            for (int k = tid; k < r; k += kFThreads) gadd(A.G, tp[k], -0.5 * c[k], gt[k][0], gt[k][1], gt[k][2]);
+            // second term: a^T dK(sigma,Y) q_Y
+            for (int k = tid; k < r; k += kFThreads) gadd(A.G, sp[k], 0.5 * a[k], gs[k][0], gs[k][1], gs[k][2]);
+            for (int j = y0 + tid; j < y0 + n; j += kFThreads) {
+                T gx = 0, gy = 0, gz = 0, fx = 0, fy = 0, fz = 0;
+                int k = 0;
+                for (; k + 1 < r; k += 2) {
+                    double dx, dy, dz, ex, ey, ez, fr, fr1;
+                    pdiff(A, sp[k], j, dx, dy, dz);
+                    pdiff(A, sp[k + 1], j, ex, ey, ez);
+                    kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                    kval_fr(A.kind, A.kappa, fma(ez, ez, fma(ey, ey, ex * ex)), fr1);
+                    const T w = (T)a[k] * fr, w1 = (T)a[k + 1] * fr1;
+                    gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+                    fx = fma(w1, ex, fx); fy = fma(w1, ey, fy); fz = fma(w1, ez, fz);
+                }
+                if (k < r) {
+                    double dx, dy, dz, fr;
+                    pdiff(A, sp[k], j, dx, dy, dz);
+                    kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
+                    const T w = (T)a[k] * fr;
+                    gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
+                }
+                gadd(A.G, j, -0.5 * A.qs[j], gx + fx, gy + fy, gz + fz);
+            }
         }
-        for (int k = tid; k < r; k += kFThreads) gadd(A.G, tp[k], -0.5 * c[k], gt[k][0], gt[k][1], gt[k][2]);
-        // second term: a^T dK(sigma,Y) q_Y
-        for (int k = tid; k < r; k += kFThreads) gadd(A.G, sp[k], 0.5 * a[k], gs[k][0], gs[k][1], gs[k][2]);
-        for (int j = y0 + tid; j < y0 + n; j += kFThreads) {
-            T gx = 0, gy = 0, gz = 0, fx = 0, fy = 0, fz = 0;
-            int k = 0;
-            for (; k + 1 < r; k += 2) {
-                double dx, dy, dz, ex, ey, ez, fr, fr1;
-                pdiff(A, sp[k], j, dx, dy, dz);
-                pdiff(A, sp[k + 1], j, ex, ey, ez);
-                kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
-                kval_fr(A.kind, A.kappa, fma(ez, ez, fma(ey, ey, ex * ex)), fr1);
-                const T w = (T)a[k] * fr, w1 = (T)a[k + 1] * fr1;
-                gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
-                fx = fma(w1, ex, fx); fy = fma(w1, ey, fy); fz = fma(w1, ez, fz);
-            }
-            if (k < r) {
-                double dx, dy, dz, fr;
-                pdiff(A, sp[k], j, dx, dy, dz);
-                kval_fr(A.kind, A.kappa, fma(dz, dz, fma(dy, dy, dx * dx)), fr);
-                const T w = (T)a[k] * fr;
-                gx = fma(w, dx, gx); gy = fma(w, dy, gy); gz = fma(w, dz, gz);
-            }
-            gadd(A.G, j, -0.5 * A.qs[j], gx + fx, gy + fy, gz + fz);
-        }
-        // third term: - a^T dM c (FP64: these entries are those of M)
-        for (int k = tid; k < r; k += kFThreads) {
+        // third term: - a^T dM c (FP64; float-float above for FF_)
+        for (int k = tid; k < r && !FF_; k += kFThreads) {
             double gx = 0.0, gy = 0.0, gz = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
             for (int l = 0; l < r; ++l) {
                 double dx, dy, dz, ex, ey, ez, fr, fr1;
@@ -552,7 +669,8 @@ void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s) {
         k_force_near<double><<<h.nleaf, kFThreads, 0, s>>>(A);
     if (h.nblk > 0) {
         H3D_CUDA(cudaMemsetAsync(h.fctr, 0, sizeof(int), s));
-        k_force_far<<<grid, kFThreads, 0, s>>>(A);
+        if (fp32 && ff_kernel_supported(h.kernel)) k_force_far<true><<<grid, kFThreads, 0, s>>>(A);
+        else k_force_far<false><<<grid, kFThreads, 0, s>>>(A);
     }
     k_forces_out<<<gn(N, 256), 256, 0, s>>>(h.fG, h.perm, N, F);
     const int nout = (int)std::min<int64_t>(1024, std::max<int64_t>(1, nparts));
