@@ -158,6 +158,7 @@ struct Handle {
     int *lu_piv = nullptr;
     double *skel_s = nullptr, *skel_c = nullptr;  // K(sigma,Y) X and K(sigma,tau)^{-1} of it, 16 per pivot
     void *skel_xs = nullptr, *skel_near = nullptr; // pass columns: permuted x point-major, near field
+    void *skel_xmr = nullptr, *skel_nmr = nullptr; // blocks of 8 columns for the multi-column near field
     int skel_nq = 16;                             // columns per skeleton pass (memory-bound choice)
     int64_t *skel_src_ptr = nullptr, *skel_src_order = nullptr;   // blocks by source box (transpose)
     int *skel_next = nullptr;                     // next block of the source-side pass (work queue head)

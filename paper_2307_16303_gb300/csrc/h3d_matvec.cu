@@ -1730,6 +1730,18 @@ __global__ void __launch_bounds__(kSkThreads) k_skel_src(SkelArgs S, const T *__
         const int64_t bp = S.bigpo[b];
         if (bp >= 0) sv = S.sbig + bp * kSkNQ;   // a large block: its sums are ready
         int kb = bp >= 0 ? r : 0;
+        if (NQ == 1 && FF_ && kb == 0 && y1 - y0 <= 64) {
+            // few source points (the leaf level): lane k sums pivot k over all of
+            // them (the points are read by every lane at once), no warp sums
+            for (int k = lane; k < r; k += 32) {
+                const int ps = x0 + sg[k];
+                const float4 ph = S.fh[ps], pl = S.fl[ps];
+                FF a{0.f, 0.f};
+                for (int j = y0; j < y1; ++j) a = ff_fma_acc(a, ff_kernel(S.kind, ph, pl, S.fh[j], S.fl[j]), (float)xs[j]);
+                st_ff(sv + (int64_t)k * kSkNQ, a);
+            }
+            kb = r;
+        }
         if (NQ == 1 && FF_)   // as below, entries and sums in float-float
             for (; kb + 4 <= r; kb += 4) {
                 float4 ph[4], pl[4];
@@ -2010,7 +2022,18 @@ __global__ void __launch_bounds__(kSkThreads) k_skelT_src(SkelArgs S, const T *_
         const int *pv = S.lu_piv + po;
         const int64_t bp = S.bigpo[b];
         if (bp >= 0) sv = S.sbig + bp * kSkNQ;   // a large block: its sums are ready
-        for (int k = bp >= 0 ? r : 0; k < r; ++k) {
+        int k0 = bp >= 0 ? r : 0;
+        if (NQ == 1 && FF_ && k0 == 0 && x1 - x0 <= 64) {   // few target points: lane k takes pivot k
+            for (int k = lane; k < r; k += 32) {
+                const int pt = y0 + ta[k];
+                const float4 ph = S.fh[pt], pl = S.fl[pt];
+                FF a{0.f, 0.f};
+                for (int i = x0; i < x1; ++i) a = ff_fma_acc(a, ff_kernel(S.kind, S.fh[i], S.fl[i], ph, pl), (float)xs[i]);
+                st_ff(sv + (int64_t)k * kSkNQ, a);
+            }
+            k0 = r;
+        }
+        for (int k = k0; k < r; ++k) {
             const int pt = y0 + ta[k];
             double acc[NQ];
             if constexpr (FF_) {
@@ -2258,6 +2281,17 @@ void skel_launch(Handle &h, const SkelArgs &S, const LeafArgs &A, const T *xs, c
     }
 }
 
+// nearbuf[(q0 + q) n + i] = nmr[i kNQ + q], q < qn: a block of the multi-column
+// near field (point-major) into the skeleton pass's column-major near buffer
+template <class T>
+__global__ void k_mr_to_cols(const T *__restrict__ nmr, int64_t n, int q0, int qn, T *__restrict__ nearbuf) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * qn) return;
+    const int64_t i = e / qn;
+    const int q = (int)(e - i * qn);
+    nearbuf[(int64_t)(q0 + q) * n + i] = nmr[i * kNQ + q];
+}
+
 // one pass of up to kSkNQ columns: x, y column-major (N x nrhs), from column q0;
 // FF_: float-float entries (FP32 handles of a kernel float-float evaluates)
 template <class T, bool FF_>
@@ -2266,9 +2300,22 @@ void matvec_skel_pass(Handle &h, const T *x, T *y, int q0, int nq, bool transpos
     T *xs = (T *)h.skel_xs, *nearbuf = (T *)h.skel_near, *x1 = (T *)h.xs;
     LeafArgs A = leaf_args(h);
     k_skel_permute<T><<<gridn(n * nq, 256), 256, 0, s>>>(x, n, q0, nq, h.perm, xs);
-    // near field one column at a time on the side stream (the single-column kernel)
+    // near field on the side stream: blocks of kNQ columns through the multi-column
+    // kernel where the leaves fit it, else one column at a time
     const int near_grid = sizeof(T) == 4 ? std::min(h.nleaf, kNearCtasPerSm * num_sms()) : h.nleaf;
-    for (int q = 0; q < nq; ++q) {
+    const bool near8 = nq > 1 && h.skel_xmr;
+    for (int q = 0; near8 && q < nq; q += kNQ) {
+        const int qn = std::min(kNQ, nq - q);
+        k_permute_in_mr<T><<<gridn(n, 256), 256, 0, s>>>(x, n, q0 + q, qn, h.perm, (T *)h.skel_xmr);
+        H3D_CUDA(cudaEventRecord(h.ev_fork, s));
+        H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
+        k_near_mr<T><<<h.nleaf, kLeafThreads, 0, h.side_stream>>>(A, (const T *)h.skel_xmr, (T *)h.skel_nmr);
+        k_mr_to_cols<T><<<gridn(n * qn, 256), 256, 0, h.side_stream>>>((const T *)h.skel_nmr, n, q, qn,
+                                                                       nearbuf);
+        H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
+        H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));   // the buffers are reused by the next block
+    }
+    for (int q = 0; !near8 && q < nq; ++q) {
         k_permute_in<T><<<gridn(n, 256), 256, 0, s>>>(x + (size_t)(q0 + q) * n, h.perm, n, x1);
         H3D_CUDA(cudaEventRecord(h.ev_fork, s));
         H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
@@ -2584,6 +2631,10 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp) {
         h.sffl = h.mem.get<float4>((size_t)std::max<int64_t>(h.N, 1));
     }
     h.skel_xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
+    if (h.leaf_size <= kMaxLeafMR) {   // multi-column near field of the passes (blocks of kNQ columns)
+        h.skel_xmr = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQ * h.elem());
+        h.skel_nmr = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kNQ * h.elem());
+    }
     h.skel_near = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * kSkNQ * h.elem());
     {   // blocks grouped by source box (stable), for the transpose product
         const int64_t nboxes = h.n_boxes;

@@ -63,9 +63,10 @@ def test_skeleton_fp32_vs_direct_multi_rhs_and_forces():
     ref = O.direct(pts, X[:, [0, 15, 16, 18]].astype(np.float64))
     assert rel(Y[:, [0, 15, 16, 18]], ref) <= 1e-6
     y1 = S.matvec(torch.from_numpy(np.ascontiguousarray(X[:, 16])).cuda()).double().cpu().numpy()
-    # a pass of one column takes the same entries and sums; only the order of its
-    # triangular solve differs, which moves a few FP32 outputs by their last bit
-    assert rel(Y[:, 16], y1) <= 1e-9
+    # a pass of one column takes the same entries and sums; the order of its
+    # triangular solve differs, and its near field comes from the one-column
+    # kernel instead of the eight-column one (FP32 sums in another order)
+    assert rel(Y[:, 16], y1) <= 5e-7
     q = torch.from_numpy(I.rhs_uniform(n, 1, 275)[:, 0].astype(np.float32)).cuda()
     E, Fo = S.forces(q)
     rows = np.arange(0, n, 97)
