@@ -229,6 +229,75 @@ __device__ __forceinline__ void gadd(double *G, int p, double s, double gx, doub
     atomicAdd(G + 3 * (int64_t)p + 2, s * gz);
 }
 
+// P M = L U with partial pivoting (ties: the smaller row) by one warp for r <= 32,
+// lane i owning row i of M (row-major in the CTA's scratch), then
+//   c = U^{-1} L^{-1} P s   (s given in c),  the block energy 1/2 u^T c,
+//   a = P^T L^{-T} U^{-T} u (u given in a and u0);  piv[k] = original row of row k.
+// The same operations as the CTA-wide path, in one warp and without barriers.
+__device__ void factor_solve_warp(double *M, int r, double *c, double *a, const double *u0, int *piv, double *Eout,
+                                  int lane) {
+    const int i = lane;
+    const bool row = i < r;
+    double ci = row ? c[i] : 0.0;
+    int pi = i;
+    for (int k = 0; k < r; ++k) {
+        double v = (row && i >= k) ? fabs(M[(size_t)i * r + k]) : -1.0;
+        int bi = i;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > v || (ov == v && oi < bi)) { v = ov; bi = oi; }
+        }
+        // lane 0's choice for every lane (uniform even if a value were not finite),
+        // and every shuffle outside the branch
+        const int p = __shfl_sync(0xffffffffu, bi, 0);
+        const double cvk = __shfl_sync(0xffffffffu, ci, k), cvp = __shfl_sync(0xffffffffu, ci, p);
+        const int pk = __shfl_sync(0xffffffffu, pi, k), pp = __shfl_sync(0xffffffffu, pi, p);
+        if (p != k) {
+            for (int j = lane; j < r; j += 32) {
+                const double t = M[(size_t)k * r + j];
+                M[(size_t)k * r + j] = M[(size_t)p * r + j];
+                M[(size_t)p * r + j] = t;
+            }
+            if (i == k) { ci = cvp; pi = pp; }
+            if (i == p) { ci = cvk; pi = pk; }
+        }
+        __syncwarp();
+        const double ck = __shfl_sync(0xffffffffu, ci, k);
+        if (row && i > k) {
+            const double l = M[(size_t)i * r + k] / M[(size_t)k * r + k];
+            M[(size_t)i * r + k] = l;
+            for (int j = k + 1; j < r; ++j) M[(size_t)i * r + j] = fma(-l, M[(size_t)k * r + j], M[(size_t)i * r + j]);
+            ci = fma(-l, ck, ci);
+        }
+        __syncwarp();
+    }
+    for (int k = r - 1; k >= 0; --k) {   // U c = z
+        if (i == k) ci = ci / M[(size_t)k * r + k];
+        const double ck = __shfl_sync(0xffffffffu, ci, k);
+        if (row && i < k) ci = fma(-M[(size_t)i * r + k], ck, ci);
+    }
+    double e = row ? 0.5 * u0[i] * ci : 0.0;
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) *Eout = e;
+    double ai = row ? a[i] : 0.0;
+    for (int k = 0; k < r; ++k) {   // U^T z = u
+        if (i == k) ai = ai / M[(size_t)k * r + k];
+        const double ak = __shfl_sync(0xffffffffu, ai, k);
+        if (row && i > k) ai = fma(-M[(size_t)k * r + i], ak, ai);
+    }
+    for (int k = r - 1; k >= 0; --k) {   // L^T w = z (unit diagonal)
+        const double wk = __shfl_sync(0xffffffffu, ai, k);
+        if (row && i < k) ai = fma(-M[(size_t)k * r + i], wk, ai);
+    }
+    __syncwarp();
+    if (row) {
+        c[i] = ci;
+        piv[i] = pi;
+        a[pi] = ai;   // a <- P^T w
+    }
+}
+
 // far field: one block at a time per CTA (taken from a queue), M in this CTA's
 // scratch.  FF_ = false: everything in FP64.  FF_ = true (FP32 handles of the
 // Laplace and 1/r^4 kernels): the entries of K(sigma,Y), K(X,tau) and their
@@ -375,84 +444,90 @@ __global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
             }
             M[e] = v;
         }
-        for (int k = tid; k < r; k += kFThreads) piv[k] = k;
-        __syncthreads();
-        // energy of the block: 1/2 u^T c with c = M^{-1} s (after the solves)
-        // P M = L U (partial pivoting), the row swaps applied to c as well
-        for (int k = 0; k < r; ++k) {
-            if (warp == 0) {
-                double best = -1.0;
-                int bi = k;
-                for (int i = k + lane; i < r; i += 32) {
-                    const double v = fabs(M[(size_t)i * r + k]);
-                    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+        __syncthreads();   // M, s (in c) and u (in a, u0) are complete
+        if (r <= 32) {   // one warp factors and solves, lane i owning row i: no CTA barriers
+            if (warp == 0) factor_solve_warp(M, r, c, a, u0, piv, A.Epart + A.nleaf + b, lane);
+            __syncthreads();
+        } else {
+            for (int k = tid; k < r; k += kFThreads) piv[k] = k;
+            __syncthreads();
+            // energy of the block: 1/2 u^T c with c = M^{-1} s (after the solves)
+            // P M = L U (partial pivoting), the row swaps applied to c as well
+            for (int k = 0; k < r; ++k) {
+                if (warp == 0) {
+                    double best = -1.0;
+                    int bi = k;
+                    for (int i = k + lane; i < r; i += 32) {
+                        const double v = fabs(M[(size_t)i * r + k]);
+                        if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+                    }
+                    if (lane == 0) pmax = bi;
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+                __syncthreads();
+                const int p = pmax;
+                if (p != k) {
+                    for (int j = tid; j < r; j += kFThreads) {
+                        const double t = M[(size_t)k * r + j];
+                        M[(size_t)k * r + j] = M[(size_t)p * r + j];
+                        M[(size_t)p * r + j] = t;
+                    }
+                    if (tid == 0) {
+                        const double t = c[k]; c[k] = c[p]; c[p] = t;
+                        const int ti = piv[k]; piv[k] = piv[p]; piv[p] = ti;
+                    }
                 }
-                if (lane == 0) pmax = bi;
+                __syncthreads();
+                const double d = M[(size_t)k * r + k];
+                for (int i = k + 1 + tid; i < r; i += kFThreads) M[(size_t)i * r + k] /= d;   // L multipliers
+                __syncthreads();
+                const int rem = r - k - 1;
+                for (int e = tid; e < rem * rem; e += kFThreads) {
+                    const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+                    M[(size_t)i * r + j] -= M[(size_t)i * r + k] * M[(size_t)k * r + j];
+                }
+                if (tid == 0)
+                    for (int i = k + 1; i < r; ++i) c[i] -= M[(size_t)i * r + k] * c[k];
+                __syncthreads();
             }
-            __syncthreads();
-            const int p = pmax;
-            if (p != k) {
-                for (int j = tid; j < r; j += kFThreads) {
-                    const double t = M[(size_t)k * r + j];
-                    M[(size_t)k * r + j] = M[(size_t)p * r + j];
-                    M[(size_t)p * r + j] = t;
-                }
-                if (tid == 0) {
-                    const double t = c[k]; c[k] = c[p]; c[p] = t;
-                    const int ti = piv[k]; piv[k] = piv[p]; piv[p] = ti;
-                }
+            // c = U^{-1} (L^{-1} P s);  a = P^T L^{-T} U^{-T} u
+            for (int k = r - 1; k >= 0; --k) {
+                double t = 0.0;
+                for (int j = k + 1 + tid; j < r; j += kFThreads) t += M[(size_t)k * r + j] * c[j];
+                t = block_sum(t, red);
+                if (tid == 0) c[k] = (c[k] - t) / M[(size_t)k * r + k];
+                __syncthreads();
             }
-            __syncthreads();
-            const double d = M[(size_t)k * r + k];
-            for (int i = k + 1 + tid; i < r; i += kFThreads) M[(size_t)i * r + k] /= d;   // L multipliers
-            __syncthreads();
-            const int rem = r - k - 1;
-            for (int e = tid; e < rem * rem; e += kFThreads) {
-                const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-                M[(size_t)i * r + j] -= M[(size_t)i * r + k] * M[(size_t)k * r + j];
+            {   // energy 1/2 u^T c, u still intact in u0
+                double e = 0.0;
+                for (int k = tid; k < r; k += kFThreads) e += 0.5 * u0[k] * c[k];
+                e = block_sum(e, red);
+                if (tid == 0) A.Epart[A.nleaf + b] = e;
             }
-            if (tid == 0)
-                for (int i = k + 1; i < r; ++i) c[i] -= M[(size_t)i * r + k] * c[k];
+            for (int k = 0; k < r; ++k) {   // U^T z = u (z in a)
+                double t = 0.0;
+                for (int l = tid; l < k; l += kFThreads) t += M[(size_t)l * r + k] * a[l];
+                t = block_sum(t, red);
+                if (tid == 0) a[k] = (a[k] - t) / M[(size_t)k * r + k];
+                __syncthreads();
+            }
+            for (int k = r - 1; k >= 0; --k) {   // L^T w = z (unit diagonal; w in a)
+                double t = 0.0;
+                for (int l = k + 1 + tid; l < r; l += kFThreads) t += M[(size_t)l * r + k] * a[l];
+                t = block_sum(t, red);
+                if (tid == 0) a[k] -= t;
+                __syncthreads();
+            }
+            // a <- P^T w: the w entry at position k belongs to original row piv[k]
+            for (int k = tid; k < r; k += kFThreads) u0[k] = a[k];
+            __syncthreads();
+            for (int k = tid; k < r; k += kFThreads) a[piv[k]] = u0[k];
             __syncthreads();
         }
-        // c = U^{-1} (L^{-1} P s);  a = P^T L^{-T} U^{-T} u
-        for (int k = r - 1; k >= 0; --k) {
-            double t = 0.0;
-            for (int j = k + 1 + tid; j < r; j += kFThreads) t += M[(size_t)k * r + j] * c[j];
-            t = block_sum(t, red);
-            if (tid == 0) c[k] = (c[k] - t) / M[(size_t)k * r + k];
-            __syncthreads();
-        }
-        {   // energy 1/2 u^T c, u still intact in u0
-            double e = 0.0;
-            for (int k = tid; k < r; k += kFThreads) e += 0.5 * u0[k] * c[k];
-            e = block_sum(e, red);
-            if (tid == 0) A.Epart[A.nleaf + b] = e;
-        }
-        for (int k = 0; k < r; ++k) {   // U^T z = u (z in a)
-            double t = 0.0;
-            for (int l = tid; l < k; l += kFThreads) t += M[(size_t)l * r + k] * a[l];
-            t = block_sum(t, red);
-            if (tid == 0) a[k] = (a[k] - t) / M[(size_t)k * r + k];
-            __syncthreads();
-        }
-        for (int k = r - 1; k >= 0; --k) {   // L^T w = z (unit diagonal; w in a)
-            double t = 0.0;
-            for (int l = k + 1 + tid; l < r; l += kFThreads) t += M[(size_t)l * r + k] * a[l];
-            t = block_sum(t, red);
-            if (tid == 0) a[k] -= t;
-            __syncthreads();
-        }
-        // a <- P^T w: the w entry at position k belongs to original row piv[k]
-        for (int k = tid; k < r; k += kFThreads) u0[k] = a[k];
-        __syncthreads();
-        for (int k = tid; k < r; k += kFThreads) a[piv[k]] = u0[k];
-        __syncthreads();
         if constexpr (FF_) {
             // the pivot points' own terms first, then gs / gt hold c and a as
             // float-float pairs for the point loops
