@@ -26,6 +26,11 @@
  *   - O2: the HODLR3D matrix-vector product: dense self/edge/face
  *     blocks at the leaf level plus the low-rank blocks of every
  *     level                                                          (Alg. 2)
+ *   - optional symmetric storage: the kernel is symmetric, so
+ *     K(Y,X) = K(X,Y)^T; each unordered admissible pair {X, Y} is
+ *     compressed once, as the block whose target has the smaller
+ *     level-local index, and its mirror (Y, X) takes the transposed
+ *     factors V U^T and the swapped pivots (tau, sigma)     (Eq. prank transposed)
  *
  * Readings where the paper is silent (all shared with the CUDA path by
  * specification only, not by code):
@@ -234,6 +239,9 @@ typedef struct {
     int64_t *piv_off;     /* per block, into sigma/tau                          */
     int *sigma, *tau;     /* local row / column indices                         */
     int64_t n_piv;
+    /* symmetric storage: partner[b] = index of the block (src, tgt) of b's level */
+    int sym;
+    int64_t *partner;
 } h3do_t;
 
 typedef struct { uint64_t key; int64_t idx; } kv_t;
@@ -345,6 +353,7 @@ void h3do_free(h3do_t *h)
     free(h->lists.blk_level); free(h->lists.blk_tgt); free(h->lists.blk_src); free(h->lists.blk_cls);
     free(h->lists.near_tgt); free(h->lists.near_src); free(h->lists.near_cls);
     free(h->rank); free(h->piv_off); free(h->sigma); free(h->tau);
+    free(h->partner);
     free(h);
 }
 
@@ -588,7 +597,52 @@ static int block_cap(const h3do_t *h, int m, int n)
     return c < h->rank_cap ? c : h->rank_cap;
 }
 
-/* Alg. 1: compress every admissible block, keeping ranks and pivots only. */
+/* Symmetric storage.  A block (X, Y) is a mirror when its target's level-local
+ * index exceeds its source's; its partner is the block (Y, X), which the
+ * admissibility relation (symmetric in X and Y) always contains.            */
+static int is_mirror(const h3do_t *h, int64_t b)
+{
+    return h->sym && h->lists.blk_tgt[b] > h->lists.blk_src[b];
+}
+
+/* Blocks are listed in (level, target, source) order: binary search. */
+static int64_t find_block(const h3do_t *h, int l, int t, int s)
+{
+    int64_t lo = 0, hi = h->lists.n_blocks;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        int ml = h->lists.blk_level[mid], mt = h->lists.blk_tgt[mid], ms = h->lists.blk_src[mid];
+        if (ml < l || (ml == l && (mt < t || (mt == t && ms < s)))) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < h->lists.n_blocks && h->lists.blk_level[lo] == l && h->lists.blk_tgt[lo] == t &&
+        h->lists.blk_src[lo] == s)
+        return lo;
+    return -1;
+}
+
+/* Switch symmetric storage on (before any compression or frozen pivots). */
+int h3do_set_symmetric(h3do_t *h, int on)
+{
+    int64_t nb = h->lists.n_blocks;
+    if (h->have_pivots) return ST_ARG;
+    free(h->partner);
+    h->partner = NULL;
+    h->sym = 0;
+    if (!on) return ST_OK;
+    h->partner = (int64_t *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(int64_t));
+    if (!h->partner) return ST_OOM;
+    for (int64_t b = 0; b < nb; ++b) {
+        h->partner[b] = find_block(h, h->lists.blk_level[b], h->lists.blk_src[b], h->lists.blk_tgt[b]);
+        if (h->partner[b] < 0) { free(h->partner); h->partner = NULL; return ST_ARG; }
+    }
+    h->sym = 1;
+    return ST_OK;
+}
+
+/* Alg. 1: compress every admissible block, keeping ranks and pivots only
+ * (symmetric storage: the primary block of each pair; its mirror takes the
+ * same rank and the swapped pivots).                                        */
 int h3do_compress(h3do_t *h)
 {
     int64_t nb = h->lists.n_blocks;
@@ -601,6 +655,7 @@ int h3do_compress(h3do_t *h)
     for (int64_t b = 0; b < nb; ++b) {
         int64_t xs, ys; int m, n, cap, k = 0, s;
         double *U, *V;
+        if (is_mirror(h, b)) { rk[b] = 0; continue; }
         block_ranges(h, b, &xs, &m, &ys, &n);
         cap = block_cap(h, m, n);
         U = (double *)malloc((size_t)m * cap * sizeof(double));
@@ -620,14 +675,22 @@ int h3do_compress(h3do_t *h)
         int64_t tot = 0;
         free(h->rank); free(h->piv_off); free(h->sigma); free(h->tau);
         h->rank = rk;
+        for (int64_t b = 0; b < nb; ++b)
+            if (is_mirror(h, b)) rk[b] = rk[h->partner[b]];
         h->piv_off = (int64_t *)malloc((size_t)(nb + 1) * sizeof(int64_t));
         for (int64_t b = 0; b < nb; ++b) { h->piv_off[b] = tot; tot += rk[b]; }
         h->piv_off[nb] = tot;
         h->sigma = (int *)malloc((size_t)(tot > 0 ? tot : 1) * sizeof(int));
         h->tau = (int *)malloc((size_t)(tot > 0 ? tot : 1) * sizeof(int));
         for (int64_t b = 0; b < nb; ++b) {
-            memcpy(h->sigma + h->piv_off[b], sg[b], (size_t)rk[b] * sizeof(int));
-            memcpy(h->tau + h->piv_off[b], ta[b], (size_t)rk[b] * sizeof(int));
+            if (is_mirror(h, b)) {   /* rows of the mirror are the primary's columns */
+                int64_t p = h->partner[b];
+                memcpy(h->sigma + h->piv_off[b], ta[p], (size_t)rk[b] * sizeof(int));
+                memcpy(h->tau + h->piv_off[b], sg[p], (size_t)rk[b] * sizeof(int));
+            } else {
+                memcpy(h->sigma + h->piv_off[b], sg[b], (size_t)rk[b] * sizeof(int));
+                memcpy(h->tau + h->piv_off[b], ta[b], (size_t)rk[b] * sizeof(int));
+            }
         }
         h->n_piv = tot;
         h->have_pivots = 1;
@@ -663,6 +726,22 @@ int h3do_set_pivots(h3do_t *h, const int *rank, const int *sigma, const int *tau
             if (sigma[tot + k] < 0 || sigma[tot + k] >= m || tau[tot + k] < 0 || tau[tot + k] >= n) return ST_ARG;
         tot += rank[b];
     }
+    if (h->sym) {   /* a mirror must carry its primary's rank and swapped pivots */
+        int64_t *off = (int64_t *)malloc((size_t)(nb + 1) * sizeof(int64_t));
+        int bad = 0;
+        if (!off) return ST_OOM;
+        off[0] = 0;
+        for (int64_t b = 0; b < nb; ++b) off[b + 1] = off[b] + rank[b];
+        for (int64_t b = 0; b < nb && !bad; ++b) {
+            int64_t p = h->partner[b];
+            if (!is_mirror(h, b)) continue;
+            if (rank[b] != rank[p]) { bad = 1; break; }
+            for (int k = 0; k < rank[b]; ++k)
+                if (sigma[off[b] + k] != tau[off[p] + k] || tau[off[b] + k] != sigma[off[p] + k]) { bad = 1; break; }
+        }
+        free(off);
+        if (bad) return ST_ARG;
+    }
     free(h->rank); free(h->piv_off); free(h->sigma); free(h->tau);
     h->rank = (int *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(int));
     h->piv_off = (int64_t *)malloc((size_t)(nb + 1) * sizeof(int64_t));
@@ -685,12 +764,20 @@ int h3do_block_factors(const h3do_t *h, int64_t b, double *U, double *V)
     int64_t xs, ys; int m, n, k = 0, r;
     int *sg, *ta, st;
     if (!h->have_pivots || b < 0 || b >= h->lists.n_blocks) return ST_ARG;
-    block_ranges(h, b, &xs, &m, &ys, &n);
     r = h->rank[b];
     sg = (int *)malloc((size_t)(r > 0 ? r : 1) * sizeof(int));
     ta = (int *)malloc((size_t)(r > 0 ? r : 1) * sizeof(int));
-    st = aca_block(h, xs, m, ys, n, r, r, h->sigma + h->piv_off[b], h->tau + h->piv_off[b],
-                   U, V, &k, sg, ta);
+    if (is_mirror(h, b)) {
+        /* K(Y,X) ~ (U_p V_p^T)^T: the primary's factors, U and V exchanged */
+        int64_t p = h->partner[b];
+        block_ranges(h, p, &xs, &m, &ys, &n);
+        st = aca_block(h, xs, m, ys, n, r, r, h->sigma + h->piv_off[p], h->tau + h->piv_off[p],
+                       V, U, &k, sg, ta);
+    } else {
+        block_ranges(h, b, &xs, &m, &ys, &n);
+        st = aca_block(h, xs, m, ys, n, r, r, h->sigma + h->piv_off[b], h->tau + h->piv_off[b],
+                       U, V, &k, sg, ta);
+    }
     free(sg); free(ta);
     return st;
 }

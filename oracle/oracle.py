@@ -17,7 +17,10 @@ Functions and the passage of arXiv 2307.16303 each one follows:
   q^T K~ q / 2 and its gradient in the point positions with the pivots frozen
   (the cross form of Eq. prank differentiated entry by entry); with
   ``admissibility="strong"`` / ``"weak"`` the paper's comparison formats on the
-  same octree (H-matrix with eta = sqrt(3), Eq. adm; HODLR, Sec. 2.3).
+  same octree (H-matrix with eta = sqrt(3), Eq. adm; HODLR, Sec. 2.3); with
+  ``symmetric=True`` each unordered admissible pair compressed once, its
+  mirror block taking the transposed factors (K symmetric, Eq. prank
+  transposed).
 
 Pins (tests under ``tests/`` marked ``not gpu``) fix each function against
 something other than itself: closed-form potentials of symmetric point sets,
@@ -26,7 +29,9 @@ reproducing the block, the skeleton identity of Eq. prank checked with a dense
 solve, exact block counts derived by hand and by geometric brute force, the
 coverage of the N x N matrix by exactly one block per entry, the error falling
 with the ACA tolerance, and the rank growth by interaction class of Table
-"rankgrowth".  No function here is "parity unpinned".
+"rankgrowth", and, for symmetric storage, the product being an exactly
+symmetric matrix whose primary blocks carry the pivots of the ordered mode.
+No function here is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -104,6 +109,7 @@ def _load():
             "h3do_export_tree": (None, [P, P, P, P, P, P, P]),
             "h3do_export_lists": (None, [P, P, P, P, P, P, P, P]),
             "h3do_compress": (i32, [P]),
+            "h3do_set_symmetric": (i32, [P, i32]),
             "h3do_num_pivots": (i64, [P]),
             "h3do_get_pivots": (i32, [P, P, P, P]),
             "h3do_set_pivots": (i32, [P, P, P, P]),
@@ -194,7 +200,7 @@ class Oracle:
 
     def __init__(self, points, kernel: str = "laplace", leaf_size: int = 64, tol: float = 1e-7,
                  rank_cap: int = 512, kappa: float = 1.0, lo=(-1.0, -1.0, -1.0), side: float = 2.0,
-                 admissibility: str = "hodlr3d"):
+                 admissibility: str = "hodlr3d", symmetric: bool = False):
         lib = _load()
         self.points = np.ascontiguousarray(points, dtype=np.float64)
         self.N = self.points.shape[0]
@@ -209,6 +215,9 @@ class Oracle:
         self.L = lib.h3do_depth(self._h)
         self.n_blocks = lib.h3do_num_blocks(self._h)
         self.n_near = lib.h3do_num_near(self._h)
+        self.symmetric = bool(symmetric)
+        if symmetric:
+            _check(lib.h3do_set_symmetric(self._h, 1))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
