@@ -97,10 +97,26 @@ typedef enum {
  *             with the LU; memory is O(sum of r^2) instead of O(sum of r (m+n)).
  *             Supports every product call (passes of up to 16 columns, each
  *             entry evaluated once per pass), h3d_energy and h3d_forces;
- *             h3d_matvec_profile returns H3D_ERR_ARG.                           */
+ *             h3d_matvec_profile returns H3D_ERR_ARG.
+ *   SYMMETRIC factors as FACTORS, but every kernel here is symmetric
+ *             (K(Y,X) = K(X,Y)^T), so each unordered admissible pair {X, Y} is
+ *             compressed once, as the block whose target box has the smaller
+ *             index; the block (Y, X) is its transpose, V U^T, with the swapped
+ *             pivots (tau, sigma) (Eq. prank transposed).  The operator is then
+ *             symmetric, and h3d_matvec_T runs the forward product.  Pairs whose
+ *             factors fit in shared memory (most of the deep levels) are stored
+ *             once and read once per product for both directions; the others
+ *             are stored for both orders in the FACTORS layout.  The fused
+ *             pairs' two contributions are summed with FP64 atomic additions, so
+ *             results may differ in the last bits from run to run.  FP32 handles
+ *             compute products of more than one column in passes of 8 (no
+ *             tensor-core path).  h3d_export_pivots returns the mirrors' swapped
+ *             pivots; h3d_import_pivots requires them (H3D_ERR_ARG otherwise).
+ *             Batches take the graph form.                                   */
 typedef enum {
     H3D_STORE_FACTORS = 0,
-    H3D_STORE_SKELETON = 1
+    H3D_STORE_SKELETON = 1,
+    H3D_STORE_SYMMETRIC = 2
 } h3d_storage;
 
 typedef struct {
@@ -304,7 +320,8 @@ typedef struct {
     int64_t n_near;            /* dense self/edge/face leaf pairs                   */
     int max_rank;
     int64_t sum_rank;
-    int64_t factor_entries;    /* sum over blocks of r (m + n)                      */
+    int64_t factor_entries;    /* sum over blocks of r (m + n) (symmetric storage:
+                                  stored entries, fused pairs counted once)         */
     int64_t u_entries;         /* sum over blocks of r m (target-side factors)      */
     int64_t v_entries;         /* sum over blocks of r n (source-side factors)      */
     int64_t factor_bytes;      /* stored factor bytes including padding             */
@@ -320,6 +337,9 @@ h3d_status h3d_get_stats(h3d_handle h, h3d_stats *s);
  * durations in milliseconds over all right-hand sides to phase_ms[0..nphase):
  *   0 permutation of x, 1 source-side gather V^T x, 2 reduction of split
  *   gathers, 3 per-leaf kernel (near field + target-side U t + permutation of y).
+ * Symmetric storage: 1 is the fused pairs' kernel (both directions) and 2 the
+ *   gather of the other pairs with its reduction and the addition of the fused
+ *   contributions to the near field.
  * phase_ms: host, nphase >= 1 (at most 4 entries are written).              */
 h3d_status h3d_matvec_profile(h3d_handle h, const void *x, void *y, int nrhs, void *stream,
                               float *phase_ms, int nphase);

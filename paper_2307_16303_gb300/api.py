@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libh3d.so")
 KERNELS = {"laplace": 0, "yukawa": 1, "inv_r4": 2, "cos_r": 3}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_3xtf32": 2}
 ADMISSIBILITY = {"hodlr3d": 0, "strong": 1, "weak": 2}
-STORAGE = {"factors": 0, "skeleton": 1}
+STORAGE = {"factors": 0, "skeleton": 1, "symmetric": 2}
 STATUS_NAMES = {0: "H3D_OK", 1: "H3D_ERR_ARG", 2: "H3D_ERR_DOMAIN", 3: "H3D_ERR_OOM", 4: "H3D_ERR_CUDA",
                 5: "H3D_ERR_ACA_RANK", 6: "H3D_ERR_TIMEOUT", 7: "H3D_ERR_STATE", 8: "H3D_ERR_DEPTH"}
 

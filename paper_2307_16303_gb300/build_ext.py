@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libh3d.so")
-SOURCES = ["h3d_util.cu", "h3d_tree.cu", "h3d_aca.cu", "h3d_matvec.cu", "h3d_api.cu", "h3d_noalloc.cu", "h3d_energy.cu", "h3d_forces.cu", "h3d_batch.cu"]
+SOURCES = ["h3d_util.cu", "h3d_tree.cu", "h3d_aca.cu", "h3d_matvec.cu", "h3d_api.cu", "h3d_noalloc.cu", "h3d_energy.cu", "h3d_forces.cu", "h3d_batch.cu", "h3d_sym.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

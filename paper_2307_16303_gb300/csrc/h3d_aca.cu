@@ -378,6 +378,28 @@ __global__ void k_pack(const AcaJob *__restrict__ jobs, int njobs, const double 
     }
 }
 
+// fused pairs of symmetric storage: U and V of the job's block into its slot of
+// symF (column-major, leading dimensions ldm / ldn; padding cleared before)
+template <class T>
+__global__ void k_pack_sym(const AcaJob *__restrict__ jobs, int njobs, const double *__restrict__ scratch,
+                           const int *__restrict__ slot, const SymBlk *__restrict__ blks, T *__restrict__ F) {
+    const int j = blockIdx.x;
+    if (j >= njobs) return;
+    const AcaJob J = jobs[j];
+    const SymBlk B = blks[slot[J.blk]];
+    const int r = J.cap, m = J.m, n = J.n;
+    const double *Us = scratch + J.uoff, *Vs = scratch + J.voff;
+    T *Fu = F + B.off, *Fv = F + B.off + (int64_t)r * B.ldm;
+    for (int64_t e = threadIdx.x; e < (int64_t)m * r; e += blockDim.x) {
+        const int k = (int)(e / m), i = (int)(e - (int64_t)k * m);
+        Fu[(int64_t)k * B.ldm + i] = (T)Us[e];
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)n * r; e += blockDim.x) {
+        const int k = (int)(e / n), i = (int)(e - (int64_t)k * n);
+        Fv[(int64_t)k * B.ldn + i] = (T)Vs[e];
+    }
+}
+
 unsigned gridn(int64_t n, int t = kThreads) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 // Run one batch of jobs: small blocks one warp each, large ones a CTA each.
@@ -408,8 +430,11 @@ namespace {
 // host copies of the block geometry (for batch planning)
 struct BlockGeometry {
     std::vector<int> tgt, src, bstart, bend;
+    std::vector<int> partner;   // symmetric storage only: the block (src, tgt)
     int m(int64_t b) const { return bend[tgt[b]] - bstart[tgt[b]]; }
     int n(int64_t b) const { return bend[src[b]] - bstart[src[b]]; }
+    // symmetric storage: the block of a pair that is not compressed itself
+    bool mirror(int64_t b) const { return !partner.empty() && tgt[b] > src[b]; }
 };
 
 BlockGeometry block_geometry(const Handle &h, cudaStream_t s) {
@@ -417,6 +442,11 @@ BlockGeometry block_geometry(const Handle &h, cudaStream_t s) {
     BlockGeometry g;
     g.tgt.resize(nblk);
     g.src.resize(nblk);
+    if (h.symmetric()) {
+        g.partner.resize(nblk);
+        if (nblk > 0)
+            H3D_CUDA(cudaMemcpyAsync(g.partner.data(), h.blk_partner, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
     g.bstart.resize(nboxes);
     g.bend.resize(nboxes);
     if (nblk > 0) {
@@ -456,29 +486,69 @@ void form_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const B
     const int64_t offL = h.box_off[h.L];
     PackArgs P{h.blk_tgt, h.blk_src, h.cu, h.cv, h.R, h.ldv, h.box_leaf_lo, h.leaf_ld, h.point_leaf, h.box_start,
                h.ubase, h.vbase, h.leaf_lp, offL};
-    std::vector<AcaJob> small, large, all;
+    const bool sym = h.symmetric();
+    if (sym) H3D_CUDA(cudaMemsetAsync(h.symF, 0, (size_t)std::max<int64_t>(h.sym_elems, 4) * es, s));
+    // symmetric storage: pack jobs (pairs in the U / V layout, both orders) and fused pairs
+    AcaJob *d_pack = sym ? tmp.get<AcaJob>((size_t)2 * kMaxJobs) : nullptr;
+    std::vector<AcaJob> small, large, all, fused;
     int mcs = 0, mcl = 0;
     int64_t used = 0;
+    auto pack = [&](const AcaJob *d, int cnt) {
+        if (cnt == 0) return;
+        if (h.prec == H3D_FP64)
+            k_pack<double><<<(unsigned)cnt, kThreads, 0, s>>>(d, cnt, scratch2, P, (double *)h.U, (double *)h.V);
+        else
+            k_pack<float><<<(unsigned)cnt, kThreads, 0, s>>>(d, cnt, scratch2, P, (float *)h.U, (float *)h.V);
+        H3D_LAUNCH_CHECK();
+    };
     auto flush = [&]() {
         if (small.empty() && large.empty()) return;
         run_batch<true>(small, large, mcs, mcl, A, d_jobs, s);
         all.clear();
         all.insert(all.end(), small.begin(), small.end());
         all.insert(all.end(), large.begin(), large.end());
-        if (h.prec == H3D_FP64)
-            k_pack<double><<<(unsigned)all.size(), kThreads, 0, s>>>(d_jobs, (int)all.size(), scratch2, P,
-                                                                     (double *)h.U, (double *)h.V);
-        else
-            k_pack<float><<<(unsigned)all.size(), kThreads, 0, s>>>(d_jobs, (int)all.size(), scratch2, P,
-                                                                    (float *)h.U, (float *)h.V);
-        H3D_LAUNCH_CHECK();
+        if (!sym) {
+            pack(d_jobs, (int)all.size());
+        } else {
+            // a pair in the U / V layout is packed for (X, Y) and, transposed, for
+            // (Y, X): the mirror's U is the primary's V and the other way round
+            std::vector<AcaJob> both;
+            fused.clear();
+            for (const AcaJob &J : all) {
+                if (h.sym_slot_h[J.blk] >= 0) {
+                    fused.push_back(J);
+                    continue;
+                }
+                both.push_back(J);
+                AcaJob M = J;
+                M.blk = g.partner[J.blk];
+                M.m = J.n; M.n = J.m; M.xs = J.ys; M.ys = J.xs;
+                M.uoff = J.voff; M.voff = J.uoff;
+                both.push_back(M);
+            }
+            if (!both.empty()) {
+                H3D_CUDA(cudaMemcpyAsync(d_pack, both.data(), both.size() * sizeof(AcaJob), cudaMemcpyHostToDevice, s));
+                pack(d_pack, (int)both.size());
+            }
+            if (!fused.empty()) {
+                AcaJob *d_f = d_pack + both.size();
+                H3D_CUDA(cudaMemcpyAsync(d_f, fused.data(), fused.size() * sizeof(AcaJob), cudaMemcpyHostToDevice, s));
+                if (h.prec == H3D_FP64)
+                    k_pack_sym<double><<<(unsigned)fused.size(), kThreads, 0, s>>>(
+                        d_f, (int)fused.size(), scratch2, h.sym_slot, h.sym_blk, (double *)h.symF);
+                else
+                    k_pack_sym<float><<<(unsigned)fused.size(), kThreads, 0, s>>>(
+                        d_f, (int)fused.size(), scratch2, h.sym_slot, h.sym_blk, (float *)h.symF);
+                H3D_LAUNCH_CHECK();
+            }
+        }
         H3D_CUDA(cudaStreamSynchronize(s));
         small.clear(); large.clear();
         mcs = mcl = 0; used = 0;
     };
     for (int64_t b = 0; b < nblk; ++b) {
         const int r = rk[b];
-        if (r == 0) continue;
+        if (r == 0 || g.mirror(b)) continue;
         const int m = g.m(b), n = g.n(b);
         const int64_t need = (int64_t)r * (m + n);
         if (used + need > dbl2 || (int64_t)(small.size() + large.size()) >= kMaxJobs) flush();
@@ -492,6 +562,7 @@ void form_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const B
         else { large.push_back(J); mcl = std::max(mcl, r); }
     }
     flush();
+    if (d_pack) tmp.free_one(d_pack);
     tmp.free_one(d_jobs);
     tmp.free_one(scratch2);
 }
@@ -516,6 +587,14 @@ void import_pivots(Handle &h, const FrozenPivots &fp, const BlockGeometry &g, st
             seen_col[j] = b;
         }
     }
+    for (int64_t b = 0; b < nblk; ++b) {   // symmetric storage: mirrors carry the swapped pivots
+        if (!g.mirror(b)) continue;
+        const int p = g.partner[b];
+        if (rk[b] != rk[p]) fail(H3D_ERR_ARG);
+        for (int k = 0; k < rk[b]; ++k)
+            if (fp.sigma[poff_h[b] + k] != fp.tau[poff_h[p] + k] || fp.tau[poff_h[b] + k] != fp.sigma[poff_h[p] + k])
+                fail(H3D_ERR_ARG);
+    }
     h.sum_rank = poff_h[nblk];
     if (nblk > 0) {
         H3D_CUDA(cudaMemcpyAsync(h.rank, rk.data(), nblk * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -529,6 +608,75 @@ void import_pivots(Handle &h, const FrozenPivots &fp, const BlockGeometry &g, st
         H3D_CUDA(cudaMemcpyAsync(h.sigma, fp.sigma, h.sum_rank * sizeof(int), cudaMemcpyHostToDevice, s));
         H3D_CUDA(cudaMemcpyAsync(h.tau, fp.tau, h.sum_rank * sizeof(int), cudaMemcpyHostToDevice, s));
     }
+    H3D_CUDA(cudaStreamSynchronize(s));
+}
+
+// Symmetric storage: the pairs whose factors fit one shared-memory stage (rank
+// at most kSymMaxR), in list order, packed into groups that one bulk copy
+// brings in: a pair that a warp can take (rank <= kSymSmallR, at most
+// kSymSmallElems entries) joins the open group while the stage has room; a
+// larger one gets a group of its own.  Their ranks leave the U / V layout.
+void plan_symmetric(Handle &h, const BlockGeometry &g, const std::vector<int> &rk, std::vector<int> &lrk,
+                    cudaStream_t s) {
+    const int64_t nblk = h.nblk;
+    const int64_t es = (int64_t)h.elem();
+    const int64_t stage = es == 8 ? kSymStageF64 : kSymStageF32;
+    std::vector<SymBlk> blks;
+    std::vector<SymGroup> grps;
+    h.sym_slot_h.assign((size_t)nblk, -1);
+    h.sym_entries = 0;
+    int64_t off = 0;
+    SymGroup cur{};
+    bool open = false;
+    auto close = [&]() {
+        if (!open) return;
+        cur.bytes = (int)round_up((off - cur.off) * es, 16);
+        off = cur.off + cur.bytes / es;
+        grps.push_back(cur);
+        open = false;
+    };
+    for (int64_t b = 0; b < nblk; ++b) {
+        if (g.mirror(b)) continue;
+        const int r = rk[b];
+        if (r == 0 || r > kSymMaxR) continue;
+        const int m = g.m(b), n = g.n(b), ldm = m | 1, ldn = n | 1;
+        const int64_t el = (int64_t)r * (ldm + ldn);
+        if (el * es > stage) continue;
+        const bool big = r > kSymSmallR || el > kSymSmallElems;
+        if (big || !open || (off - cur.off + el) * es > stage) {
+            close();
+            cur = SymGroup{};
+            cur.off = off;
+            cur.b0 = (int)blks.size();
+            cur.big = big ? 1 : 0;
+            open = true;
+        }
+        SymBlk B{};
+        B.off = off;
+        B.xs = g.bstart[g.tgt[b]]; B.ys = g.bstart[g.src[b]];
+        B.m = m; B.n = n; B.r = r; B.ldm = ldm; B.ldn = ldn;
+        h.sym_slot_h[b] = (int)blks.size();
+        blks.push_back(B);
+        off += el;
+        ++cur.nb;
+        if (big) close();
+        lrk[b] = 0;
+        lrk[g.partner[b]] = 0;
+        h.sym_entries += (int64_t)r * (m + n);
+    }
+    close();
+    h.nsym = (int)blks.size();
+    h.nsym_grp = (int)grps.size();
+    h.sym_elems = off;
+    h.sym_blk = h.mem.get<SymBlk>(std::max<size_t>(blks.size(), 1));
+    h.sym_grp = h.mem.get<SymGroup>(std::max<size_t>(grps.size(), 1));
+    h.sym_slot = h.mem.get<int>((size_t)std::max<int64_t>(nblk, 1));
+    if (!blks.empty())
+        H3D_CUDA(cudaMemcpyAsync(h.sym_blk, blks.data(), blks.size() * sizeof(SymBlk), cudaMemcpyHostToDevice, s));
+    if (!grps.empty())
+        H3D_CUDA(cudaMemcpyAsync(h.sym_grp, grps.data(), grps.size() * sizeof(SymGroup), cudaMemcpyHostToDevice, s));
+    if (nblk > 0)
+        H3D_CUDA(cudaMemcpyAsync(h.sym_slot, h.sym_slot_h.data(), nblk * sizeof(int), cudaMemcpyHostToDevice, s));
     H3D_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -587,6 +735,7 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const 
                 mcs = mcl = 0; used = fused = 0;
             };
             for (int64_t b = 0; b < nblk; ++b) {
+                if (g.mirror(b)) continue;   // symmetric storage: compressed as its primary
                 const int m = g.m(b), n = g.n(b);
                 const int cap = std::min(std::min(m, n), h.rank_cap);
                 const int64_t need = (int64_t)cap * (m + n);
@@ -606,8 +755,16 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const 
         }
         if (read_scalar(h.d_err, s) & (1 << H3D_ERR_ACA_RANK)) fail(H3D_ERR_ACA_RANK);
 
-        // ranks -> pivot offsets, compact pivots
-        if (nblk > 0) H3D_CUDA(cudaMemcpyAsync(rk.data(), h.rank, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+        // ranks -> pivot offsets, compact pivots (a mirror takes its primary's rank)
+        if (nblk > 0) {
+            H3D_CUDA(cudaMemcpyAsync(rk.data(), h.rank, nblk * sizeof(int), cudaMemcpyDeviceToHost, s));
+            H3D_CUDA(cudaStreamSynchronize(s));
+        }
+        if (!g.partner.empty()) {
+            for (int64_t b = 0; b < nblk; ++b)
+                if (g.mirror(b)) rk[b] = rk[g.partner[b]];
+            if (nblk > 0) H3D_CUDA(cudaMemcpyAsync(h.rank, rk.data(), nblk * sizeof(int), cudaMemcpyHostToDevice, s));
+        }
         h.sum_rank = scan_exclusive(h.rank, h.piv_off, nblk, s, tmp);
         H3D_CUDA(cudaMemcpyAsync(h.piv_off + nblk, &h.sum_rank, sizeof(int64_t), cudaMemcpyHostToDevice, s));
         H3D_CUDA(cudaStreamSynchronize(s));
@@ -616,10 +773,28 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const 
         h.tau = h.mem.get<int>((size_t)std::max<int64_t>(h.sum_rank, 1));
         for (int64_t b0 = 0; b0 < nblk; b0 += kMaxJobs) {
             const int64_t nb = std::min(kMaxJobs, nblk - b0);
-            std::vector<AcaJob> jobs(nb);
-            for (int64_t q = 0; q < nb; ++q) { jobs[q].blk = (int)(b0 + q); jobs[q].poff = slot[b0 + q]; }
-            H3D_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), nb * sizeof(AcaJob), cudaMemcpyHostToDevice, s));
-            k_copy_pivots<<<(unsigned)nb, 64, 0, s>>>(d_jobs, (int)nb, h.rank, h.piv_off, ssig, stau, h.sigma, h.tau);
+            // own pivots first; then the mirrors, whose rows are their primary's
+            // columns (the pivot arrays passed the other way round)
+            std::vector<AcaJob> jobs, mir;
+            for (int64_t q = 0; q < nb; ++q) {
+                AcaJob J{};
+                J.blk = (int)(b0 + q);
+                if (g.mirror(b0 + q)) {
+                    J.poff = slot[g.partner[b0 + q]];
+                    mir.push_back(J);
+                } else {
+                    J.poff = slot[b0 + q];
+                    jobs.push_back(J);
+                }
+            }
+            const size_t nj = jobs.size();
+            jobs.insert(jobs.end(), mir.begin(), mir.end());
+            H3D_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(AcaJob), cudaMemcpyHostToDevice, s));
+            if (nj > 0)
+                k_copy_pivots<<<(unsigned)nj, 64, 0, s>>>(d_jobs, (int)nj, h.rank, h.piv_off, ssig, stau, h.sigma, h.tau);
+            if (!mir.empty())
+                k_copy_pivots<<<(unsigned)mir.size(), 64, 0, s>>>(d_jobs + nj, (int)mir.size(), h.rank, h.piv_off, stau,
+                                                                  ssig, h.sigma, h.tau);
             H3D_LAUNCH_CHECK();
             H3D_CUDA(cudaStreamSynchronize(s));
         }
@@ -632,21 +807,34 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const 
     h.max_rank = 0;
     for (int64_t b = 0; b < nblk; ++b) h.max_rank = std::max(h.max_rank, rk[b]);
 
+    // ---------------- symmetric storage: the fused pairs and the layout ranks
+    std::vector<int> lrk;
+    if (h.symmetric()) {
+        lrk = rk;
+        sym_prepare();
+        plan_symmetric(h, g, rk, lrk, s);
+        h.lrank = h.mem.get<int>((size_t)std::max<int64_t>(nblk, 1));
+        if (nblk > 0) H3D_CUDA(cudaMemcpyAsync(h.lrank, lrk.data(), nblk * sizeof(int), cudaMemcpyHostToDevice, s));
+    } else {
+        h.lrank = h.rank;
+    }
+    const std::vector<int> &lr = h.symmetric() ? lrk : rk;
+
     // ---------------- layout
     h.R = h.mem.get<int>((size_t)nboxes);
     h.cu = h.mem.get<int>((size_t)std::max<int64_t>(nblk, 1));
     h.Rv = h.mem.get<int>((size_t)nboxes);
     h.ldv = h.mem.get<int>((size_t)nboxes);
     h.cv = h.mem.get<int>((size_t)std::max<int64_t>(nblk, 1));
-    k_target_cols<<<gridn(nboxes), kThreads, 0, s>>>(h.tgt_ptr, h.rank, nboxes, h.R, h.cu);
+    k_target_cols<<<gridn(nboxes), kThreads, 0, s>>>(h.tgt_ptr, h.lrank, nboxes, h.R, h.cu);
     H3D_LAUNCH_CHECK();
     H3D_CUDA(cudaMemsetAsync(h.d_err, 0, sizeof(int), s));
-    k_source_cols<<<gridn(nboxes), kThreads, 0, s>>>(h.tgt_ptr, h.blk_partner, h.rank, nboxes, vw, h.Rv, h.ldv, h.cv,
+    k_source_cols<<<gridn(nboxes), kThreads, 0, s>>>(h.tgt_ptr, h.blk_partner, h.lrank, nboxes, vw, h.Rv, h.ldv, h.cv,
                                                       h.d_err);
     H3D_LAUNCH_CHECK();
     if (read_scalar(h.d_err, s) & (1 << H3D_ERR_STATE)) fail(H3D_ERR_STATE);
     h.tofs = h.mem.get<int64_t>((size_t)std::max<int64_t>(nblk, 1));
-    scan_exclusive(h.rank, h.tofs, nblk, s, tmp);
+    scan_exclusive(h.lrank, h.tofs, nblk, s, tmp);
     h.tbase = h.mem.get<int64_t>((size_t)nboxes);
     scan_exclusive(h.R, h.tbase, nboxes, s, tmp);
     h.vcol0 = h.mem.get<int64_t>((size_t)nboxes);
@@ -669,13 +857,16 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const 
     tmp.free_one(vsz);
     h.map_v = h.mem.get<int64_t>((size_t)std::max<int64_t>(h.sum_rank, 1));
     if (nblk > 0) {
-        k_map_v<<<gridn(nblk), kThreads, 0, s>>>(h.blk_src, h.rank, h.cv, h.vcol0, h.tofs, nblk, h.map_v);
+        k_map_v<<<gridn(nblk), kThreads, 0, s>>>(h.blk_src, h.lrank, h.cv, h.vcol0, h.tofs, nblk, h.map_v);
         H3D_LAUNCH_CHECK();
     }
+    // entries stored (symmetric storage: the layout's pairs in both orders, the
+    // fused pairs once)
     h.u_entries = h.v_entries = 0;
     for (int64_t b = 0; b < nblk; ++b) {
-        h.u_entries += (int64_t)rk[b] * g.m(b);
-        h.v_entries += (int64_t)rk[b] * g.n(b);
+        const int r = lr[b] > 0 ? lr[b] : (h.symmetric() && h.sym_slot_h[b] >= 0 ? rk[b] : 0);
+        h.u_entries += (int64_t)r * g.m(b);
+        h.v_entries += (int64_t)r * g.n(b);
     }
     h.factor_entries = h.u_entries + h.v_entries;
 
@@ -686,6 +877,10 @@ void build_factors(Handle &h, cudaStream_t s, Arena &tmp, int64_t budget, const 
     const size_t es = h.elem();
     h.U = h.mem.alloc((size_t)std::max<int64_t>(h.u_elems, 4) * es);
     h.V = h.mem.alloc((size_t)std::max<int64_t>(h.v_elems, 4) * es);
+    if (h.symmetric()) {
+        h.symF = h.mem.alloc((size_t)std::max<int64_t>(h.sym_elems, 4) * es);
+        h.sym_acc = h.mem.get<double>((size_t)h.N * 8);
+    }
 
     // ---------------- pass 2: frozen pivots -> U, V -> final layout
     form_factors(h, s, tmp, budget, g, rk, poff_h);

@@ -139,7 +139,8 @@ h3d_status h3d_build(const double *points, int64_t N, h3d_kernel kernel, int lea
         if (!std::isfinite(o.lo[d])) return H3D_ERR_ARG;
     if (!(o.kappa >= 0.0) || !std::isfinite(o.kappa)) return H3D_ERR_ARG;
     if (o.admissibility < H3D_ADM_HODLR3D || o.admissibility > H3D_ADM_WEAK) return H3D_ERR_ARG;
-    if (o.storage != H3D_STORE_FACTORS && o.storage != H3D_STORE_SKELETON) return H3D_ERR_ARG;
+    if (o.storage != H3D_STORE_FACTORS && o.storage != H3D_STORE_SKELETON && o.storage != H3D_STORE_SYMMETRIC)
+        return H3D_ERR_ARG;
     if (o.workspace_bytes < 0) return H3D_ERR_ARG;
     if (!is_device_ptr(points)) return H3D_ERR_ARG;
 
@@ -301,7 +302,7 @@ h3d_status h3d_get_stats(h3d_handle hh, h3d_stats *st) {
     st->v_entries = h.v_entries;
     st->factor_bytes = h.storage == H3D_STORE_SKELETON
                            ? h.lu_off_total * (int64_t)sizeof(double) + h.sum_rank * (int64_t)sizeof(int)
-                           : (h.u_elems + h.v_elems) * (int64_t)h.elem();
+                           : (h.u_elems + h.v_elems + h.sym_elems) * (int64_t)h.elem();
     st->near_interactions = h.near_interactions;
     st->device_bytes = (int64_t)h.mem.total();
     st->build_ms = h.build_ms;

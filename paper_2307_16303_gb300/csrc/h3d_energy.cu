@@ -59,15 +59,17 @@ void energy(Handle &h, const void *q, double *E, void *grad, cudaStream_t s) {
                           {(void **)&h.epart, kEnergyBlocks * sizeof(double)}});
     }
     run_matvec(h, q, h.ey, 1, false, s);
-    if (grad) run_matvec(h, q, h.eyT, 1, true, s);
+    // symmetric storage: A~^T q = A~ q, no second product
+    if (grad && !h.symmetric()) run_matvec(h, q, h.eyT, 1, true, s);
+    const void *yT = grad && h.symmetric() ? h.ey : h.eyT;
     const int nb = (int)std::min<int64_t>(kEnergyBlocks, (h.N + kEnergyThreads - 1) / kEnergyThreads);
     if (h.prec == H3D_FP64)
         k_energy_partial<double><<<nb, kEnergyThreads, 0, s>>>((const double *)q, (const double *)h.ey,
-                                                                (const double *)h.eyT, (double *)grad, h.N,
+                                                                (const double *)yT, (double *)grad, h.N,
                                                                 h.epart);
     else
         k_energy_partial<float><<<nb, kEnergyThreads, 0, s>>>((const float *)q, (const float *)h.ey,
-                                                               (const float *)h.eyT, (float *)grad, h.N, h.epart);
+                                                               (const float *)yT, (float *)grad, h.N, h.epart);
     k_energy_final<<<1, kEnergyThreads, 0, s>>>(h.epart, nb, E);
     H3D_LAUNCH_CHECK();
 }

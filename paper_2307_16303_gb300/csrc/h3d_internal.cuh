@@ -16,6 +16,15 @@
 //              rounded up, R'_Y = sum of ranks of the blocks whose source is Y.
 //   t          per block b, r_b entries at tofs_b (target-major order), so the
 //              coefficients of all blocks of a target box are contiguous.
+//   symmetric  (H3D_STORE_SYMMETRIC) each unordered pair {X, Y} is compressed
+//              once, as the block whose target has the smaller index.  Pairs
+//              whose factors fit one shared-memory stage ("fused" set) are kept
+//              once, block-major in symF: U (ldm x r) then V (ldn x r), both
+//              column-major with odd leading dimensions, blocks packed into
+//              16-byte aligned groups of at most one stage.  The other pairs are
+//              kept in the U / V layout above for both orders, the mirror (Y, X)
+//              holding the transposed factors; the layout counts only their
+//              ranks (lrank).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -143,6 +152,26 @@ struct TcGatherItem {
     int nrows, ncols, to_t;   // rows, valid columns, output kind
 };
 
+// Symmetric storage: one fused pair (offsets in elements of the factor type) and
+// one group of fused pairs that a single bulk copy brings into shared memory.
+struct SymBlk {
+    int64_t off;              // U at off, V at off + r * ldm (in symF)
+    int xs, ys, m, n, r;      // first sorted point and size of X and Y, rank
+    int ldm, ldn;             // odd leading dimensions (>= m, n)
+    int pad;
+};
+struct SymGroup {
+    int64_t off;              // first element (16-byte aligned)
+    int bytes;                // multiple of 16, at most one stage
+    int b0, nb;               // SymBlk range
+    int big;                  // one pair taken by the whole CTA (else one warp per pair)
+};
+constexpr int kSymStageF32 = 80 * 1024;   // stage bytes (FP32 / FP64 handles); two stages per CTA
+constexpr int kSymStageF64 = 64 * 1024;
+constexpr int kSymSmallR = 64;            // a warp takes a pair of rank <= 64 and at most
+constexpr int kSymSmallElems = 4096;      // this many factor entries; larger ones a CTA
+constexpr int kSymMaxR = 256;             // largest rank of a fused pair
+
 struct Handle {
     // parameters
     int64_t N = 0;
@@ -171,6 +200,19 @@ struct Handle {
     double *skel_sbig = nullptr;
     double tol = 0, kappa = 1.0, lo[3] = {-1, -1, -1}, side = 2.0;
     int L = 0;
+    // symmetric storage: per block its rank in the U / V layout (0 for fused
+    // pairs; the ranks themselves elsewhere), the fused pairs and their groups
+    int *lrank = nullptr;
+    int nsym = 0, nsym_grp = 0;
+    SymBlk *sym_blk = nullptr;
+    SymGroup *sym_grp = nullptr;
+    int *sym_slot = nullptr;                      // per block: fused slot, or -1 (mirrors too)
+    std::vector<int> sym_slot_h;                  // host copy
+    void *symF = nullptr;
+    int64_t sym_elems = 0;                        // stored entries of symF (with padding)
+    int64_t sym_entries = 0;                      // sum over fused pairs of r (m + n)
+    double *sym_acc = nullptr;                    // fused contributions, N x 8 doubles (Morton order)
+    bool symmetric() const { return storage == H3D_STORE_SYMMETRIC; }
 
     Arena mem;          // everything the handle keeps
     int *d_err = nullptr;
@@ -402,6 +444,13 @@ void build_skeleton(Handle &h, cudaStream_t s, Arena &tmp);
 void matvec_skeleton(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s);
 void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cudaStream_t s,
                 cudaEvent_t *ev = nullptr);  // h3d_matvec.cu; ev: 5 events per rhs
+// Symmetric storage (h3d_sym.cu): every fused pair's contribution to both of its
+// boxes into the handle's FP64 accumulator (N x nq, point-major, Morton order,
+// zeroed first); then out (N x nq, point-major: the near-field buffer) += it.
+// nq is 1 or 8.
+void sym_prepare();   // kernel attributes (once)
+void sym_product(Handle &h, const void *xs, int nq, cudaStream_t s);
+void sym_finish(Handle &h, void *out, int nq, cudaStream_t s);
 
 // One persistent launch for the single-column products of many operators
 // (h3d_batch.cu).  batch_plan_create returns nullptr when the handles cannot

@@ -1220,16 +1220,22 @@ void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s, cud
     k_near<T><<<near_grid, kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
     H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
     if (!transpose) {
+        const bool sym = h.symmetric();
+        if (sym) {   // symmetric storage: the fused pairs, both directions, beside the near field
+            sym_product(h, xs, 1, s);
+            if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
+        }
         if (h.ngtask > 0) {
             GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
             k_gather<T><<<h.ngtask, kGatherThreads, 0, s>>>(G, (const T *)h.V, xs, t, (T *)h.partial);
         }
-        if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
+        if (ev && !sym) H3D_CUDA(cudaEventRecord(ev[2], s));
         if (h.nsplit > 0) {
             SplitArgs S{h.split_box, h.split_ntask, h.split_pbase, h.Rv, h.ldv, h.vcol0, h.map_v};
             k_reduce_partials<T><<<h.nsplit, 256, 0, s>>>(S, (const T *)h.partial, t);
         }
         H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
+        if (sym) sym_finish(h, nearbuf, 1, s);
         if (ev) H3D_CUDA(cudaEventRecord(ev[3], s));
         k_leaf<T><<<h.nleaf, kLeafThreads, kLeafDynSmem, s>>>(A, (const T *)h.U, t, nearbuf, y);
         if (ev) H3D_CUDA(cudaEventRecord(ev[4], s));
@@ -1325,16 +1331,22 @@ void matvec_mr(Handle &h, const T *x, T *y, int q0, int nq, cudaStream_t s, cuda
     H3D_CUDA(cudaStreamWaitEvent(h.side_stream, h.ev_fork, 0));
     k_near_mr<T><<<h.nleaf, kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
     H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
+    const bool sym = h.symmetric();
+    if (sym) {   // symmetric storage: the fused pairs, both directions, 8 columns at once
+        sym_product(h, xs, kNQ, s);
+        if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
+    }
     if (h.ngtask > 0) {
         GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
         k_gather_mr<T><<<h.ngtask, kGatherThreads, 0, s>>>(G, (const T *)h.V, xs, t, (T *)h.partial_mr);
     }
-    if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
+    if (ev && !sym) H3D_CUDA(cudaEventRecord(ev[2], s));
     if (h.nsplit > 0) {
         SplitArgs S{h.split_box, h.split_ntask, h.split_pbase, h.Rv, h.ldv, h.vcol0, h.map_v};
         k_reduce_partials_mr<T><<<h.nsplit, 256, 0, s>>>(S, (const T *)h.partial_mr, t);
     }
     H3D_CUDA(cudaStreamWaitEvent(s, h.ev_join, 0));
+    if (sym) sym_finish(h, nearbuf, kNQ, s);
     if (ev) H3D_CUDA(cudaEventRecord(ev[3], s));
     k_leaf_mr<T><<<h.nleaf, kLeafThreads, kLeafDynSmem, s>>>(A, (const T *)h.U, t, nearbuf, y, n, q0, nq);
     if (ev) H3D_CUDA(cudaEventRecord(ev[4], s));
@@ -2499,7 +2511,7 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     }
     h.partial_elems = pel;
     // the skeleton storage's products use none of the factor-streaming scratch
-    const bool stream = h.storage == H3D_STORE_FACTORS;
+    const bool stream = h.storage != H3D_STORE_SKELETON;
     h.partial = h.mem.alloc((size_t)std::max<int64_t>(stream ? pel : 0, 4) * es);
     h.t = h.mem.alloc((size_t)std::max<int64_t>(stream ? h.sum_rank : 0, 4) * es);
     h.xs = h.mem.alloc((size_t)std::max<int64_t>(h.N, 4) * es);
@@ -2569,6 +2581,7 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
 }
 
 int matvec_passes(const Handle &h, int nrhs, bool transpose) {
+    if (h.symmetric()) transpose = false;   // the operator is symmetric
     if (use_wide(h, nrhs, transpose)) return (nrhs + kNQW - 1) / kNQW;
     if (nrhs > 1 && !transpose && h.leaf_size <= kMaxLeafMR) return (nrhs + kNQ - 1) / kNQ;
     return nrhs;
@@ -2690,6 +2703,7 @@ void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cud
         matvec_skeleton(h, x, y, nrhs, transpose, s);
         return;
     }
+    if (h.symmetric()) transpose = false;   // the operator is symmetric: A~^T = A~
     if (use_wide(h, nrhs, transpose)) {
         ensure_wide_scratch(h, s);
         for (int q0 = 0, b = 0; q0 < nrhs; q0 += kNQW, ++b)

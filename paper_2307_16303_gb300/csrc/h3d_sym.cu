@@ -1,0 +1,328 @@
+// h3d_sym.cu -- products of symmetric storage (H3D_STORE_SYMMETRIC): the pairs
+// whose factors are kept once ("fused" pairs).
+//
+// Every kernel here is symmetric, K(Y,X) = K(X,Y)^T, so the admissible blocks
+// (X, Y) and (Y, X) of Alg. 2 share one approximation K(X,Y) ~ U V^T (Eq. prank;
+// its transpose V U^T).  A fused pair is streamed from HBM once per product and
+// serves both directions:
+//   t  = V^T x_Y,   t' = U^T x_X,   y_X += U t,   y_Y += V t'.
+// The pair's factors (U then V, column-major, odd leading dimensions) come into
+// shared memory by one bulk copy per group of pairs, double-buffered, in a
+// persistent grid of one CTA per SM.  A group of small pairs (the leaf level)
+// is taken one pair per warp; a larger pair (the level above) by the whole CTA.
+// Both directions add into an FP64 accumulator with atomic additions (each
+// output row receives the contributions of all pairs it belongs to); after the
+// near field is done the accumulator is added to the near-field buffer, which
+// the leaf kernel then adds to the other pairs' far field.
+//
+// Sums: FP32 products are accumulated with fused multiply-adds in runs of four
+// terms, each run added with Kahan compensation (FP64 handles: plain FP64).
+#include "h3d_async.cuh"
+#include "h3d_internal.cuh"
+
+namespace h3d {
+
+namespace {
+
+struct SymArgs {
+    const SymBlk *blk;
+    const SymGroup *grp;
+    int ngrp;
+    int stage;                 // bytes per stage
+    const unsigned char *F;    // symF
+    int *err;                  // device-visible error word (a copy that did not arrive)
+};
+
+template <class T> struct KSum;
+template <> struct KSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float get() const { return s - c; }
+};
+template <> struct KSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
+// the NQ values of point i (point-major, i * NQ + q)
+template <class T, int NQ>
+__device__ __forceinline__ void load_x(const T *__restrict__ xs, int64_t i, T (&o)[NQ]) {
+    if constexpr (NQ == 8 && sizeof(T) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(xs + i * 8));
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(xs + i * 8) + 1);
+        o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+    } else if constexpr (NQ == 8) {
+        const double2 *p = reinterpret_cast<const double2 *>(xs + i * 8);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const double2 v = __ldg(p + h);
+            o[2 * h] = v.x;
+            o[2 * h + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) o[q] = __ldg(xs + i * NQ + q);
+    }
+}
+
+// the NQ coefficients of column k (shared memory, k * NQ + q)
+template <class T, int NQ>
+__device__ __forceinline__ void load_t(const T *t, int k, T (&o)[NQ]) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) o[q] = t[k * NQ + q];
+}
+
+// sum over l < len of c[l] x(x0 + l) for the NQ columns of x, in runs of four
+// fused multiply-adds
+template <class T, int NQ>
+__device__ __forceinline__ void dot_x(const T *c, int len, const T *__restrict__ xs, int64_t x0, KSum<T> (&a)[NQ]) {
+    int l = 0;
+    for (; l + 4 <= len; l += 4) {
+        T p[NQ], x[NQ];
+        load_x<T, NQ>(xs, x0 + l, x);
+        const T c0 = c[l];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) p[q] = c0 * x[q];
+#pragma unroll
+        for (int e = 1; e < 4; ++e) {
+            load_x<T, NQ>(xs, x0 + l + e, x);
+            const T ce = c[l + e];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) p[q] = fma(ce, x[q], p[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a[q].add(p[q]);
+    }
+    for (; l < len; ++l) {
+        T x[NQ];
+        load_x<T, NQ>(xs, x0 + l, x);
+        const T cl = c[l];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a[q].add(cl * x[q]);
+    }
+}
+
+// sum over k < r of row[k * ld] t(k) for the NQ coefficient columns, in runs of four
+template <class T, int NQ>
+__device__ __forceinline__ void dot_t(const T *row, int ld, int r, const T *t, KSum<T> (&a)[NQ]) {
+    int k = 0;
+    for (; k + 4 <= r; k += 4) {
+        T p[NQ], tv[NQ];
+        load_t<T, NQ>(t, k, tv);
+        const T u0 = row[k * ld];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) p[q] = u0 * tv[q];
+#pragma unroll
+        for (int e = 1; e < 4; ++e) {
+            load_t<T, NQ>(t, k + e, tv);
+            const T ue = row[(k + e) * ld];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) p[q] = fma(ue, tv[q], p[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a[q].add(p[q]);
+    }
+    for (; k < r; ++k) {
+        T tv[NQ];
+        load_t<T, NQ>(t, k, tv);
+        const T uk = row[k * ld];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a[q].add(uk * tv[q]);
+    }
+}
+
+// row i of U t (i < m) or of V t' (m <= i < m + n), added to its output row
+template <class T, int NQ>
+__device__ __forceinline__ void pair_row(const SymBlk &B, const T *U, const T *V, const T *tt, const T *tu, int i,
+                                         double *__restrict__ acc) {
+    const bool xu = i < B.m;
+    const int ii = xu ? i : i - B.m;
+    KSum<T> a[NQ];
+    dot_t<T, NQ>(xu ? U + ii : V + ii, xu ? B.ldm : B.ldn, B.r, xu ? tt : tu, a);
+    const int64_t o = ((int64_t)(xu ? B.xs : B.ys) + ii) * NQ;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) atomicAdd(acc + o + q, (double)a[q].get());
+}
+
+// One pair by one warp: lane k forms column k of t and t' (the odd leading
+// dimensions keep the lanes' column walks on distinct banks), then lane i
+// forms rows i of U t and V t'.  tw: 2 * kSymSmallR * NQ values of this warp.
+template <class T, int NQ>
+__device__ __forceinline__ void pair_warp(const SymBlk &B, const T *st, const T *__restrict__ xs,
+                                          double *__restrict__ acc, T *tw, int lane) {
+    const T *U = st, *V = st + (int64_t)B.r * B.ldm;
+    T *tt = tw, *tu = tw + kSymSmallR * NQ;
+    for (int k = lane; k < B.r; k += 32) {
+        KSum<T> a[NQ], c[NQ];
+        dot_x<T, NQ>(V + (int64_t)k * B.ldn, B.n, xs, B.ys, a);
+        dot_x<T, NQ>(U + (int64_t)k * B.ldm, B.m, xs, B.xs, c);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            tt[k * NQ + q] = a[q].get();
+            tu[k * NQ + q] = c[q].get();
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < B.m + B.n; i += 32) pair_row<T, NQ>(B, U, V, tt, tu, i, acc);
+    __syncwarp();
+}
+
+// One pair by the whole CTA: warp w forms the columns w, w + NW, ... of t and t'
+// (lanes over the rows, then a butterfly sum), then thread i rows i of U t and
+// V t'.  tb: 2 * kSymMaxR * NQ values.
+template <class T, int NQ, int NW>
+__device__ __forceinline__ void pair_cta(const SymBlk &B, const T *st, const T *__restrict__ xs,
+                                         double *__restrict__ acc, T *tb, int warp, int lane) {
+    const T *U = st, *V = st + (int64_t)B.r * B.ldm;
+    T *tt = tb, *tu = tb + kSymMaxR * NQ;
+    for (int d = warp; d < 2 * B.r; d += NW) {
+        const bool isv = d < B.r;
+        const int k = isv ? d : d - B.r;
+        const T *col = isv ? V + (int64_t)k * B.ldn : U + (int64_t)k * B.ldm;
+        const int len = isv ? B.n : B.m;
+        const int64_t x0 = isv ? B.ys : B.xs;
+        KSum<T> a[NQ];
+        for (int j = lane; j < len; j += 32) {
+            T x[NQ];
+            load_x<T, NQ>(xs, x0 + j, x);
+            const T cj = col[j];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) a[q].add(cj * x[q]);
+        }
+        T v[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            v[q] = a[q].get();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        }
+        if (lane == 0) {
+            T *dst = isv ? tt : tu;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) dst[k * NQ + q] = v[q];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < B.m + B.n; i += NW * 32) pair_row<T, NQ>(B, U, V, tt, tu, i, acc);
+}
+
+constexpr int kSymWarps1 = 16, kSymWarps8 = 8;   // warps per CTA for 1 and 8 columns
+
+template <class T, int NQ, int NW>
+constexpr size_t tbuf_elems() {
+    return (size_t)(NW * kSymSmallR * NQ * 2 > kSymMaxR * NQ * 2 ? NW * kSymSmallR * NQ * 2 : kSymMaxR * NQ * 2);
+}
+
+template <class T, int NQ, int NW>
+constexpr size_t sym_smem() {
+    return 2 * (size_t)(sizeof(T) == 8 ? kSymStageF64 : kSymStageF32) + tbuf_elems<T, NQ, NW>() * sizeof(T);
+}
+
+// Persistent: CTA c takes groups c, c + gridDim.x, ...; group j of a CTA lands
+// in stage j % 2, the copy of group j + 2 is issued once group j is done.
+template <class T, int NQ, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_sym(SymArgs S, const T *__restrict__ xs, double *__restrict__ acc) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[2];
+    T *tbuf = reinterpret_cast<T *>(smem + 2 * (size_t)S.stage);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g0 = blockIdx.x, gs = gridDim.x;
+    const int nmine = g0 < S.ngrp ? (S.ngrp - g0 + gs - 1) / gs : 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int j) {
+        const SymGroup G = S.grp[g0 + j * gs];
+        mbar_arrive_expect_tx(&bars[j & 1], (uint32_t)G.bytes);
+        bulk_copy_g2s(smem + (size_t)(j & 1) * S.stage, S.F + G.off * (int64_t)sizeof(T), (uint32_t)G.bytes,
+                      &bars[j & 1]);
+    };
+    if (threadIdx.x == 0)
+        for (int j = 0; j < min(2, nmine); ++j) issue(j);
+    for (int j = 0; j < nmine; ++j) {
+        const bool ok = mbar_wait(&bars[j & 1], (uint32_t)(j >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                *S.err = H3D_ERR_TIMEOUT;
+                for (int q = j; q < min(j + 2, nmine); ++q) mbar_wait(&bars[q & 1], (uint32_t)(q >> 1) & 1u);
+            }
+            return;
+        }
+        const SymGroup G = S.grp[g0 + j * gs];
+        const T *st = reinterpret_cast<const T *>(smem + (size_t)(j & 1) * S.stage);
+        if (G.big) {
+            pair_cta<T, NQ, NW>(S.blk[G.b0], st, xs, acc, tbuf, warp, lane);
+        } else {
+            T *tw = tbuf + (size_t)warp * kSymSmallR * NQ * 2;
+            for (int p = warp; p < G.nb; p += NW) {
+                const SymBlk B = S.blk[G.b0 + p];
+                pair_warp<T, NQ>(B, st + (B.off - G.off), xs, acc, tw, lane);
+            }
+        }
+        __syncthreads();   // stage j % 2 and the coefficient buffer are free again
+        if (threadIdx.x == 0 && j + 2 < nmine) issue(j + 2);
+    }
+}
+
+template <class T>
+__global__ void k_sym_add(T *__restrict__ out, const double *__restrict__ acc, int64_t n) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = (T)((double)out[e] + acc[e]);
+}
+
+template <class T, int NQ, int NW>
+void launch_sym(Handle &h, const T *xs, cudaStream_t s) {
+    SymArgs A{h.sym_blk, h.sym_grp, h.nsym_grp, sizeof(T) == 8 ? kSymStageF64 : kSymStageF32,
+              static_cast<const unsigned char *>(h.symF), h.d_async_err};
+    const int grid = std::min(h.nsym_grp, num_sms());
+    k_sym<T, NQ, NW><<<grid, NW * 32, sym_smem<T, NQ, NW>(), s>>>(A, xs, h.sym_acc);
+    H3D_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+void sym_prepare() {
+    static bool done = false;
+    if (done) return;
+    H3D_CUDA(cudaFuncSetAttribute(k_sym<float, 1, kSymWarps1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sym_smem<float, 1, kSymWarps1>()));
+    H3D_CUDA(cudaFuncSetAttribute(k_sym<float, 8, kSymWarps8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sym_smem<float, 8, kSymWarps8>()));
+    H3D_CUDA(cudaFuncSetAttribute(k_sym<double, 1, kSymWarps1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sym_smem<double, 1, kSymWarps1>()));
+    H3D_CUDA(cudaFuncSetAttribute(k_sym<double, 8, kSymWarps8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sym_smem<double, 8, kSymWarps8>()));
+    done = true;
+}
+
+void sym_product(Handle &h, const void *xs, int nq, cudaStream_t s) {
+    if (h.nsym_grp == 0) return;
+    H3D_CUDA(cudaMemsetAsync(h.sym_acc, 0, (size_t)h.N * nq * sizeof(double), s));
+    if (h.prec == H3D_FP64) {
+        if (nq == 1) launch_sym<double, 1, kSymWarps1>(h, (const double *)xs, s);
+        else launch_sym<double, 8, kSymWarps8>(h, (const double *)xs, s);
+    } else {
+        if (nq == 1) launch_sym<float, 1, kSymWarps1>(h, (const float *)xs, s);
+        else launch_sym<float, 8, kSymWarps8>(h, (const float *)xs, s);
+    }
+}
+
+void sym_finish(Handle &h, void *out, int nq, cudaStream_t s) {
+    if (h.nsym_grp == 0) return;
+    const int64_t n = h.N * nq;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, (n + 255) / 256);
+    if (h.prec == H3D_FP64) k_sym_add<double><<<grid, 256, 0, s>>>((double *)out, h.sym_acc, n);
+    else k_sym_add<float><<<grid, 256, 0, s>>>((float *)out, h.sym_acc, n);
+    H3D_LAUNCH_CHECK();
+}
+
+}  // namespace h3d
