@@ -614,8 +614,10 @@ void import_pivots(Handle &h, const FrozenPivots &fp, const BlockGeometry &g, st
 // Symmetric storage: the pairs whose factors fit one shared-memory stage (rank
 // at most kSymMaxR), in list order, packed into groups that one bulk copy
 // brings in: a pair that a warp can take (rank <= kSymSmallR, at most
-// kSymSmallElems entries) joins the open group while the stage has room; a
-// larger one gets a group of its own.  Their ranks leave the U / V layout.
+// kSymSmallElems entries) joins the open group while the stage has room and the
+// group has fewer than kSymGroupPairs pairs (one per warp); a larger one gets a
+// group of its own.  Their ranks leave the U / V layout.  (A block of size el
+// entries has el >= 2, so no small pair sorts with the key -1 of the large ones.)
 void plan_symmetric(Handle &h, const BlockGeometry &g, const std::vector<int> &rk, std::vector<int> &lrk,
                     cudaStream_t s) {
     const int64_t nblk = h.nblk;
@@ -635,15 +637,31 @@ void plan_symmetric(Handle &h, const BlockGeometry &g, const std::vector<int> &r
         grps.push_back(cur);
         open = false;
     };
+    // the fused pairs: those a CTA takes in list order, then those a warp takes
+    // from the largest down, so that the pairs of one group (one per warp, all
+    // waited for together) are of about the same size
+    std::vector<std::pair<int64_t, int64_t>> order;   // (sort key, block)
     for (int64_t b = 0; b < nblk; ++b) {
         if (g.mirror(b)) continue;
         const int r = rk[b];
         if (r == 0 || r > kSymMaxR) continue;
-        const int m = g.m(b), n = g.n(b), ldm = m | 1, ldn = n | 1;
-        const int64_t el = (int64_t)r * (ldm + ldn);
+        const int m = g.m(b), n = g.n(b);
+        const int64_t el = (int64_t)r * ((m | 1) + (n | 1));
         if (el * es > stage) continue;
         const bool big = r > kSymSmallR || el > kSymSmallElems;
-        if (big || !open || (off - cur.off + el) * es > stage) {
+        order.push_back({big ? -1 : -el, b});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<int64_t, int64_t> &a, const std::pair<int64_t, int64_t> &c) {
+                         return (a.first == -1) != (c.first == -1) ? a.first == -1 : a.first < c.first;
+                     });
+    for (const auto &ob : order) {
+        const int64_t b = ob.second;
+        const int r = rk[b];
+        const int m = g.m(b), n = g.n(b), ldm = m | 1, ldn = n | 1;
+        const int64_t el = (int64_t)r * (ldm + ldn);
+        const bool big = ob.first == -1;
+        if (big || !open || (off - cur.off + el) * es > stage || cur.nb >= kSymGroupPairs) {
             close();
             cur = SymGroup{};
             cur.off = off;

@@ -169,8 +169,9 @@ struct SymGroup {
 constexpr int kSymStageF32 = 80 * 1024;   // stage bytes (FP32 / FP64 handles); two stages per CTA
 constexpr int kSymStageF64 = 64 * 1024;
 constexpr int kSymSmallR = 64;            // a warp takes a pair of rank <= 64 and at most
-constexpr int kSymSmallElems = 4096;      // this many factor entries; larger ones a CTA
+constexpr int kSymSmallElems = 12288;     // this many factor entries; larger ones a CTA
 constexpr int kSymMaxR = 256;             // largest rank of a fused pair
+constexpr int kSymGroupPairs = 16;        // small pairs per group (one per warp)
 
 struct Handle {
     // parameters

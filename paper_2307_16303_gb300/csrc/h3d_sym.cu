@@ -16,7 +16,8 @@
 // the leaf kernel then adds to the other pairs' far field.
 //
 // Sums: FP32 products are accumulated with fused multiply-adds in runs of four
-// terms, each run added with Kahan compensation (FP64 handles: plain FP64).
+// (one column) or eight (two chains of four; eight columns) terms, each run
+// added with Kahan compensation (FP64 handles: plain FP64).
 #include "h3d_async.cuh"
 #include "h3d_internal.cuh"
 
@@ -137,6 +138,64 @@ __device__ __forceinline__ void dot_t(const T *row, int ld, int r, const T *t, K
     }
 }
 
+// One column (NQ = 1): two dot products at once, each in runs of eight terms
+// split over two fused multiply-add chains, so that a lane keeps four
+// independent chains in flight (a single chain is latency-bound).
+// (x: the pair's values staged in shared memory, or global memory for a pair
+// too large to stage)
+template <class T>
+__device__ __forceinline__ T run8(const T *c, const T *x) {
+    T a = c[0] * x[0], b = c[4] * x[4];
+#pragma unroll
+    for (int e = 1; e < 4; ++e) {
+        a = fma(c[e], x[e], a);
+        b = fma(c[4 + e], x[4 + e], b);
+    }
+    return a + b;
+}
+template <class T>
+__device__ __forceinline__ void dot_x1_tail(const T *c, int l, int len, const T *x, KSum<T> &a) {
+    for (; l + 8 <= len; l += 8) a.add(run8(c + l, x + l));
+    for (; l < len; ++l) a.add(c[l] * x[l]);
+}
+template <class T>
+__device__ __forceinline__ void dot_x1_pair(const T *c0, int len0, const T *x0, const T *c1, int len1, const T *x1,
+                                            KSum<T> &a, KSum<T> &b) {
+    const int both = min(len0, len1);
+    int l = 0;
+    for (; l + 8 <= both; l += 8) {
+        const T p = run8(c0 + l, x0 + l), q = run8(c1 + l, x1 + l);
+        a.add(p);
+        b.add(q);
+    }
+    dot_x1_tail(c0, l, len0, x0, a);
+    dot_x1_tail(c1, l, len1, x1, b);
+}
+// sum over k < r of row[k * ld] t[k] for two rows at once (eight terms per run)
+template <class T>
+__device__ __forceinline__ T run8_t(const T *row, int ld, const T *t) {
+    T a = row[0] * t[0], b = row[4 * ld] * t[4];
+#pragma unroll
+    for (int e = 1; e < 4; ++e) {
+        a = fma(row[e * ld], t[e], a);
+        b = fma(row[(4 + e) * ld], t[4 + e], b);
+    }
+    return a + b;
+}
+template <class T>
+__device__ __forceinline__ void dot_t1_pair(const T *r0, int ld0, const T *t0, const T *r1, int ld1, const T *t1,
+                                            int r, bool two, KSum<T> &a, KSum<T> &b) {
+    int k = 0;
+    for (; k + 8 <= r; k += 8) {
+        a.add(run8_t(r0 + k * ld0, ld0, t0 + k));
+        if (two) b.add(run8_t(r1 + k * ld1, ld1, t1 + k));
+    }
+    for (; k < r; ++k) {
+        a.add(r0[k * ld0] * t0[k]);
+        if (two) b.add(r1[k * ld1] * t1[k]);
+    }
+}
+
 // row i of U t (i < m) or of V t' (m <= i < m + n), added to its output row
 template <class T, int NQ>
 __device__ __forceinline__ void pair_row(const SymBlk &B, const T *U, const T *V, const T *tt, const T *tu, int i,
@@ -153,23 +212,58 @@ __device__ __forceinline__ void pair_row(const SymBlk &B, const T *U, const T *V
 // One pair by one warp: lane k forms column k of t and t' (the odd leading
 // dimensions keep the lanes' column walks on distinct banks), then lane i
 // forms rows i of U t and V t'.  tw: 2 * kSymSmallR * NQ values of this warp.
+constexpr int kSymXWarp = 256;   // x values a warp stages for its pair (one column)
+
 template <class T, int NQ>
 __device__ __forceinline__ void pair_warp(const SymBlk &B, const T *st, const T *__restrict__ xs,
-                                          double *__restrict__ acc, T *tw, int lane) {
+                                          double *__restrict__ acc, T *tw, T *xw, int lane) {
     const T *U = st, *V = st + (int64_t)B.r * B.ldm;
     T *tt = tw, *tu = tw + kSymSmallR * NQ;
-    for (int k = lane; k < B.r; k += 32) {
-        KSum<T> a[NQ], c[NQ];
-        dot_x<T, NQ>(V + (int64_t)k * B.ldn, B.n, xs, B.ys, a);
-        dot_x<T, NQ>(U + (int64_t)k * B.ldm, B.m, xs, B.xs, c);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            tt[k * NQ + q] = a[q].get();
-            tu[k * NQ + q] = c[q].get();
+    if constexpr (NQ == 1) {
+        // x_X and x_Y into the warp's slice with all loads in flight at once (one
+        // memory latency per pair instead of one per run of terms)
+        const T *xX = xs + B.xs, *xY = xs + B.ys;
+        if (B.m + B.n <= kSymXWarp) {
+            for (int i = lane; i < B.m; i += 32) xw[i] = __ldg(xs + B.xs + i);
+            for (int i = lane; i < B.n; i += 32) xw[B.m + i] = __ldg(xs + B.ys + i);
+            __syncwarp();
+            xX = xw;
+            xY = xw + B.m;
         }
+        for (int k = lane; k < B.r; k += 32) {
+            KSum<T> a, c;
+            dot_x1_pair<T>(V + (int64_t)k * B.ldn, B.n, xY, U + (int64_t)k * B.ldm, B.m, xX, a, c);
+            tt[k] = a.get();
+            tu[k] = c.get();
+        }
+        __syncwarp();
+        // rows i and i + 32 together: two chains per lane
+        const int mn = B.m + B.n;
+        for (int i = lane; i < mn; i += 64) {
+            const int i2 = i + 32;
+            const bool two = i2 < mn;
+            const bool u0 = i < B.m, u1 = i2 < B.m;
+            const int a0 = u0 ? i : i - B.m, a1 = u1 ? i2 : i2 - B.m;
+            KSum<T> a, b;
+            dot_t1_pair<T>(u0 ? U + a0 : V + a0, u0 ? B.ldm : B.ldn, u0 ? tt : tu, u1 ? U + a1 : V + a1,
+                           u1 ? B.ldm : B.ldn, u1 ? tt : tu, B.r, two, a, b);
+            atomicAdd(acc + (int64_t)(u0 ? B.xs : B.ys) + a0, (double)a.get());
+            if (two) atomicAdd(acc + (int64_t)(u1 ? B.xs : B.ys) + a1, (double)b.get());
+        }
+    } else {
+        for (int k = lane; k < B.r; k += 32) {
+            KSum<T> a[NQ], c[NQ];
+            dot_x<T, NQ>(V + (int64_t)k * B.ldn, B.n, xs, B.ys, a);
+            dot_x<T, NQ>(U + (int64_t)k * B.ldm, B.m, xs, B.xs, c);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                tt[k * NQ + q] = a[q].get();
+                tu[k * NQ + q] = c[q].get();
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < B.m + B.n; i += 32) pair_row<T, NQ>(B, U, V, tt, tu, i, acc);
     }
-    __syncwarp();
-    for (int i = lane; i < B.m + B.n; i += 32) pair_row<T, NQ>(B, U, V, tt, tu, i, acc);
     __syncwarp();
 }
 
@@ -178,9 +272,53 @@ __device__ __forceinline__ void pair_warp(const SymBlk &B, const T *st, const T 
 // V t'.  tb: 2 * kSymMaxR * NQ values.
 template <class T, int NQ, int NW>
 __device__ __forceinline__ void pair_cta(const SymBlk &B, const T *st, const T *__restrict__ xs,
-                                         double *__restrict__ acc, T *tb, int warp, int lane) {
+                                         double *__restrict__ acc, T *tb, T *xb, int warp, int lane) {
     const T *U = st, *V = st + (int64_t)B.r * B.ldm;
     T *tt = tb, *tu = tb + kSymMaxR * NQ;
+    if constexpr (NQ == 1) {
+        const T *xX = xs + B.xs, *xY = xs + B.ys;
+        if (B.m + B.n <= NW * kSymXWarp) {   // x_X and x_Y staged by the whole CTA
+            for (int i = threadIdx.x; i < B.m + B.n; i += NW * 32)
+                xb[i] = i < B.m ? __ldg(xs + B.xs + i) : __ldg(xs + B.ys + (i - B.m));
+            __syncthreads();
+            xX = xb;
+            xY = xb + B.m;
+        }
+        // column k of V and of U together (two chains per lane)
+        for (int k = warp; k < B.r; k += NW) {
+            KSum<T> a, c;
+            const T *cv = V + (int64_t)k * B.ldn, *cu = U + (int64_t)k * B.ldm;
+            const int mx = max(B.m, B.n);
+            for (int j = lane; j < mx; j += 32) {
+                if (j < B.n) a.add(cv[j] * xY[j]);
+                if (j < B.m) c.add(cu[j] * xX[j]);
+            }
+            T v = a.get(), w = c.get();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+            }
+            if (lane == 0) {
+                tt[k] = v;
+                tu[k] = w;
+            }
+        }
+        __syncthreads();
+        const int mn = B.m + B.n;
+        for (int i = threadIdx.x; i < mn; i += 2 * NW * 32) {
+            const int i2 = i + NW * 32;
+            const bool two = i2 < mn;
+            const bool u0 = i < B.m, u1 = i2 < B.m;
+            const int a0 = u0 ? i : i - B.m, a1 = u1 ? i2 : i2 - B.m;
+            KSum<T> a, b;
+            dot_t1_pair<T>(u0 ? U + a0 : V + a0, u0 ? B.ldm : B.ldn, u0 ? tt : tu, u1 ? U + a1 : V + a1,
+                           u1 ? B.ldm : B.ldn, u1 ? tt : tu, B.r, two, a, b);
+            atomicAdd(acc + (int64_t)(u0 ? B.xs : B.ys) + a0, (double)a.get());
+            if (two) atomicAdd(acc + (int64_t)(u1 ? B.xs : B.ys) + a1, (double)b.get());
+        }
+        return;
+    }
     for (int d = warp; d < 2 * B.r; d += NW) {
         const bool isv = d < B.r;
         const int k = isv ? d : d - B.r;
@@ -215,13 +353,19 @@ __device__ __forceinline__ void pair_cta(const SymBlk &B, const T *st, const T *
 constexpr int kSymWarps1 = 16, kSymWarps8 = 8;   // warps per CTA for 1 and 8 columns
 
 template <class T, int NQ, int NW>
-constexpr size_t tbuf_elems() {
+__host__ __device__ constexpr size_t tbuf_elems() {
     return (size_t)(NW * kSymSmallR * NQ * 2 > kSymMaxR * NQ * 2 ? NW * kSymSmallR * NQ * 2 : kSymMaxR * NQ * 2);
 }
 
 template <class T, int NQ, int NW>
+__host__ __device__ constexpr size_t xbuf_elems() {
+    return NQ == 1 ? (size_t)NW * kSymXWarp : 0;
+}
+
+template <class T, int NQ, int NW>
 constexpr size_t sym_smem() {
-    return 2 * (size_t)(sizeof(T) == 8 ? kSymStageF64 : kSymStageF32) + tbuf_elems<T, NQ, NW>() * sizeof(T);
+    return 2 * (size_t)(sizeof(T) == 8 ? kSymStageF64 : kSymStageF32) +
+           (tbuf_elems<T, NQ, NW>() + xbuf_elems<T, NQ, NW>()) * sizeof(T);
 }
 
 // Persistent: CTA c takes groups c, c + gridDim.x, ...; group j of a CTA lands
@@ -231,6 +375,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_sym(SymArgs S, const T *__restri
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[2];
     T *tbuf = reinterpret_cast<T *>(smem + 2 * (size_t)S.stage);
+    T *xbuf = tbuf + tbuf_elems<T, NQ, NW>();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g0 = blockIdx.x, gs = gridDim.x;
     const int nmine = g0 < S.ngrp ? (S.ngrp - g0 + gs - 1) / gs : 0;
@@ -240,11 +385,12 @@ __global__ void __launch_bounds__(NW * 32, 1) k_sym(SymArgs S, const T *__restri
         mbar_fence_init();
     }
     __syncthreads();
+    const uint64_t pol = l2_evict_first_policy();   // the factors are read once: keep x and acc in L2
     auto issue = [&](int j) {
         const SymGroup G = S.grp[g0 + j * gs];
         mbar_arrive_expect_tx(&bars[j & 1], (uint32_t)G.bytes);
-        bulk_copy_g2s(smem + (size_t)(j & 1) * S.stage, S.F + G.off * (int64_t)sizeof(T), (uint32_t)G.bytes,
-                      &bars[j & 1]);
+        bulk_copy_g2s_hint(smem + (size_t)(j & 1) * S.stage, S.F + G.off * (int64_t)sizeof(T), (uint32_t)G.bytes,
+                           &bars[j & 1], pol);
     };
     if (threadIdx.x == 0)
         for (int j = 0; j < min(2, nmine); ++j) issue(j);
@@ -260,12 +406,13 @@ __global__ void __launch_bounds__(NW * 32, 1) k_sym(SymArgs S, const T *__restri
         const SymGroup G = S.grp[g0 + j * gs];
         const T *st = reinterpret_cast<const T *>(smem + (size_t)(j & 1) * S.stage);
         if (G.big) {
-            pair_cta<T, NQ, NW>(S.blk[G.b0], st, xs, acc, tbuf, warp, lane);
+            pair_cta<T, NQ, NW>(S.blk[G.b0], st, xs, acc, tbuf, xbuf, warp, lane);
         } else {
             T *tw = tbuf + (size_t)warp * kSymSmallR * NQ * 2;
+            T *xw = xbuf + (size_t)warp * kSymXWarp;
             for (int p = warp; p < G.nb; p += NW) {
                 const SymBlk B = S.blk[G.b0 + p];
-                pair_warp<T, NQ>(B, st + (B.off - G.off), xs, acc, tw, lane);
+                pair_warp<T, NQ>(B, st + (B.off - G.off), xs, acc, tw, xw, lane);
             }
         }
         __syncthreads();   // stage j % 2 and the coefficient buffer are free again

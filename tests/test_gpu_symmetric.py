@@ -10,8 +10,7 @@
   1e-12.
 * FP32 at N = 262,144 (seed 1), leaf 128, tol 1e-7: one column and 19 columns
   against the FP64 direct sum O1 on 4,096 seeded rows to 1e-6, with fewer
-  stored factor bytes than the ordered handle (fused pairs of the level above
-  the leaves taken by whole CTAs).
+  stored factor bytes than the ordered handle.
 * The operator is symmetric: x^T A z = z^T A x, and the transpose product is the
   forward one.  Energy, its q-gradient and forces agree with the oracle's
   symmetric mode; moved points (pivots frozen) too.  Pivots that break the
@@ -108,9 +107,11 @@ def test_symmetric_fp32_cfg2_vs_direct(cfg2_sym):
     refX = O.direct_rows(pts, X[:, [0, 9, 18]].astype(np.float64), rows)
     for c, q in enumerate((0, 9, 18)):
         assert rel(Y[rows, q], refX[:, c]) <= 1e-6
+    # at this size only the leaf level's pairs fit a stage (the level above has
+    # ~512 points per box): fewer bytes, by less than at the 1M-point workload
     st = A.stats()
     P = H(pts, leaf_size=128, tol=1e-7)
-    assert st["factor_bytes"] < 0.8 * P.stats()["factor_bytes"]
+    assert st["factor_bytes"] < 0.9 * P.stats()["factor_bytes"]
     P.free()
 
 
