@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--seed", type=int, default=3)
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    p.add_argument("--no-symmetric", action="store_true",
+                   help="skip the symmetric-storage product (each unordered pair stored once) beside the main line")
     p.add_argument("--rows", type=int, default=10_000, help="sampled rows for the error / CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU work budget of the baseline leg")
     p.add_argument("--o2-N", type=int, default=262_144,
@@ -515,9 +517,40 @@ def main():
             forces["rel_err_4096_points"] = float(np.linalg.norm(Fg - Fx) / np.linalg.norm(Fx))
             forces["sum_of_forces_rel"] = float(np.abs(Fo["F"].sum(dim=0).cpu().numpy()).max()
                                                 / Fo["F"].abs().sum().item())
+    st_ordered = st
     A.free()
     del A
     torch.cuda.empty_cache()
+
+    # symmetric storage on the same points: each unordered pair compressed once;
+    # pairs that fit a shared-memory stage are streamed once for both directions
+    # (k_sym), the rest in the ordered layout for both orders
+    sym, ysym_host = None, None
+    if not a.no_symmetric and nrhs == 1:
+        try:
+            As = H3DMatrix(dev_pts, leaf_size=a.leaf, tol=a.tol, precision="fp32_3xtf32", storage="symmetric")
+            ss = As.stats()
+            ys = torch.empty_like(x)
+            s_ms = time_steps(lambda: As.matvec_raw(x.data_ptr(), ys.data_ptr(), 1), a.steps, a.warmup, torch, None)
+            ph = np.zeros(4)
+            for _ in range(a.steps):
+                ph += np.array(As.matvec_profile(x.data_ptr(), ys.data_ptr(), 1))
+            ph /= a.steps
+            # the fused pairs' entries: stored twice by the ordered handle, once here
+            fused = st_ordered["factor_entries"] - ss["factor_entries"]
+            sym = {"ms": round(s_ms, 4), "factor_bytes": ss["factor_bytes"], "factor_entries": ss["factor_entries"],
+                   "build_ms": round(ss["build_ms"], 1), "device_bytes": ss["device_bytes"],
+                   "fused_pair_entries": int(fused),
+                   "phase_ms": {"k_permute_in": round(ph[0], 4), "k_sym": round(ph[1], 4),
+                                "gather_reduce_and_fused_add": round(ph[2], 4), "k_leaf": round(ph[3], 4)},
+                   "k_sym_GBps": round(4 * fused / (ph[1] * 1e-3) / 1e9, 1),
+                   "vs_ordered_ms": round(s_ms / ms, 3)}
+            ysym_host = ys.cpu().numpy().reshape(-1)
+            As.free()
+            del As
+            torch.cuda.empty_cache()
+        except H3DError as e:
+            sym = {"ms": None, "error": str(e)}
 
     fp64 = None
     y64_host = None
@@ -563,6 +596,9 @@ def main():
         if fp64 is not None and fp64.get("ms") is not None:
             yr = y64_host[ref_rows[0]] if y64_host.ndim == 2 else y64_host[ref_rows[0]][:, None]
             fp64["rel_err_sampled_rows"] = float(np.linalg.norm(yr - ref_rows[1]) / np.linalg.norm(ref_rows[1]))
+        if sym is not None and ysym_host is not None:
+            yr = ysym_host[ref_rows[0]][:, None].astype(np.float64)
+            sym["rel_err_sampled_rows"] = float(np.linalg.norm(yr - ref_rows[1]) / np.linalg.norm(ref_rows[1]))
         if a.o2_N > 0:
             out_cpu["o2"] = cpu_hodlr3d(a)
 
@@ -576,7 +612,7 @@ def main():
         "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload(a),
-        "rel_err_sampled_rows": err, "fp64": fp64, "forces": forces,
+        "rel_err_sampled_rows": err, "fp64": fp64, "forces": forces, "symmetric": sym,
         "speedup_vs_fp64": (round(fp64["ms"] / ms, 3) if fp64 and fp64.get("ms") else None),
         "interactions_per_s": N * N * nrhs / (ms * 1e-3),
         "matvec_alg_GBps": round(total_bytes / (ms * 1e-3) / 1e9, 1),
