@@ -64,6 +64,9 @@ def parse():
                         "half sphere, Laplace / Yukawa alternating, FP32) as one persistent launch or one graph "
                         "(whichever the tuner picks; both reported) against separate products")
     p.add_argument("--batch-nmax", type=int, default=131072)
+    p.add_argument("--batch-storage", default="factors", choices=["factors", "symmetric"],
+                   help="storage of the members that fit in device memory (the rest take skeleton storage): "
+                        "ordered factors, or symmetric storage (each unordered pair once, fewer bytes)")
     p.add_argument("--batch-count", type=int, default=64, help="clouds in the batch (64: the batched workload)")
     p.add_argument("--batch-reserve-gb", type=float, default=24.0,
                    help="device memory kept free while clouds are built with stored factors; larger clouds then "
@@ -247,10 +250,11 @@ def run_reference(a):
 def run_batched(a):
     """Independent clouds: one batched product (persistent kernel or graph) against
     separate products.  Clouds are built smallest first with stored FP32 factors
-    while they fit in device memory (keeping --batch-reserve-gb free); larger
-    clouds then take the skeleton storage (pivots and LU of K(sigma,tau), FP64
-    entries recomputed), which only the graph form runs.  The factor members are
-    also timed as a batch of their own (persistent and graph)."""
+    (ordered, or symmetric storage with --batch-storage symmetric) while they fit
+    in device memory (keeping --batch-reserve-gb free); larger clouds then take
+    the skeleton storage (pivots and LU of K(sigma,tau), entries recomputed),
+    which only the graph form runs, as it does symmetric storage.  The factor
+    members are also timed as a batch of their own."""
     import torch
     from paper_2307_16303_gb300.api import H3DMatrix, H3DBatch, H3DError
     from oracle import oracle as O
@@ -267,17 +271,17 @@ def run_batched(a):
         p = I.uniform(n, 500 + c) if c % 2 == 0 else I.sphere(n, 500 + c)
         kern = "laplace" if (c // 2) % 2 == 0 else "yukawa"
         dev = torch.from_numpy(p).cuda()
-        kind = "factors"
+        kind = a.batch_storage
         if skeleton_from is not None or torch.cuda.mem_get_info()[0] - 1.3 * per_point * n < reserve:
             kind = "skeleton"
         try:
             m = H3DMatrix(dev, leaf_size=a.leaf, tol=a.tol, precision="fp32", kernel=kern, storage=kind)
         except H3DError as e:
-            if e.status != 3 or kind != "factors":
+            if e.status != 3 or kind == "skeleton":
                 raise
             kind = "skeleton"
             m = H3DMatrix(dev, leaf_size=a.leaf, tol=a.tol, precision="fp32", kernel=kern, storage=kind)
-        if kind == "factors":
+        if kind != "skeleton":
             per_point = max(per_point, m.stats()["device_bytes"] / n)
         elif skeleton_from is None:
             skeleton_from = n
@@ -286,7 +290,7 @@ def run_batched(a):
         del dev
     build_s = time.perf_counter() - t0
     ys = [torch.empty_like(x) for x in xs]
-    fac = [c for c in range(nc) if store[c] == "factors"]
+    fac = [c for c in range(nc) if store[c] != "skeleton"]
     skel = [c for c in range(nc) if store[c] == "skeleton"]
     peak, src = peaks()
 
@@ -348,11 +352,15 @@ def run_batched(a):
            "form": "persistent" if persistent else "graph", "ctas_per_sm": info["ctas_per_sm"],
            "graph_branches": branches if branches else info["branches"], "item_shapes": groups,
            "separate_products_ms": round(seq, 4), "speedup_vs_separate": round(seq / ms, 3), "forms": forms,
-           "storage": {"factor_members": len(fac), "factor_points": int(sum(sizes[c] for c in fac)),
+           "storage": {"factor_storage": a.batch_storage,
+                       "factor_members": len(fac), "factor_points": int(sum(sizes[c] for c in fac)),
                        "skeleton_members": len(skel), "skeleton_points": int(sum(sizes[c] for c in skel)),
                        "skeleton_from_N": skeleton_from, "factor_bytes": fbytes},
            "build_s": round(build_s, 1), "rel_err_sampled_rows": errs, "clocks": clk,
-           "gpu_launches": (1 if persistent else 5 * nc) * a.steps}
+           # kernels per product: ordered 5 (permute, near field, gather, reduce, leaf),
+           # symmetric 7 (and the fused pairs' kernel and its addition), skeleton ~6
+           "gpu_launches": (1 if persistent else sum(7 if store[c] == "symmetric" else 5 if store[c] == "factors"
+                                                     else 6 for c in range(nc))) * a.steps}
     if not skel:
         alg = fbytes + 8 * int(sizes.sum())
         gbs = alg / (ms * 1e-3) / 1e9
