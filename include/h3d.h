@@ -337,9 +337,10 @@ h3d_status h3d_get_stats(h3d_handle h, h3d_stats *s);
  * durations in milliseconds over all right-hand sides to phase_ms[0..nphase):
  *   0 permutation of x, 1 source-side gather V^T x, 2 reduction of split
  *   gathers, 3 per-leaf kernel (near field + target-side U t + permutation of y).
- * Symmetric storage: 1 is the fused pairs' kernel (both directions) and 2 the
- *   gather of the other pairs with its reduction and the addition of the fused
- *   contributions to the near field.
+ * Symmetric storage: 1 is the fused pairs' kernel (both directions, on a stream
+ *   of its own beside the other pairs' gather) and 2 the rest of that gather
+ *   with its reduction and the addition of the fused contributions to the near
+ *   field.
  * phase_ms: host, nphase >= 1 (at most 4 entries are written).              */
 h3d_status h3d_matvec_profile(h3d_handle h, const void *x, void *y, int nrhs, void *stream,
                               float *phase_ms, int nphase);

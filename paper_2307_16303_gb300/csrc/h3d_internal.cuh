@@ -223,6 +223,10 @@ struct Handle {
     // second stream for the near field, and the fork / join events
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // symmetric storage: the fused pairs' kernel on a stream of its own, beside
+    // the other pairs' gather (it is latency-bound and leaves HBM bandwidth free)
+    cudaStream_t sym_stream = nullptr;
+    cudaEvent_t ev_sym_fork = nullptr, ev_sym_join = nullptr;
     void *nearbuf = nullptr;                      // near-field result, Morton order (N)
     // multi-RHS scratch: blocks of 8 columns, point-major
     void *xs_mr = nullptr, *nearbuf_mr = nullptr, *t_mr = nullptr, *partial_mr = nullptr;
@@ -244,6 +248,10 @@ struct Handle {
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (side_stream) cudaStreamDestroy(side_stream);
+        if (sym_stream) cudaStreamSynchronize(sym_stream);
+        if (ev_sym_fork) cudaEventDestroy(ev_sym_fork);
+        if (ev_sym_join) cudaEventDestroy(ev_sym_join);
+        if (sym_stream) cudaStreamDestroy(sym_stream);
         if (h_async_err) cudaFreeHost(h_async_err);
     }
 
@@ -447,10 +455,11 @@ void run_matvec(Handle &h, const void *x, void *y, int nrhs, bool transpose, cud
                 cudaEvent_t *ev = nullptr);  // h3d_matvec.cu; ev: 5 events per rhs
 // Symmetric storage (h3d_sym.cu): every fused pair's contribution to both of its
 // boxes into the handle's FP64 accumulator (N x nq, point-major, Morton order,
-// zeroed first); then out (N x nq, point-major: the near-field buffer) += it.
-// nq is 1 or 8.
+// zeroed first), on the handle's sym_stream after the work already on s (ev, if
+// given, is recorded when the kernel is done); then, on s after it, out (N x nq,
+// point-major: the near-field buffer) += the accumulator.  nq is 1 or 8.
 void sym_prepare();   // kernel attributes (once)
-void sym_product(Handle &h, const void *xs, int nq, cudaStream_t s);
+void sym_product(Handle &h, const void *xs, int nq, cudaStream_t s, cudaEvent_t ev = nullptr);
 void sym_finish(Handle &h, void *out, int nq, cudaStream_t s);
 
 // One persistent launch for the single-column products of many operators

@@ -1221,10 +1221,7 @@ void matvec_one(Handle &h, const T *x, T *y, bool transpose, cudaStream_t s, cud
     H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
     if (!transpose) {
         const bool sym = h.symmetric();
-        if (sym) {   // symmetric storage: the fused pairs, both directions, beside the near field
-            sym_product(h, xs, 1, s);
-            if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
-        }
+        if (sym) sym_product(h, xs, 1, s, ev ? ev[2] : nullptr);   // the fused pairs, beside the gather
         if (h.ngtask > 0) {
             GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
             k_gather<T><<<h.ngtask, kGatherThreads, 0, s>>>(G, (const T *)h.V, xs, t, (T *)h.partial);
@@ -1332,10 +1329,7 @@ void matvec_mr(Handle &h, const T *x, T *y, int q0, int nq, cudaStream_t s, cuda
     k_near_mr<T><<<h.nleaf, kLeafThreads, 0, h.side_stream>>>(A, xs, nearbuf);
     H3D_CUDA(cudaEventRecord(h.ev_join, h.side_stream));
     const bool sym = h.symmetric();
-    if (sym) {   // symmetric storage: the fused pairs, both directions, 8 columns at once
-        sym_product(h, xs, kNQ, s);
-        if (ev) H3D_CUDA(cudaEventRecord(ev[2], s));
-    }
+    if (sym) sym_product(h, xs, kNQ, s, ev ? ev[2] : nullptr);   // the fused pairs, 8 columns, beside the gather
     if (h.ngtask > 0) {
         GatherArgs G{h.gtask, h.gtask_pbase, h.box_start, h.Rv, h.ldv, h.vbase, h.vcol0, h.map_v};
         k_gather_mr<T><<<h.ngtask, kGatherThreads, 0, s>>>(G, (const T *)h.V, xs, t, (T *)h.partial_mr);
@@ -2528,6 +2522,11 @@ void build_matvec_plan(Handle &h, cudaStream_t s, Arena &tmp) {
     H3D_CUDA(cudaStreamCreateWithPriority(&h.side_stream, cudaStreamNonBlocking, prio_hi));
     H3D_CUDA(cudaEventCreateWithFlags(&h.ev_fork, cudaEventDisableTiming));
     H3D_CUDA(cudaEventCreateWithFlags(&h.ev_join, cudaEventDisableTiming));
+    if (h.symmetric()) {
+        H3D_CUDA(cudaStreamCreateWithFlags(&h.sym_stream, cudaStreamNonBlocking));
+        H3D_CUDA(cudaEventCreateWithFlags(&h.ev_sym_fork, cudaEventDisableTiming));
+        H3D_CUDA(cudaEventCreateWithFlags(&h.ev_sym_join, cudaEventDisableTiming));
+    }
 
     // transpose partials: per level l < L, per leaf z, R of its ancestor
     const int L = h.L, nleaf = h.nleaf;

@@ -13,7 +13,9 @@
 // Both directions add into an FP64 accumulator with atomic additions (each
 // output row receives the contributions of all pairs it belongs to); after the
 // near field is done the accumulator is added to the near-field buffer, which
-// the leaf kernel then adds to the other pairs' far field.
+// the leaf kernel then adds to the other pairs' far field.  The kernel runs on a
+// stream of its own, beside the other pairs' gather: it is bound by latency
+// (one CTA of 16 warps per SM) and leaves most of the HBM bandwidth to it.
 //
 // Sums: FP32 products are accumulated with fused multiply-adds in runs of four
 // (one column) or eight (two chains of four; eight columns) terms, each run
@@ -370,8 +372,11 @@ constexpr size_t sym_smem() {
 
 // Persistent: CTA c takes groups c, c + gridDim.x, ...; group j of a CTA lands
 // in stage j % 2, the copy of group j + 2 is issued once group j is done.
+// (one column: at most 80 registers, so that the other pairs' gather and the
+// near field have room on every SM beside it)
 template <class T, int NQ, int NW>
-__global__ void __launch_bounds__(NW * 32, 1) k_sym(SymArgs S, const T *__restrict__ xs, double *__restrict__ acc) {
+__global__ void __maxnreg__(NQ == 1 ? 80 : 65536 / (NW * 32)) k_sym(SymArgs S, const T *__restrict__ xs,
+                                                                   double *__restrict__ acc) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[2];
     T *tbuf = reinterpret_cast<T *>(smem + 2 * (size_t)S.stage);
@@ -451,20 +456,26 @@ void sym_prepare() {
     done = true;
 }
 
-void sym_product(Handle &h, const void *xs, int nq, cudaStream_t s) {
+void sym_product(Handle &h, const void *xs, int nq, cudaStream_t s, cudaEvent_t ev) {
     if (h.nsym_grp == 0) return;
-    H3D_CUDA(cudaMemsetAsync(h.sym_acc, 0, (size_t)h.N * nq * sizeof(double), s));
+    cudaStream_t ss = h.sym_stream;
+    H3D_CUDA(cudaEventRecord(h.ev_sym_fork, s));
+    H3D_CUDA(cudaStreamWaitEvent(ss, h.ev_sym_fork, 0));
+    H3D_CUDA(cudaMemsetAsync(h.sym_acc, 0, (size_t)h.N * nq * sizeof(double), ss));
     if (h.prec == H3D_FP64) {
-        if (nq == 1) launch_sym<double, 1, kSymWarps1>(h, (const double *)xs, s);
-        else launch_sym<double, 8, kSymWarps8>(h, (const double *)xs, s);
+        if (nq == 1) launch_sym<double, 1, kSymWarps1>(h, (const double *)xs, ss);
+        else launch_sym<double, 8, kSymWarps8>(h, (const double *)xs, ss);
     } else {
-        if (nq == 1) launch_sym<float, 1, kSymWarps1>(h, (const float *)xs, s);
-        else launch_sym<float, 8, kSymWarps8>(h, (const float *)xs, s);
+        if (nq == 1) launch_sym<float, 1, kSymWarps1>(h, (const float *)xs, ss);
+        else launch_sym<float, 8, kSymWarps8>(h, (const float *)xs, ss);
     }
+    if (ev) H3D_CUDA(cudaEventRecord(ev, ss));
+    H3D_CUDA(cudaEventRecord(h.ev_sym_join, ss));
 }
 
 void sym_finish(Handle &h, void *out, int nq, cudaStream_t s) {
     if (h.nsym_grp == 0) return;
+    H3D_CUDA(cudaStreamWaitEvent(s, h.ev_sym_join, 0));
     const int64_t n = h.N * nq;
     const unsigned grid = (unsigned)std::max<int64_t>(1, (n + 255) / 256);
     if (h.prec == H3D_FP64) k_sym_add<double><<<grid, 256, 0, s>>>((double *)out, h.sym_acc, n);
