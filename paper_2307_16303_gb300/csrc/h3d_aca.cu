@@ -379,7 +379,8 @@ __global__ void k_pack(const AcaJob *__restrict__ jobs, int njobs, const double 
 }
 
 // fused pairs of symmetric storage: U and V of the job's block into its slot of
-// symF (column-major, leading dimensions ldm / ldn; padding cleared before)
+// symF (column-major, leading dimensions ldm / ldn; padding cleared before,
+// so padding rows hold zeros)
 template <class T>
 __global__ void k_pack_sym(const AcaJob *__restrict__ jobs, int njobs, const double *__restrict__ scratch,
                            const int *__restrict__ slot, const SymBlk *__restrict__ blks, T *__restrict__ F) {
@@ -646,7 +647,7 @@ void plan_symmetric(Handle &h, const BlockGeometry &g, const std::vector<int> &r
         const int r = rk[b];
         if (r == 0 || r > kSymMaxR) continue;
         const int m = g.m(b), n = g.n(b);
-        const int64_t el = (int64_t)r * ((m | 1) + (n | 1));
+        const int64_t el = (int64_t)r * (sym_ld(m) + sym_ld(n));
         if (el * es > stage) continue;
         const bool big = r > kSymSmallR || el > kSymSmallElems;
         order.push_back({big ? -1 : -el, b});
@@ -658,7 +659,7 @@ void plan_symmetric(Handle &h, const BlockGeometry &g, const std::vector<int> &r
     for (const auto &ob : order) {
         const int64_t b = ob.second;
         const int r = rk[b];
-        const int m = g.m(b), n = g.n(b), ldm = m | 1, ldn = n | 1;
+        const int m = g.m(b), n = g.n(b), ldm = sym_ld(m), ldn = sym_ld(n);
         const int64_t el = (int64_t)r * (ldm + ldn);
         const bool big = ob.first == -1;
         if (big || !open || (off - cur.off + el) * es > stage || cur.nb >= kSymGroupPairs) {

@@ -20,7 +20,7 @@
 //              once, as the block whose target has the smaller index.  Pairs
 //              whose factors fit one shared-memory stage ("fused" set) are kept
 //              once, block-major in symF: U (ldm x r) then V (ldn x r), both
-//              column-major with odd leading dimensions, blocks packed into
+//              column-major with leading dimensions = 2 (mod 4), blocks packed into
 //              16-byte aligned groups of at most one stage.  The other pairs are
 //              kept in the U / V layout above for both orders, the mirror (Y, X)
 //              holding the transposed factors; the layout counts only their
@@ -157,7 +157,7 @@ struct TcGatherItem {
 struct SymBlk {
     int64_t off;              // U at off, V at off + r * ldm (in symF)
     int xs, ys, m, n, r;      // first sorted point and size of X and Y, rank
-    int ldm, ldn;             // odd leading dimensions (>= m, n)
+    int ldm, ldn;             // leading dimensions (>= m, n, = 2 mod 4: sym_ld)
     int pad;
 };
 struct SymGroup {
@@ -166,6 +166,15 @@ struct SymGroup {
     int b0, nb;               // SymBlk range
     int big;                  // one pair taken by the whole CTA (else one warp per pair)
 };
+// Leading dimension of a fused pair's factor: the smallest ld >= m with
+// ld = 2 (mod 4).  Columns then start 8 bytes aligned (FP32 pairs of rows load
+// as one float2), and both the lanes' column walks (addresses k ld) and their
+// row walks touch distinct banks: ld / 2 is odd.
+__host__ __device__ inline int sym_ld(int m) {
+    int l = (m + 1) & ~1;
+    if ((l & 3) == 0) l += 2;
+    return l;
+}
 constexpr int kSymStageF32 = 80 * 1024;   // stage bytes (FP32 / FP64 handles); two stages per CTA
 constexpr int kSymStageF64 = 64 * 1024;
 constexpr int kSymSmallR = 64;            // a warp takes a pair of rank <= 64 and at most

@@ -6,7 +6,7 @@
 // its transpose V U^T).  A fused pair is streamed from HBM once per product and
 // serves both directions:
 //   t  = V^T x_Y,   t' = U^T x_X,   y_X += U t,   y_Y += V t'.
-// The pair's factors (U then V, column-major, odd leading dimensions) come into
+// The pair's factors (U then V, column-major, leading dimensions = 2 mod 4) come into
 // shared memory by one bulk copy per group of pairs, double-buffered, in a
 // persistent grid of one CTA per SM.  A group of small pairs (the leaf level)
 // is taken one pair per warp; a larger pair (the level above) by the whole CTA.
@@ -18,8 +18,8 @@
 // (one CTA of 16 warps per SM) and leaves most of the HBM bandwidth to it.
 //
 // Sums: FP32 products are accumulated with fused multiply-adds in runs of four
-// (one column) or eight (two chains of four; eight columns) terms, each run
-// added with Kahan compensation (FP64 handles: plain FP64).
+// or eight terms (one column: packed two-lane FP32 FMAs over pairs of rows),
+// each run added with Kahan compensation (FP64 handles: plain FP64).
 #include "h3d_async.cuh"
 #include "h3d_internal.cuh"
 
@@ -198,6 +198,93 @@ __device__ __forceinline__ void dot_t1_pair(const T *r0, int ld0, const T *t0, c
     }
 }
 
+// FP32, one column, packed pairs of rows (Blackwell's two-lane FP32 FMA): the
+// factors' columns start 8-byte aligned (sym_ld), x is staged with each segment
+// padded to an even length (zeros), so two terms are one 8-byte load and one
+// packed FMA.  run4x2: 8 terms as two 4-term chains (the two halves).
+__device__ __forceinline__ float run4x2(const float2 *c, const float2 *x) {
+    float2 a = __fmul2_rn(c[0], x[0]);
+#pragma unroll
+    for (int e = 1; e < 4; ++e) a = __ffma2_rn(c[e], x[e], a);
+    return a.x + a.y;
+}
+__device__ __forceinline__ void dot2_tail(const float2 *c, int p, int np, const float2 *x, KSum<float> &a) {
+    for (; p + 4 <= np; p += 4) a.add(run4x2(c + p, x + p));
+    for (; p < np; ++p) {
+        const float2 q = __fmul2_rn(c[p], x[p]);
+        a.add(q.x + q.y);
+    }
+}
+// two dot products at once (np0 and np1 pairs of terms)
+__device__ __forceinline__ void dot2_pair(const float2 *c0, int np0, const float2 *x0, const float2 *c1, int np1,
+                                          const float2 *x1, KSum<float> &a, KSum<float> &b) {
+    const int both = min(np0, np1);
+    int p = 0;
+    for (; p + 4 <= both; p += 4) {
+        const float u = run4x2(c0 + p, x0 + p), v = run4x2(c1 + p, x1 + p);
+        a.add(u);
+        b.add(v);
+    }
+    dot2_tail(c0, p, np0, x0, a);
+    dot2_tail(c1, p, np1, x1, b);
+}
+// rows (2p, 2p + 1) of a factor times t: col = &F[2p] (8-byte aligned), column
+// stride ld (even); eight k per run in two packed chains, each half of the
+// result Kahan-added
+__device__ __forceinline__ void rows2_t(const float *col, int ld, int r, const float *t, KSum<float> &a0,
+                                        KSum<float> &a1) {
+    int k = 0;
+    for (; k + 8 <= r; k += 8) {
+        float2 u = __fmul2_rn(*reinterpret_cast<const float2 *>(col + (int64_t)k * ld), make_float2(t[k], t[k]));
+        float2 v = __fmul2_rn(*reinterpret_cast<const float2 *>(col + (int64_t)(k + 4) * ld),
+                              make_float2(t[k + 4], t[k + 4]));
+#pragma unroll
+        for (int e = 1; e < 4; ++e) {
+            u = __ffma2_rn(*reinterpret_cast<const float2 *>(col + (int64_t)(k + e) * ld),
+                           make_float2(t[k + e], t[k + e]), u);
+            v = __ffma2_rn(*reinterpret_cast<const float2 *>(col + (int64_t)(k + 4 + e) * ld),
+                           make_float2(t[k + 4 + e], t[k + 4 + e]), v);
+        }
+        const float2 w = __fadd2_rn(u, v);
+        a0.add(w.x);
+        a1.add(w.y);
+    }
+    for (; k < r; ++k) {
+        const float2 w =
+            __fmul2_rn(*reinterpret_cast<const float2 *>(col + (int64_t)k * ld), make_float2(t[k], t[k]));
+        a0.add(w.x);
+        a1.add(w.y);
+    }
+}
+// x_X then x_Y into dst, each padded with zeros to an even length (threads
+// tid, tid + nthr, ...)
+__device__ __forceinline__ void stage_x2(float *dst, const float *__restrict__ xs, const SymBlk &B, int tid,
+                                         int nthr) {
+    const int mE = (B.m + 1) & ~1, nE = (B.n + 1) & ~1;
+    for (int i = tid; i < mE + nE; i += nthr) {
+        float v = 0.f;
+        if (i < B.m) v = __ldg(xs + B.xs + i);
+        else if (i >= mE && i - mE < B.n) v = __ldg(xs + B.ys + (i - mE));
+        dst[i] = v;
+    }
+}
+// the row pairs of U t and V t' (pairs p < PU of U, then of V), threads tid,
+// tid + nthr, ...; rows past m (n) are padding and not written
+__device__ __forceinline__ void rows2_out(const SymBlk &B, const float *U, const float *V, const float *tt,
+                                          const float *tu, double *__restrict__ acc, int tid, int nthr) {
+    const int PU = (B.m + 1) >> 1, PV = (B.n + 1) >> 1;
+    for (int p = tid; p < PU + PV; p += nthr) {
+        const bool xu = p < PU;
+        const int r0 = 2 * (xu ? p : p - PU);
+        KSum<float> a0, a1;
+        rows2_t(xu ? U + r0 : V + r0, xu ? B.ldm : B.ldn, B.r, xu ? tt : tu, a0, a1);
+        const int len = xu ? B.m : B.n;
+        double *o = acc + (int64_t)(xu ? B.xs : B.ys) + r0;
+        atomicAdd(o, (double)a0.get());
+        if (r0 + 1 < len) atomicAdd(o + 1, (double)a1.get());
+    }
+}
+
 // row i of U t (i < m) or of V t' (m <= i < m + n), added to its output row
 template <class T, int NQ>
 __device__ __forceinline__ void pair_row(const SymBlk &B, const T *U, const T *V, const T *tt, const T *tu, int i,
@@ -211,7 +298,7 @@ __device__ __forceinline__ void pair_row(const SymBlk &B, const T *U, const T *V
     for (int q = 0; q < NQ; ++q) atomicAdd(acc + o + q, (double)a[q].get());
 }
 
-// One pair by one warp: lane k forms column k of t and t' (the odd leading
+// One pair by one warp: lane k forms column k of t and t' (the leading
 // dimensions keep the lanes' column walks on distinct banks), then lane i
 // forms rows i of U t and V t'.  tw: 2 * kSymSmallR * NQ values of this warp.
 constexpr int kSymXWarp = 256;   // x values a warp stages for its pair (one column)
@@ -221,6 +308,25 @@ __device__ __forceinline__ void pair_warp(const SymBlk &B, const T *st, const T 
                                           double *__restrict__ acc, T *tw, T *xw, int lane) {
     const T *U = st, *V = st + (int64_t)B.r * B.ldm;
     T *tt = tw, *tu = tw + kSymSmallR * NQ;
+    if constexpr (NQ == 1 && sizeof(T) == 4) {
+        const int mE = (B.m + 1) & ~1, nE = (B.n + 1) & ~1;
+        if (mE + nE <= kSymXWarp) {   // packed pairs of rows
+            stage_x2(xw, xs, B, lane, 32);
+            __syncwarp();
+            const float2 *xX2 = reinterpret_cast<const float2 *>(xw), *xY2 = reinterpret_cast<const float2 *>(xw + mE);
+            for (int k = lane; k < B.r; k += 32) {
+                KSum<float> a, c;
+                dot2_pair(reinterpret_cast<const float2 *>(V + (int64_t)k * B.ldn), nE >> 1, xY2,
+                          reinterpret_cast<const float2 *>(U + (int64_t)k * B.ldm), mE >> 1, xX2, a, c);
+                tt[k] = a.get();
+                tu[k] = c.get();
+            }
+            __syncwarp();
+            rows2_out(B, U, V, tt, tu, acc, lane, 32);
+            __syncwarp();
+            return;
+        }
+    }
     if constexpr (NQ == 1) {
         // x_X and x_Y into the warp's slice with all loads in flight at once (one
         // memory latency per pair instead of one per run of terms)
@@ -277,6 +383,44 @@ __device__ __forceinline__ void pair_cta(const SymBlk &B, const T *st, const T *
                                          double *__restrict__ acc, T *tb, T *xb, int warp, int lane) {
     const T *U = st, *V = st + (int64_t)B.r * B.ldm;
     T *tt = tb, *tu = tb + kSymMaxR * NQ;
+    if constexpr (NQ == 1 && sizeof(T) == 4) {
+        const int mE = (B.m + 1) & ~1, nE = (B.n + 1) & ~1;
+        if (mE + nE <= NW * kSymXWarp) {   // packed pairs of rows
+            stage_x2(xb, xs, B, threadIdx.x, NW * 32);
+            __syncthreads();
+            const float2 *xX2 = reinterpret_cast<const float2 *>(xb), *xY2 = reinterpret_cast<const float2 *>(xb + mE);
+            // column k of V and of U: lanes over pairs of rows, then a butterfly sum
+            for (int k = warp; k < B.r; k += NW) {
+                KSum<float> a, c;
+                const float2 *cv = reinterpret_cast<const float2 *>(V + (int64_t)k * B.ldn);
+                const float2 *cu = reinterpret_cast<const float2 *>(U + (int64_t)k * B.ldm);
+                const int mx = max(mE, nE) >> 1;
+                for (int q = lane; q < mx; q += 32) {
+                    if (2 * q < nE) {
+                        const float2 w = __fmul2_rn(cv[q], xY2[q]);
+                        a.add(w.x + w.y);
+                    }
+                    if (2 * q < mE) {
+                        const float2 w = __fmul2_rn(cu[q], xX2[q]);
+                        c.add(w.x + w.y);
+                    }
+                }
+                float v = a.get(), w = c.get();
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+                    w += __shfl_xor_sync(0xffffffffu, w, o);
+                }
+                if (lane == 0) {
+                    tt[k] = v;
+                    tu[k] = w;
+                }
+            }
+            __syncthreads();
+            rows2_out(B, U, V, tt, tu, acc, threadIdx.x, NW * 32);
+            return;
+        }
+    }
     if constexpr (NQ == 1) {
         const T *xX = xs + B.xs, *xY = xs + B.ys;
         if (B.m + B.n <= NW * kSymXWarp) {   // x_X and x_Y staged by the whole CTA
