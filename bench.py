@@ -77,8 +77,11 @@ def parse():
     p.add_argument("--points", default="uniform", choices=["uniform", "jittered"],
                    help="jittered: the cell-centred grid of round(N^(1/3))^3 points with U(-h/4, h/4) jitter")
     p.add_argument("--forces", action="store_true",
-                   help="also time the energy and forces (charges ~ U(-1,1) FP32, pivots frozen) and check them "
-                        "against the exact dense forces on 4,096 sampled points")
+                   help="(the default) time the energy and forces (charges ~ U(-1,1) FP32, pivots frozen) and check "
+                        "them against the exact dense forces on 4,096 sampled points")
+    p.add_argument("--no-forces", action="store_true", help="skip the energy and forces")
+    p.add_argument("--no-wide", action="store_true",
+                   help="skip the 32-column product (3xTF32 tensor cores) beside the one-column headline")
     return p.parse_args()
 
 
@@ -503,11 +506,35 @@ def main():
         e2e_step()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / a.steps
 
+    # 32 right-hand sides in one call (3xTF32 factor products on the tensor cores)
+    wide = None
+    if not a.no_wide and nrhs == 1 and a.leaf <= 128:
+        xw = I.rhs_normal(a.N, 32, xseed + 17).astype(np.float32)
+        Xw = torch.from_numpy(np.ascontiguousarray(xw.T)).cuda()
+        Yw = torch.empty_like(Xw)
+        w_ms = time_steps(lambda: A.matvec_raw(Xw.data_ptr(), Yw.data_ptr(), 32), max(2, a.steps // 4), 2, torch,
+                          None)
+        wph = np.array(A.matvec_profile(Xw.data_ptr(), Yw.data_ptr(), 32))
+        fb = 4 * (st["u_entries"] + st["v_entries"])
+        wide = {"nrhs": 32, "ms": round(w_ms, 4), "ms_per_column": round(w_ms / 32, 4),
+                "phase_ms": {"k_permute_in_w": round(float(wph[0]), 4), "k_tc_stream_gather": round(float(wph[1]), 4),
+                             "k_reduce_partials_w": round(float(wph[2]), 4), "k_tc_stream_far": round(float(wph[3]), 4)},
+                "factor_bytes_per_pass": fb,
+                "factor_GBps": round(fb / (w_ms * 1e-3) / 1e9, 1),
+                "factor_hbm_frac": round(fb / (w_ms * 1e-3) / 1e9 / peaks()[0], 4)}
+        if rank == 0:
+            from oracle import oracle as O
+            wrows = I.sample_rows(a.N, 1000, 9)
+            ref = O.direct_rows(pts, xw[:, [0, 31]].astype(np.float64), wrows)
+            got = Yw.cpu().numpy().T[wrows][:, [0, 31]].astype(np.float64)
+            wide["rel_err_1000_rows_cols_0_31"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        del Xw, Yw
+
     y_host = y.cpu().numpy().T          # N x nrhs
     if nrhs == 1:
         y_host = y_host.reshape(-1)
     forces = None
-    if a.forces:
+    if not a.no_forces:
         qh = I.rhs_uniform(a.N, 1, 6 + 1000 * rank)[:, 0].astype(np.float32)
         qd = torch.from_numpy(qh).cuda()
         Fo = {}
@@ -620,7 +647,7 @@ def main():
         "metric": METRIC, "value": round(ms, 4), "unit": "ms", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": round(ms, 4), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload(a),
-        "rel_err_sampled_rows": err, "fp64": fp64, "forces": forces, "symmetric": sym,
+        "rel_err_sampled_rows": err, "fp64": fp64, "forces": forces, "symmetric": sym, "nrhs32": wide,
         "speedup_vs_fp64": (round(fp64["ms"] / ms, 3) if fp64 and fp64.get("ms") else None),
         "interactions_per_s": N * N * nrhs / (ms * 1e-3),
         "matvec_alg_GBps": round(total_bytes / (ms * 1e-3) / 1e9, 1),
