@@ -164,13 +164,15 @@ h3d_status h3d_matvec(h3d_handle h, const void *x, void *y, int nrhs, void *stre
 
 /* y = A~^T x: the same blocks with the roles of the two factors exchanged (the
  * compressed operator is not exactly symmetric because every ordered pair is
- * compressed on its own, as Alg. 1 does).  Arguments as h3d_matvec.          */
+ * compressed on its own, as Alg. 1 does; with H3D_STORE_SYMMETRIC it is, and
+ * this runs the forward product).  Arguments as h3d_matvec.                  */
 h3d_status h3d_matvec_T(h3d_handle h, const void *x, void *y, int nrhs, void *stream);
 
 /* Energy of charges q and its gradient (differentiation of the product):
  *   E = 1/2 q^T A~ q,   grad = dE/dq = 1/2 (A~ + A~^T) q
  * with A~ the operator of h3d_matvec (Alg. 2); both products are taken because
- * A~ is not exactly symmetric (Alg. 1 compresses every ordered pair on its own).
+ * A~ is not exactly symmetric (Alg. 1 compresses every ordered pair on its own;
+ * with H3D_STORE_SYMMETRIC it is, and one product gives both).
  *   q     device, N values in the caller's order (read only).
  *   E     device, one double: the energy, reduced in FP64 in a fixed order.
  *   grad  device, N values (element type of the handle), overwritten; NULL skips
@@ -185,10 +187,12 @@ h3d_status h3d_energy(h3d_handle h, const void *q, double *E, void *grad, void *
  * of its pivots (Sec. 4.1, Eq. prank), so E is the energy of the paper's
  * representation (it equals that of h3d_energy up to rounding times the
  * condition of K(sigma,tau)).  Kernel entries and their gradients are
- * recomputed (nothing is stored): the admissible blocks in FP64 for every
- * handle (their weights carry the condition of K(sigma,tau)), the near field in
- * the handle's precision; K(sigma,tau) is factored in FP64 with partial
- * pivoting.  Supported for every kernel of h3d_kernel.
+ * recomputed (nothing is stored): the admissible blocks to ~1e-12 or better
+ * (their weights carry the condition of K(sigma,tau)): in FP64 for FP64
+ * handles, in float-float on the FP32 pipes for FP32 handles of the Laplace
+ * and 1/r^4 kernels, in FP64 for the other FP32 handles; the near field in the
+ * handle's precision; K(sigma,tau) is factored in FP64 with partial pivoting.
+ * Supported for every kernel of h3d_kernel and every storage.
  *   q  device, N charges in the caller's order (element type of the handle).
  *   E  device, one double: the energy.
  *   F  device, N x 3 doubles, row-major, the caller's order; overwritten.
@@ -372,9 +376,10 @@ h3d_status h3d_export_pivots(h3d_handle h, int *rank, int *sigma, int *tau);
  * by an independent CPU search) and to restore pivots saved earlier.
  *   rank, sigma, tau  host, in the format of h3d_export_pivots; 0 <= rank[b] <=
  *          min(m_b, n_b, rank_cap), indices inside the block, no row or column
- *          twice in one block; otherwise H3D_ERR_ARG.  Pivots that ACA could
- *          not have chosen (a vanishing residual at a pivot) give non-finite
- *          factors.
+ *          twice in one block; with H3D_STORE_SYMMETRIC every mirror block
+ *          carries its primary's rank and swapped pivots; otherwise
+ *          H3D_ERR_ARG.  Pivots that ACA could not have chosen (a vanishing
+ *          residual at a pivot) give non-finite factors.
  * Builds the replacement first (synchronising `stream` and the device) and
  * swaps it in only on success; on error the handle is unchanged.  Batches that
  * hold the handle must be re-created afterwards.                              */
