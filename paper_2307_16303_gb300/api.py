@@ -119,7 +119,13 @@ def _stream_ptr(stream) -> int | None:
 
 
 class H3DMatrix:
-    """A built HODLR3D operator.  ``points``: (N, 3) float64 CUDA tensor."""
+    """A built HODLR3D operator.  ``points``: (N, 3) float64 CUDA tensor.
+
+    ``storage``: "factors" (the ACA factors of every ordered block, Alg. 1),
+    "skeleton" (pivots and the LU of K(sigma,tau), entries recomputed in every
+    product) or "symmetric" (each unordered pair compressed once, the mirror its
+    transpose: an exactly symmetric operator with fewer stored bytes); see
+    h3d_storage in include/h3d.h."""
 
     def __init__(self, points, kernel: str = "laplace", leaf_size: int = 128, tol: float = 1e-7,
                  precision: str = "fp32_3xtf32", rank_cap: int = 512, kappa: float = 1.0, lo=(-1.0, -1.0, -1.0),
