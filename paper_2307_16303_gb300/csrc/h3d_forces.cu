@@ -304,12 +304,19 @@ __device__ void factor_solve_warp(double *M, int r, double *c, double *a, const 
 // gradients, and the sums over the points, in float-float on the FP32 pipes
 // (coordinates split hi + lo, FP32 charges exact); M, its factorisation, the
 // solves and the -a^T dM c term stay FP64.
+// per-block arrays in dynamic shared memory, sized by the largest rank mr:
+// c, a, u0 (mr doubles each), gs, gt (3 mr doubles each), sp, tp, piv (mr ints)
+inline size_t far_smem(int mr) { return (size_t)mr * (9 * sizeof(double) + 3 * sizeof(int)); }
+constexpr int kFarCtasMax = 6;   // per SM (80 registers; fewer when mr makes the arrays large)
+
 template <bool FF_>
-__global__ void __launch_bounds__(kFThreads) k_force_far(ForceArgs A) {
+__global__ void __launch_bounds__(kFThreads, kFarCtasMax) k_force_far(ForceArgs A) {
     using T = double;
-    __shared__ int sp[kMaxRank], tp[kMaxRank], piv[kMaxRank];
-    __shared__ double c[kMaxRank], a[kMaxRank], u0[kMaxRank];
-    __shared__ double gs[kMaxRank][3], gt[kMaxRank][3];   // sum_j q_j dK(sigma_k, p_j), sum_i q_i dK(p_i, tau_k)
+    extern __shared__ __align__(16) unsigned char fsm[];
+    double *c = reinterpret_cast<double *>(fsm), *a = c + A.mr, *u0 = a + A.mr;
+    double(*gs)[3] = reinterpret_cast<double(*)[3]>(u0 + A.mr);   // sum_j q_j dK(sigma_k, p_j)
+    double(*gt)[3] = gs + A.mr;                                     // sum_i q_i dK(p_i, tau_k)
+    int *sp = reinterpret_cast<int *>(gt + A.mr), *tp = sp + A.mr, *piv = tp + A.mr;
     __shared__ double red[kFWarps];
     __shared__ int pmax, sblk[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -688,11 +695,13 @@ unsigned gn(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1
 }  // namespace
 
 void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s) {
-    constexpr int kFarCtas = 5;   // per SM (43 KB of shared memory each)
     int dev = 0, sms = 0;
     H3D_CUDA(cudaGetDevice(&dev));
     H3D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h.nblk, (int64_t)kFarCtas * sms));
+    // CTAs per SM: up to kFarCtasMax while their arrays fit the SM's shared memory
+    const size_t fsm = far_smem(std::max(1, h.max_rank));
+    const int far_ctas = (int)std::max<size_t>(1, std::min<size_t>(kFarCtasMax, (200u << 10) / (fsm + 1024)));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h.nblk, (int64_t)far_ctas * sms));
     const int64_t nparts = h.nleaf + h.nblk;
     const bool fp32 = h.prec != H3D_FP64;
     if (!h.fG) {   // scratch kept by the handle
@@ -744,8 +753,8 @@ void forces(Handle &h, const void *q, double *E, double *F, cudaStream_t s) {
         k_force_near<double><<<h.nleaf, kFThreads, 0, s>>>(A);
     if (h.nblk > 0) {
         H3D_CUDA(cudaMemsetAsync(h.fctr, 0, sizeof(int), s));
-        if (fp32 && ff_kernel_supported(h.kernel)) k_force_far<true><<<grid, kFThreads, 0, s>>>(A);
-        else k_force_far<false><<<grid, kFThreads, 0, s>>>(A);
+        if (fp32 && ff_kernel_supported(h.kernel)) k_force_far<true><<<grid, kFThreads, fsm, s>>>(A);
+        else k_force_far<false><<<grid, kFThreads, fsm, s>>>(A);
     }
     k_forces_out<<<gn(N, 256), 256, 0, s>>>(h.fG, h.perm, N, F);
     const int nout = (int)std::min<int64_t>(1024, std::max<int64_t>(1, nparts));
