@@ -307,7 +307,7 @@ __device__ void factor_solve_warp(double *M, int r, double *c, double *a, const 
 // per-block arrays in dynamic shared memory, sized by the largest rank mr:
 // c, a, u0 (mr doubles each), gs, gt (3 mr doubles each), sp, tp, piv (mr ints)
 inline size_t far_smem(int mr) { return (size_t)mr * (9 * sizeof(double) + 3 * sizeof(int)); }
-constexpr int kFarCtasMax = 6;   // per SM (80 registers; fewer when mr makes the arrays large)
+constexpr int kFarCtasMax = 7;   // per SM (72 registers; fewer when mr makes the arrays large)
 
 template <bool FF_>
 __global__ void __launch_bounds__(kFThreads, kFarCtasMax) k_force_far(ForceArgs A) {
